@@ -1,0 +1,84 @@
+"""The oracle pinned to closed forms, brute force and the paper's exact identities."""
+import pytest
+
+from seeded_inputs import splitmix64, uniform01
+import oracle_pins as P
+
+
+def test_splitmix64_published_values():
+    # first outputs of SplitMix64 seeded with 0 and with 1234567 (reference implementation)
+    assert [int(v) for v in splitmix64(0, 0, 3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert int(splitmix64(1234567, 0, 1)[0]) == 6457827717110365317
+    u = uniform01(5, 0, 10000)
+    assert 0.0 <= u.min() and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.01
+
+
+def test_dft_matches_defining_sum():
+    assert P.pin_dft_bruteforce() < 1e-13
+
+
+def test_dft_backends_agree():
+    assert P.pin_backends() < 1e-13
+
+
+def test_spectral_derivatives_trig_polynomials():
+    assert P.pin_derivatives() < 1e-12
+
+
+def test_nonlinear_potential_cosine_closed_form():
+    assert P.pin_nonlinear_cosine() < 1e-12
+
+
+def test_nonlinear_potential_against_symbolic_calculus():
+    assert P.pin_nonlinear_sympy() < 1e-12
+
+
+def test_summation_by_parts_odd_n():
+    assert P.pin_sbp_odd() < 1e-12
+
+
+def test_E1_lower_bound():
+    assert P.min_E1_margin() >= -1e-14
+
+
+def test_scheme_residual_2d():
+    assert P.pin_residual(2) < 1e-12
+
+
+def test_scheme_residual_3d():
+    assert P.pin_residual(3) < 1e-12
+
+
+def test_bdf1_start_residual():
+    assert P.pin_bdf1_residual() < 1e-12
+
+
+def test_exact_dissipation_identity():
+    assert P.pin_dissipation() < 1e-9
+
+
+def test_linear_part_closed_form():
+    assert P.pin_linear_closed_form() < 1e-12
+
+
+def test_mass_conservation():
+    assert P.mass_drift() < 1e-13
+
+
+def test_constant_state_is_steady():
+    assert P.constant_state_error() < 1e-13
+
+
+def test_ghost_point_closed_form():
+    assert P.ghost_cosine_error() < 1e-12
+
+
+def test_second_order_manufactured_solution():
+    slope = P.manufactured_slope()
+    assert -2.2 < slope < -1.8, slope
+
+
+def test_self_convergence_ratio():
+    ratio = P.self_convergence_ratio()
+    assert 3.6 < ratio < 4.4, ratio
