@@ -1,0 +1,146 @@
+/*
+ * spfc.h -- C interface of the GB300 BDF2-SAV Fourier pseudo-spectral solver
+ * for the square phase field crystal (SPFC) equation.
+ *
+ * The problem (Sec. 1, eqs. energy-SPFC and equation-SPFC): on a periodic box
+ * [0,L]^d, d = 2 or 3, evolve the density phi by the H^{-1} gradient flow
+ *     phi_t = Delta mu,  mu = -div(beta |grad phi|^2 grad phi) + a phi + 2 Delta phi + Delta^2 phi,
+ * a = 1 - eps > 0, of the energy
+ *     E(phi) = int a/2 phi^2 + beta/4 |grad phi|^4 - |grad phi|^2 + 1/2 (Delta phi)^2.
+ * (The paper fixes beta = 1.) Space: Fourier collocation on N points per axis
+ * (Sec. 2.1). Time: the second-order BDF2 scheme with a scalar auxiliary
+ * variable r = sqrt(E_1) (eq. scheme-SAV-1), E_1 = int beta/4 |grad phi|^4 -
+ * |grad phi|^2 + (1 + 1/beta), solved per step by the scalar elimination of
+ * Sec. 2.3 (eqs. solver-1 .. solver-6): a few FFTs, diagonal solves with the
+ * positive symbol 3/2 + dt |k|^2 (a + |k|^4), and global inner products.
+ *
+ * Conventions shared by all calls
+ *  - Every call returns an spfc_status; on failure spfc_last_error() gives a
+ *    message. A device-side failure (non-finite value or an infeasible scalar
+ *    system in the SAV solve) is latched on the GPU, stops further steps, and
+ *    is reported by the next call that synchronises (spfc_energy, spfc_mass,
+ *    spfc_sav_scalars, spfc_get_field, spfc_sync).
+ *  - Real fields are float64, row-major with x fastest: index x + N*(y + N*z).
+ *  - Pointers flagged *_on_device are CUDA device pointers on the handle's
+ *    device; they are only read or written during the call (on the handle's
+ *    stream, which is synchronised before the call returns). Host pointers
+ *    are plain memory and are likewise not retained.
+ *  - The handle owns all of its device memory (allocated in spfc_create,
+ *    released in spfc_destroy) and launches all work on the stream given at
+ *    creation. A handle must not be used from two threads at once.
+ *  - The GPU supports N in {16, 32, 64, 128, 256, 512} (2D) and
+ *    {16, 32, 64, 128} (3D), the same N on every axis.
+ */
+#ifndef SPFC_H
+#define SPFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spfc_s* spfc_t;
+
+typedef enum {
+  SPFC_OK = 0,
+  SPFC_EINVAL = 1,     /* invalid argument */
+  SPFC_ENOMEM = 2,     /* device allocation failed */
+  SPFC_ECUDA = 3,      /* CUDA runtime error */
+  SPFC_ENONFINITE = 4, /* non-finite value or infeasible SAV scalar system (latched on device) */
+  SPFC_ETIMEOUT = 5,   /* a bounded device-side wait expired */
+  SPFC_ESTATE = 6      /* call out of order (e.g. step before init) */
+} spfc_status;
+
+/* Start-up of the two-level scheme. */
+typedef enum {
+  SPFC_START_BDF1 = 0,  /* one first-order SAV step from phi^0 (not printed in the paper) */
+  SPFC_START_GHOST = 1, /* phi^{-1} = phi^0 - dt Delta_N mu^0, eq. scheme-SAV-initial-1 */
+  SPFC_START_COPY = 2   /* phi^{-1} = phi^0, the restart rule of Sec. 5.2 */
+} spfc_start;
+
+typedef enum {
+  SPFC_FP64 = 0,      /* all arithmetic in float64 */
+  SPFC_FP32_BULK = 1  /* FFTs and pointwise work in float32; E_1, inner products, r and the
+                         zero mode (mass) in float64 */
+} spfc_precision;
+
+/* Create a solver for one run.
+ * d: 2 or 3; n[d]: points per axis (x first, all equal); L[d]: box lengths (x first);
+ * eps: a = 1 - eps must be > 0; beta > 0; dt > 0; precision: spfc_precision;
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on the current device.
+ * Cites: Sec. 1 (problem), Sec. 2.1 (grid), eq. scheme-SAV-1 (scheme).
+ * Errors: SPFC_EINVAL for unsupported sizes or parameters, SPFC_ENOMEM, SPFC_ECUDA. */
+int spfc_create(int d, const int* n, const double* L, double eps, double beta, double dt,
+                int precision, void* cuda_stream, spfc_t* out);
+
+/* Load phi^0 (N^d float64 values) and start the scheme with `mode` (spfc_start).
+ * After BDF1 the handle holds (phi^1, phi^0, r^1, r^0); after GHOST/COPY it
+ * holds (phi^0, phi^{-1}, r^0, r^{-1}) with r = sqrt(E_{1,N}) as in the line
+ * after eq. scheme-SAV-initial-2. */
+int spfc_init(spfc_t h, const double* phi0, int phi0_on_device, int mode);
+
+/* Set the two time levels and auxiliary scalars directly: phi = phi^n,
+ * phi_prev = phi^{n-1}, r = r^n, r_prev = r^{n-1} (used for restarts and
+ * for per-step comparisons from a given state). */
+int spfc_set_state(spfc_t h, const double* phi, const double* phi_prev, double r, double r_prev,
+                   int on_device);
+
+/* Advance nsteps >= 0 steps of eq. scheme-SAV-1 (asynchronous on the stream;
+ * a latched device failure is returned by the next synchronising call). */
+int spfc_step(spfc_t h, int64_t nsteps);
+
+/* Energies of the current state (synchronising):
+ * E_orig = E_N(phi^n) (eq. energy-discrete-spectral, with beta),
+ * E_mod  = the modified energy of eq. discrete energy,
+ * E_breve = a/2 ||phi||^2 + 1/2 ||Delta_N phi||^2 + r^2 (Sec. 5.2). Any pointer may be NULL. */
+int spfc_energy(spfc_t h, double* E_orig, double* E_mod, double* E_breve);
+
+/* mass = <phi, 1> = h^d sum phi (invariant, Theorem SPFC solvability); mean = mass / |Omega|.
+ * Either pointer may be NULL. */
+int spfc_mass(spfc_t h, double* mass, double* mean);
+
+/* Scalars of the current state and of the last SAV solve (synchronising):
+ * out[0] = r^n, out[1] = r^{n-1}, out[2] = xi = r^n / sqrt(E_1), out[3] = gamma =
+ * <N, A^{-1} Delta N> (<= 0, eq. solver-5), out[4] = E_1 at the extrapolation,
+ * out[5] = the steps taken since init. `nout` entries (<= 6) are written. */
+int spfc_sav_scalars(spfc_t h, double* out, int nout);
+
+/* Copy phi^n (which = 0) or phi^{n-1} (which = 1) to `out` (N^d float64 values). */
+int spfc_get_field(spfc_t h, double* out, int out_on_device, int which);
+
+/* Change dt and restart the two-level scheme with phi^{n-1} = phi^n (Sec. 5.2). */
+int spfc_dt_change(spfc_t h, double dt_new);
+
+/* Write / read a checkpoint: the exact device state (both spectral levels in the
+ * handle's precision, r^n, r^{n-1}, the step count) plus the grid and parameters.
+ * A resumed run continues bit-identically. spfc_load rejects a file whose grid,
+ * precision, L, dt, eps or beta differ from the handle's (SPFC_EINVAL). */
+int spfc_save(spfc_t h, const char* path);
+int spfc_load(spfc_t h, const char* path);
+
+/* Wait for the handle's stream and report any latched device status. */
+int spfc_sync(spfc_t h);
+
+/* Per-kernel timing: when enabled (on != 0), spfc_step launches its kernels
+ * one by one with CUDA events around each (no graph), and
+ * spfc_kernel_times() returns, per kernel class, the number of launches and
+ * the summed device milliseconds since the last reset (synchronising).
+ * names[i] receives a static string. Returns the number of classes. */
+int spfc_set_timing(spfc_t h, int on);
+int spfc_kernel_times(spfc_t h, int max, const char** names, int64_t* launches, double* ms);
+
+/* Device memory held by the handle, in bytes. */
+int64_t spfc_device_bytes(spfc_t h);
+
+void spfc_destroy(spfc_t h);
+
+/* Message of the last failed call on this handle (or of the last failed
+ * spfc_create on this thread when h is NULL). Never NULL. */
+const char* spfc_last_error(spfc_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPFC_H */

@@ -1,0 +1,11 @@
+// float32-bulk instantiation of the solvers (FP64 reductions and scalars).
+#include "spfc_solver2d.cuh"
+
+namespace spfc {
+SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int* status, std::string* err) {
+  if (P.d == 2) return make_solver_2d<float>(P, st, status, err);
+  *status = 1;
+  *err = "3D is not available in this build";
+  return nullptr;
+}
+}  // namespace spfc

@@ -1,0 +1,529 @@
+// Host driver of the 2D step kernels for one run: device buffers, the launch
+// sequences of init / step / diagnostics, and CUDA-graph replay of the step.
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spfc_internal.h"
+#include "spfc_kernels2d.cuh"
+
+namespace spfc {
+
+#define SPFC_CK(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return 3;                                                                    \
+    }                                                                              \
+  } while (0)
+
+// Launch shape per grid size: CT kx columns per column-pass block, RPC rows
+// per row-pass block. Every block fills whole warps.
+template <int N> struct Shape2D {
+  static constexpr int T = fft_shape<N>::T;
+  static constexpr int CT = (32 / T > 4) ? 32 / T : 4;
+  static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
+  static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
+  static_assert(N % RPC == 0 && (RPC * T) % 32 == 0, "row tile must divide N and fill warps");
+};
+
+template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
+  tw.resize(TW_N);
+  for (int m = 0; m < TW_N; ++m) {
+    // exp(-2 pi i m / TW_N) from libm in double precision
+    const double ang = 2.0 * M_PI * (double)m / (double)TW_N;
+    tw[m].x = (R)std::cos(ang);
+    tw[m].y = (R)(-std::sin(ang));
+  }
+}
+
+template <typename R, int N>
+class Solver2D final : public SolverBase {
+  using C = C_t<R>;
+  using SH = Shape2D<N>;
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T;
+  static constexpr int GCOL = (NH + CT - 1) / CT;
+  static constexpr int GROW = N / RPC;
+  static constexpr int PW_THREADS = 256;
+
+ public:
+  Solver2D(const Params& p, cudaStream_t s) : st_(s) { P = p; }
+
+  int setup() {
+    const size_t sb = (size_t)N * NH * sizeof(C);
+    spec_bytes_ = sb;
+    total_ = 0;
+    auto al = [&](void** ptr, size_t bytes) -> cudaError_t {
+      cudaError_t e = cudaMalloc(ptr, bytes);
+      if (e == cudaSuccess) total_ += bytes;
+      return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = al((void**)&S_.s[0], sb);
+    if (e == cudaSuccess) e = al((void**)&S_.s[1], sb);
+    if (e == cudaSuccess) e = al((void**)&Nhat_, sb);
+    if (e == cudaSuccess) e = al((void**)&W_[0], sb);
+    if (e == cudaSuccess) e = al((void**)&W_[1], sb);
+    if (e == cudaSuccess) e = al((void**)&real_, (size_t)N * N * sizeof(double));
+    gpw_ = (int)std::min<size_t>(((size_t)N * NH + PW_THREADS - 1) / PW_THREADS, 608);
+    nE_ = GROW;
+    nG_ = GCOL;
+    if (e == cudaSuccess) e = al((void**)&partE_, 2 * (size_t)nE_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&partG_, 3 * (size_t)nG_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
+    if (e == cudaSuccess) e = al((void**)&counter_, sizeof(unsigned));
+    if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
+    if (e != cudaSuccess) {
+      err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+      return (e == cudaErrorMemoryAllocation) ? 2 : 3;
+    }
+    std::vector<C> tw;
+    host_twiddles<R>(tw);
+    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemset(counter_, 0, sizeof(unsigned)));
+    SavScal z{};
+    SPFC_CK(cudaMemcpy(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemset(S_.s[0], 0, sb));
+    SPFC_CK(cudaMemset(S_.s[1], 0, sb));
+    SPFC_CK(cudaMemset(Nhat_, 0, sb));
+    // opt in to > 48 KB dynamic shared memory where a tile needs it
+    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_STEP>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_GRAD>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_FIELD>, smem_col(1)));
+    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_NONLIN>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_ENERGY>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_OUT_REAL>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_IN_REAL>, smem_row()));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_BDF2>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_BDF1>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_NHAT>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_TO_STATE>, smem_col(1)));
+    SPFC_CK(cudaStreamCreateWithFlags(&cap_st_, cudaStreamNonBlocking));
+    return 0;
+  }
+
+  ~Solver2D() override {
+    if (g1_) cudaGraphExecDestroy(g1_);
+    if (g16_) cudaGraphExecDestroy(g16_);
+    for (auto ev : evpool_) cudaEventDestroy(ev);
+    if (cap_st_) cudaStreamDestroy(cap_st_);
+    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], real_, partE_, partG_, partN_, partS_, sc_, counter_, tw_};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+
+  int64_t device_bytes() const override { return (int64_t)total_; }
+
+  // ---- init / state --------------------------------------------------------
+  int init(const double* phi0, bool on_device, int mode) override {
+    int rc = load_field(phi0, on_device, /*slot_rel=*/0, /*reset=*/true);
+    if (rc) return rc;
+    if (mode == 0) {  // BDF1
+      rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+      rc = launch_row(RW_NONLIN); if (rc) return rc;
+      rc = launch_col_fwd(CF_BDF1, 0); if (rc) return rc;
+      rc = finalize(); if (rc) return rc;
+    } else if (mode == 1) {  // ghost
+      rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+      rc = launch_row(RW_NONLIN); if (rc) return rc;
+      rc = scalar_op(SO_R_NEWEST, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+      rc = launch_col_fwd(CF_NHAT, 0); if (rc) return rc;
+      k2d_ghost<R><<<gpw_, PW_THREADS, 0, st_>>>(P, S_, Nhat_, sc_);
+      SPFC_CK(cudaGetLastError());
+      rc = launch_col_inv(CI_GRAD, 1); if (rc) return rc;
+      rc = launch_row(RW_ENERGY); if (rc) return rc;
+      rc = scalar_op(SO_R_PREV, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+    } else if (mode == 2) {  // copy
+      rc = copy_newest_to_prev(); if (rc) return rc;
+      rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+      rc = launch_row(RW_ENERGY); if (rc) return rc;
+      rc = scalar_op(SO_R_NEWEST, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+      rc = scalar_op(SO_R_PREV, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+    } else {
+      err = "unknown start mode";
+      return 1;
+    }
+    inited = true;
+    return 0;
+  }
+
+  int set_state(const double* phi, const double* phi_prev, double r, double r_prev, bool on_device) override {
+    int rc = load_field(phi, on_device, 0, true);
+    if (rc) return rc;
+    rc = load_field(phi_prev, on_device, 1, false);
+    if (rc) return rc;
+    rc = scalar_op(SO_SET_R, nullptr, 0, nullptr, 0, 0, r, r_prev);
+    if (rc) return rc;
+    inited = true;
+    return 0;
+  }
+
+  int dt_change(double dt) override {
+    int rc = finalize(); if (rc) return rc;
+    P.dt = dt;
+    drop_graphs();
+    rc = copy_newest_to_prev(); if (rc) return rc;
+    rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+    rc = launch_row(RW_ENERGY); if (rc) return rc;
+    rc = scalar_op(SO_R_NEWEST, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+    rc = scalar_op(SO_R_PREV, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+    return 0;
+  }
+
+  // ---- stepping ------------------------------------------------------------
+  int step(long long n) override {
+    if (n <= 0) return 0;
+    if (timing_) {
+      for (long long i = 0; i < n; ++i) {
+        int rc = timed_step();
+        if (rc) return rc;
+      }
+      return 0;
+    }
+    int rc = ensure_graphs();
+    if (rc) return rc;
+    long long chunks = n / 16, rest = n % 16;
+    for (long long i = 0; i < chunks; ++i) SPFC_CK(cudaGraphLaunch(g16_, st_));
+    for (long long i = 0; i < rest; ++i) SPFC_CK(cudaGraphLaunch(g1_, st_));
+    return 0;
+  }
+
+  // ---- diagnostics ----------------------------------------------------------
+  int energy(double* E_orig, double* E_mod, double* E_breve) override {
+    int rc = finalize(); if (rc) return rc;
+    k2d_norms<R><<<gpw_, PW_THREADS, 0, st_>>>(P, S_, sc_, partN_);
+    SPFC_CK(cudaGetLastError());
+    rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+    rc = launch_row(RW_ENERGY); if (rc) return rc;
+    rc = scalar_op(SO_ENERGY, partE_, nE_, partN_, gpw_, 0); if (rc) return rc;
+    SavScal h;
+    rc = read_scal(&h); if (rc) return rc;
+    if (E_orig) *E_orig = h.E_orig;
+    if (E_mod) *E_mod = h.E_mod;
+    if (E_breve) *E_breve = h.E_breve;
+    return 0;
+  }
+
+  int mass(double* m, double* mean) override {
+    int rc = finalize(); if (rc) return rc;
+    SavScal h;
+    rc = read_scal(&h); if (rc) return rc;
+    if (m) *m = P.vol * h.zm[h.p];
+    if (mean) *mean = h.zm[h.p];
+    return 0;
+  }
+
+  int scalars(SavScal* out) override {
+    int rc = finalize(); if (rc) return rc;
+    return read_scal(out);
+  }
+
+  int get_field(double* out, bool on_device, int which) override {
+    int rc = finalize(); if (rc) return rc;
+    rc = launch_col_inv(CI_FIELD, which); if (rc) return rc;
+    rc = launch_row(RW_OUT_REAL); if (rc) return rc;
+    const size_t bytes = (size_t)N * N * sizeof(double);
+    SPFC_CK(cudaMemcpyAsync(out, real_, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st_));
+    return sync();
+  }
+
+  int sync() override {
+    SPFC_CK(cudaStreamSynchronize(st_));
+    SavScal h;
+    SPFC_CK(cudaMemcpy(&h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost));
+    if (h.status != DEV_OK) {
+      err = "device status: non-finite value or infeasible SAV scalar system";
+      return h.status;
+    }
+    return 0;
+  }
+
+  int dump(std::string* blob) override {
+    int rc = finalize(); if (rc) return rc;
+    SavScal h;
+    rc = read_scal(&h); if (rc) return rc;
+    blob->assign(sizeof(SavScal) + 2 * spec_bytes_, '\0');
+    char* b = &(*blob)[0];
+    std::memcpy(b, &h, sizeof(SavScal));
+    SPFC_CK(cudaMemcpy(b + sizeof(SavScal), S_.s[h.p], spec_bytes_, cudaMemcpyDeviceToHost));
+    SPFC_CK(cudaMemcpy(b + sizeof(SavScal) + spec_bytes_, S_.s[1 - h.p], spec_bytes_, cudaMemcpyDeviceToHost));
+    return 0;
+  }
+
+  int restore(const std::string& blob) override {
+    if (blob.size() != sizeof(SavScal) + 2 * spec_bytes_) { err = "checkpoint size mismatch"; return 1; }
+    SavScal h;
+    std::memcpy(&h, blob.data(), sizeof(SavScal));
+    const int p = h.p;
+    h.p = 0;
+    h.pending = PEND_NONE;
+    h.status = DEV_OK;
+    const double z0 = h.zm[p], z1 = h.zm[1 - p];
+    h.zm[0] = z0;
+    h.zm[1] = z1;
+    drop_graphs();
+    SPFC_CK(cudaStreamSynchronize(st_));
+    SPFC_CK(cudaMemcpy(S_.s[0], blob.data() + sizeof(SavScal), spec_bytes_, cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(S_.s[1], blob.data() + sizeof(SavScal) + spec_bytes_, spec_bytes_, cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(sc_, &h, sizeof(SavScal), cudaMemcpyHostToDevice));
+    inited = true;
+    return 0;
+  }
+
+  int set_timing(bool on) override {
+    timing_ = on;
+    return 0;
+  }
+
+  int kernel_times(KernelTimes* kt) override {
+    SPFC_CK(cudaStreamSynchronize(st_));
+    for (auto& rec : trecs_) {
+      float ms = 0.f;
+      SPFC_CK(cudaEventElapsedTime(&ms, evpool_[rec.e0], evpool_[rec.e1]));
+      tms_[rec.cls] += ms;
+      tcount_[rec.cls] += 1;
+    }
+    trecs_.clear();
+    evnext_ = 0;
+    kt->names = {"col_inv", "row", "col_fwd"};
+    kt->launches.assign(tcount_, tcount_ + 3);
+    kt->ms.assign(tms_, tms_ + 3);
+    for (int i = 0; i < 3; ++i) { tcount_[i] = 0; tms_[i] = 0.0; }
+    return 0;
+  }
+
+ private:
+  template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  static constexpr size_t smem_col(int nf) { return (size_t)nf * N * (CT + 1) * sizeof(C); }
+  static constexpr size_t smem_row() { return (size_t)RPC * (N + 1) * sizeof(C); }
+
+  int launch_col_inv(int mode, int which) {
+    switch (mode) {
+      case CI_STEP:
+        k2d_col_inv<R, N, CT, CI_STEP><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        break;
+      case CI_GRAD:
+        k2d_col_inv<R, N, CT, CI_GRAD><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        break;
+      default:
+        k2d_col_inv<R, N, CT, CI_FIELD><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+    }
+    SPFC_CK(cudaGetLastError());
+    return 0;
+  }
+  int launch_row(int mode) {
+    switch (mode) {
+      case RW_NONLIN:
+        k2d_row<R, N, RPC, RW_NONLIN><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        break;
+      case RW_ENERGY:
+        k2d_row<R, N, RPC, RW_ENERGY><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        break;
+      case RW_OUT_REAL:
+        k2d_row<R, N, RPC, RW_OUT_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        break;
+      default:
+        k2d_row<R, N, RPC, RW_IN_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+    }
+    SPFC_CK(cudaGetLastError());
+    return 0;
+  }
+  int launch_col_fwd(int mode, int target) {
+    switch (mode) {
+      case CF_BDF2:
+        k2d_col_fwd<R, N, CT, CF_BDF2><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        break;
+      case CF_BDF1:
+        k2d_col_fwd<R, N, CT, CF_BDF1><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        break;
+      case CF_NHAT:
+        k2d_col_fwd<R, N, CT, CF_NHAT><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        break;
+      default:
+        k2d_col_fwd<R, N, CT, CF_TO_STATE><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+    }
+    SPFC_CK(cudaGetLastError());
+    return 0;
+  }
+  int scalar_op(int op, const double* a, int na, const double* b, int nb, int arg, double x0 = 0, double x1 = 0) {
+    k_scalar_op<<<1, 32, 0, st_>>>(P, sc_, op, a, na, b, nb, arg, x0, x1);
+    SPFC_CK(cudaGetLastError());
+    return 0;
+  }
+  int read_scal(SavScal* h) {
+    SPFC_CK(cudaMemcpyAsync(h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaStreamSynchronize(st_));
+    if (h->status != DEV_OK) {
+      err = "device status: non-finite value or infeasible SAV scalar system";
+      return h->status;
+    }
+    return 0;
+  }
+
+  // materialise a pending update (no-op otherwise)
+  int finalize() {
+    k2d_finalize<R><<<gpw_, PW_THREADS, 0, st_>>>(P, S_, Nhat_, sc_);
+    SPFC_CK(cudaGetLastError());
+    return scalar_op(SO_FLIP, nullptr, 0, nullptr, 0, 0);
+  }
+
+  int copy_newest_to_prev() {
+    SavScal h;
+    int rc = read_scal(&h);
+    if (rc) return rc;
+    SPFC_CK(cudaMemcpyAsync(S_.s[1 - h.p], S_.s[h.p], spec_bytes_, cudaMemcpyDeviceToDevice, st_));
+    h.zm[1 - h.p] = h.zm[h.p];
+    SPFC_CK(cudaMemcpyAsync(sc_, &h, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
+    SPFC_CK(cudaStreamSynchronize(st_));
+    return 0;
+  }
+
+  // Transform a real field into slot (newest if slot_rel == 0, previous
+  // otherwise). reset: clear the scalar record first (p = 0, no pending).
+  int load_field(const double* f, bool on_device, int slot_rel, bool reset) {
+    const size_t bytes = (size_t)N * N * sizeof(double);
+    if (reset) {
+      SavScal z{};
+      SPFC_CK(cudaMemcpyAsync(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
+      drop_graphs();
+    }
+    SPFC_CK(cudaMemcpyAsync(real_, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
+    k_real_sum<<<gpw_, PW_THREADS, 0, st_>>>(real_, (size_t)N * N, partS_);
+    SPFC_CK(cudaGetLastError());
+    int rc = scalar_op(SO_ZM_SLOT, partS_, gpw_, nullptr, 0, slot_rel);
+    if (rc) return rc;
+    rc = launch_row(RW_IN_REAL); if (rc) return rc;
+    // slot index: p = 0 after a reset, so newest = 0 and previous = 1
+    rc = launch_col_fwd(CF_TO_STATE, slot_rel == 0 ? 0 : 1); if (rc) return rc;
+    k_put_zero_modes<R><<<1, 1, 0, st_>>>(S_, sc_);
+    SPFC_CK(cudaGetLastError());
+    SPFC_CK(cudaStreamSynchronize(st_));
+    return 0;
+  }
+
+  int launch_step_kernels() {
+    int rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
+    rc = launch_row(RW_NONLIN); if (rc) return rc;
+    return launch_col_fwd(CF_BDF2, 0);
+  }
+
+  void drop_graphs() {
+    if (g1_) { cudaGraphExecDestroy(g1_); g1_ = nullptr; }
+    if (g16_) { cudaGraphExecDestroy(g16_); g16_ = nullptr; }
+  }
+
+  int capture(int nsteps, cudaGraphExec_t* out) {
+    cudaStream_t keep = st_;
+    st_ = cap_st_;
+    cudaGraph_t g = nullptr;
+    SPFC_CK(cudaStreamBeginCapture(cap_st_, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int i = 0; i < nsteps && rc == 0; ++i) rc = launch_step_kernels();
+    cudaError_t e = cudaStreamEndCapture(cap_st_, &g);
+    st_ = keep;
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) { err = std::string("graph capture: ") + cudaGetErrorString(e); return 3; }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { err = std::string("graph instantiate: ") + cudaGetErrorString(e); return 3; }
+    return 0;
+  }
+
+  int ensure_graphs() {
+    if (!g1_) { int rc = capture(1, &g1_); if (rc) return rc; }
+    if (!g16_) { int rc = capture(16, &g16_); if (rc) return rc; }
+    return 0;
+  }
+
+  int ev(int* idx) {
+    if (evnext_ >= (int)evpool_.size()) {
+      cudaEvent_t e;
+      SPFC_CK(cudaEventCreate(&e));
+      evpool_.push_back(e);
+    }
+    *idx = evnext_++;
+    return 0;
+  }
+
+  int timed_step() {
+    int e0, e1, e2, e3, rc;
+    if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2)) || (rc = ev(&e3))) return rc;
+    SPFC_CK(cudaEventRecord(evpool_[e0], st_));
+    if ((rc = launch_col_inv(CI_STEP, 0))) return rc;
+    SPFC_CK(cudaEventRecord(evpool_[e1], st_));
+    if ((rc = launch_row(RW_NONLIN))) return rc;
+    SPFC_CK(cudaEventRecord(evpool_[e2], st_));
+    if ((rc = launch_col_fwd(CF_BDF2, 0))) return rc;
+    SPFC_CK(cudaEventRecord(evpool_[e3], st_));
+    trecs_.push_back({0, e0, e1});
+    trecs_.push_back({1, e1, e2});
+    trecs_.push_back({2, e2, e3});
+    return 0;
+  }
+
+  struct TRec { int cls, e0, e1; };
+
+  cudaStream_t st_ = nullptr, cap_st_ = nullptr;
+  Slots<R> S_{{nullptr, nullptr}};
+  C* Nhat_ = nullptr;
+  C* W_[2] = {nullptr, nullptr};
+  double* real_ = nullptr;
+  double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
+  SavScal* sc_ = nullptr;
+  unsigned* counter_ = nullptr;
+  C* tw_ = nullptr;
+  int gpw_ = 0, nE_ = 0, nG_ = 0;
+  size_t spec_bytes_ = 0, total_ = 0;
+  cudaGraphExec_t g1_ = nullptr, g16_ = nullptr;
+  bool timing_ = false;
+  std::vector<cudaEvent_t> evpool_;
+  int evnext_ = 0;
+  std::vector<TRec> trecs_;
+  int64_t tcount_[3] = {0, 0, 0};
+  double tms_[3] = {0, 0, 0};
+};
+
+template <typename R>
+SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
+  SolverBase* s = nullptr;
+  switch (P.N) {
+    case 16: s = new Solver2D<R, 16>(P, st); break;
+    case 32: s = new Solver2D<R, 32>(P, st); break;
+    case 64: s = new Solver2D<R, 64>(P, st); break;
+    case 128: s = new Solver2D<R, 128>(P, st); break;
+    case 256: s = new Solver2D<R, 256>(P, st); break;
+    case 512: s = new Solver2D<R, 512>(P, st); break;
+    default:
+      *status = 1;
+      *err = "2D grid size must be one of 16, 32, 64, 128, 256, 512";
+      return nullptr;
+  }
+  int rc = 0;
+  switch (P.N) {
+    case 16: rc = static_cast<Solver2D<R, 16>*>(s)->setup(); break;
+    case 32: rc = static_cast<Solver2D<R, 32>*>(s)->setup(); break;
+    case 64: rc = static_cast<Solver2D<R, 64>*>(s)->setup(); break;
+    case 128: rc = static_cast<Solver2D<R, 128>*>(s)->setup(); break;
+    case 256: rc = static_cast<Solver2D<R, 256>*>(s)->setup(); break;
+    case 512: rc = static_cast<Solver2D<R, 512>*>(s)->setup(); break;
+  }
+  if (rc) {
+    *status = rc;
+    *err = s->err;
+    delete s;
+    return nullptr;
+  }
+  return s;
+}
+
+}  // namespace spfc

@@ -1,0 +1,221 @@
+"""ctypes binding of ``libspfc.so`` (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts Python
+arguments (numpy arrays for host data, torch CUDA tensors for device data,
+torch streams) into the plain pointers and sizes of ``include/spfc.h``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from .build import LIB
+
+FP64, FP32_BULK = 0, 1
+START_BDF1, START_GHOST, START_COPY = 0, 1, 2
+_PREC = {"fp64": FP64, "f64": FP64, FP64: FP64, "fp32": FP32_BULK, "f32": FP32_BULK,
+         "fp32_bulk": FP32_BULK, FP32_BULK: FP32_BULK}
+_START = {"bdf1": START_BDF1, "ghost": START_GHOST, "copy": START_COPY,
+          START_BDF1: START_BDF1, START_GHOST: START_GHOST, START_COPY: START_COPY}
+
+_P = ct.c_void_p
+_D = ct.c_double
+_I = ct.c_int
+_DP = ct.POINTER(ct.c_double)
+
+# name -> (restype, argtypes), one entry per function of include/spfc.h
+_SIGS = {
+    "spfc_create": (_I, [_I, ct.POINTER(_I), _DP, _D, _D, _D, _I, _P, ct.POINTER(_P)]),
+    "spfc_init": (_I, [_P, _P, _I, _I]),
+    "spfc_set_state": (_I, [_P, _P, _P, _D, _D, _I]),
+    "spfc_step": (_I, [_P, ct.c_int64]),
+    "spfc_energy": (_I, [_P, _DP, _DP, _DP]),
+    "spfc_mass": (_I, [_P, _DP, _DP]),
+    "spfc_sav_scalars": (_I, [_P, _DP, _I]),
+    "spfc_get_field": (_I, [_P, _P, _I, _I]),
+    "spfc_dt_change": (_I, [_P, _D]),
+    "spfc_save": (_I, [_P, ct.c_char_p]),
+    "spfc_load": (_I, [_P, ct.c_char_p]),
+    "spfc_sync": (_I, [_P]),
+    "spfc_set_timing": (_I, [_P, _I]),
+    "spfc_kernel_times": (_I, [_P, _I, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_int64), _DP]),
+    "spfc_device_bytes": (ct.c_int64, [_P]),
+    "spfc_destroy": (None, [_P]),
+    "spfc_last_error": (ct.c_char_p, [_P]),
+}
+EXPORTED_SYMBOLS = tuple(_SIGS)
+
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load_library(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_2012_15133_gb300.build.build(); "
+                           "the solver has no CPU fallback")
+    lib = ct.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class SPFCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"spfc error {code}: {msg}")
+        self.code = code
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _current_stream_ptr():
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """One SPFC run on the current CUDA device (see include/spfc.h).
+
+    Host arrays are numpy float64 arrays of shape (N,)*d (x fastest = last
+    axis); device arrays are contiguous float64 torch CUDA tensors.
+    """
+
+    def __init__(self, d, n, L, eps, beta, dt, precision="fp64", stream=None):
+        self._lib = load_library()
+        self.d = int(d)
+        n = [int(n)] * self.d if np.isscalar(n) else [int(v) for v in n]
+        L = [float(L)] * self.d if np.isscalar(L) else [float(v) for v in L]
+        self.n, self.L = n, L
+        self.shape = tuple(reversed(n))
+        self.precision = _PREC[precision]
+        if stream is None:
+            sp = _current_stream_ptr()
+        elif isinstance(stream, int):
+            sp = ct.c_void_p(stream)
+        else:
+            sp = ct.c_void_p(stream.cuda_stream)
+        self._stream = sp
+        h = ct.c_void_p()
+        rc = self._lib.spfc_create(self.d, (ct.c_int * self.d)(*n), (ct.c_double * self.d)(*L),
+                                   float(eps), float(beta), float(dt), self.precision, sp,
+                                   ct.byref(h))
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_last_error(None).decode())
+        self._h = h
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_last_error(self._h).decode())
+
+    def _field_arg(self, a):
+        """Return (pointer, on_device, keepalive) for an input field."""
+        if _is_torch(a):
+            import torch
+            if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+                raise ValueError("device fields must be contiguous float64 CUDA tensors")
+            if tuple(a.shape) != self.shape and a.numel() != int(np.prod(self.shape)):
+                raise ValueError("field has the wrong size")
+            return ct.c_void_p(a.data_ptr()), 1, a
+        arr = np.ascontiguousarray(a, dtype=np.float64)
+        if arr.size != int(np.prod(self.shape)):
+            raise ValueError("field has the wrong size")
+        return arr.ctypes.data_as(ct.c_void_p), 0, arr
+
+    # -- API -------------------------------------------------------------------
+    def init(self, phi0, mode="bdf1"):
+        ptr, dev, keep = self._field_arg(phi0)
+        self._check(self._lib.spfc_init(self._h, ptr, dev, _START[mode]))
+        return self
+
+    def set_state(self, phi, phi_prev, r, r_prev):
+        p1, d1, k1 = self._field_arg(phi)
+        p2, d2, k2 = self._field_arg(phi_prev)
+        if d1 != d2:
+            raise ValueError("both fields must be on the host or both on the device")
+        self._check(self._lib.spfc_set_state(self._h, p1, p2, float(r), float(r_prev), d1))
+        return self
+
+    def step(self, nsteps=1):
+        self._check(self._lib.spfc_step(self._h, int(nsteps)))
+        return self
+
+    def energy(self):
+        """(E_orig, E_mod, E_breve)"""
+        a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
+        self._check(self._lib.spfc_energy(self._h, ct.byref(a), ct.byref(b), ct.byref(c)))
+        return a.value, b.value, c.value
+
+    def mass(self):
+        """(mass, mean)"""
+        a, b = ct.c_double(), ct.c_double()
+        self._check(self._lib.spfc_mass(self._h, ct.byref(a), ct.byref(b)))
+        return a.value, b.value
+
+    def sav_scalars(self):
+        out = (ct.c_double * 6)()
+        self._check(self._lib.spfc_sav_scalars(self._h, out, 6))
+        keys = ("r", "r_prev", "xi", "gamma", "E1", "nsteps")
+        return dict(zip(keys, list(out)))
+
+    def get_field(self, which=0, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev, keep = self._field_arg(out)
+        self._check(self._lib.spfc_get_field(self._h, ptr, dev, int(which)))
+        return out
+
+    def dt_change(self, dt):
+        self._check(self._lib.spfc_dt_change(self._h, float(dt)))
+        return self
+
+    def save(self, path):
+        self._check(self._lib.spfc_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        self._check(self._lib.spfc_load(self._h, os.fsencode(path)))
+        return self
+
+    def sync(self):
+        self._check(self._lib.spfc_sync(self._h))
+
+    def set_timing(self, on=True):
+        self._check(self._lib.spfc_set_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        names = (ct.c_char_p * 16)()
+        launches = (ct.c_int64 * 16)()
+        ms = (ct.c_double * 16)()
+        n = self._lib.spfc_kernel_times(self._h, 16, names, launches, ms)
+        if n < 0:
+            self._check(n)
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+    def device_bytes(self):
+        return int(self._lib.spfc_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.spfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
