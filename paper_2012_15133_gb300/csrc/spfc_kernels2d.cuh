@@ -43,13 +43,46 @@ enum ColInvMode : int { CI_STEP = 0, CI_GRAD = 1, CI_FIELD = 2 };
 enum RowMode : int { RW_NONLIN = 0, RW_ENERGY = 1, RW_OUT_REAL = 2, RW_IN_REAL = 3 };
 enum ColFwdMode : int { CF_BDF2 = 0, CF_BDF1 = 1, CF_NHAT = 2, CF_TO_STATE = 3 };
 
+// Explicitly rounded arithmetic for the spectral symbols and the update, so
+// that every kernel that evaluates them (the lazy update in the column pass,
+// the explicit finalize) produces bit-identical results regardless of how the
+// compiler would contract multiply-adds.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// |k|^2 (full wave numbers, Nyquist included) of half-spectrum index (kx, ky).
+template <typename R>
+__device__ __forceinline__ R sym_K2(int kx, int ky, const Params& P) {
+  const R kxx = rn_mul((R)kx, (R)P.kf[0]);
+  const R kyy = (R)kfull(ky, P.N, P.kf[1]);
+  return rn_fma(kxx, kxx, rn_mul(kyy, kyy));
+}
+
+// 1 / (c0 + dt |k|^2 (a + |k|^4)): inverse symbol of A_N (c0 = 3/2, eq. solver-1)
+// or of the first-order operator (c0 = 1).
+template <typename R>
+__device__ __forceinline__ R sym_invA(R K2, R c0, const Params& P) {
+  const R A = rn_fma((R)P.dt, rn_mul(K2, rn_fma(K2, K2, (R)P.a)), c0);
+  return (R)1 / A;
+}
+
 // BDF2 update of one spectral coefficient (eq. solver-6 in the form
 // phi^{n+1} = (dt r^{n+1}/sqrt(E1)) A^{-1} Delta N + A^{-1}(2 phi^n - phi^{n-1}/2)).
 template <typename C, typename R>
 __device__ __forceinline__ C bdf2_update(C cur, C old, C nh, R K2, R invA, R alpha) {
-  const R bfac = -alpha * K2 * invA;
-  return mk<C>(bfac * nh.x + ((R)2 * cur.x - (R)0.5 * old.x) * invA,
-               bfac * nh.y + ((R)2 * cur.y - (R)0.5 * old.y) * invA);
+  const R bfac = rn_mul(rn_mul(-alpha, K2), invA);
+  const R vx = rn_fma((R)2, cur.x, rn_mul((R)-0.5, old.x));
+  const R vy = rn_fma((R)2, cur.y, rn_mul((R)-0.5, old.y));
+  return mk<C>(rn_fma(bfac, nh.x, rn_mul(vx, invA)), rn_fma(bfac, nh.y, rn_mul(vy, invA)));
+}
+
+// First-order (BDF1 start) update: phi^1 = alpha A1^{-1} Delta N + A1^{-1} phi^0.
+template <typename C, typename R>
+__device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha) {
+  const R bfac = rn_mul(rn_mul(-alpha, K2), invA);
+  return mk<C>(rn_fma(bfac, nh.x, rn_mul(cur.x, invA)), rn_fma(bfac, nh.y, rn_mul(cur.y, invA)));
 }
 
 // ---------------------------------------------------------------------------
@@ -83,8 +116,6 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
     src_new = S.at(which == 0 ? p : 1 - p);
     src_old = src_new;
   }
-  const R kfx = (R)P.kf[0], kfy = (R)P.kf[1];
-
   for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
     const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
     C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
@@ -96,16 +127,14 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
         C cur = src_new[off], old = src_old[off];
         C nw = cur;
         if (pending) {
-          const R kxx = (R)kx * kfx, kyy = (R)kfull(ky, N, P.kf[1]);
-          const R K2 = kxx * kxx + kyy * kyy;
           if (off == 0) {
             // zero mode: c_0 = phi_0^n + (phi_0^n - phi_0^{n-1})/3 (A_0 = 3/2, Delta kills N)
             const double z = sc->zm[p] + (sc->zm[p] - sc->zm[1 - p]) / 3.0;
             sc->zm[1 - p] = z;
             nw = mk<C>((R)z, (R)0);
           } else {
-            const R A = (R)1.5 + (R)P.dt * K2 * ((R)P.a + K2 * K2);
-            nw = bdf2_update<C, R>(cur, old, Nhat[off], K2, (R)1 / A, alpha);
+            const R K2 = sym_K2<R>(kx, ky, P);
+            nw = bdf2_update<C, R>(cur, old, Nhat[off], K2, sym_invA<R>(K2, (R)1.5, P), alpha);
           }
           src_old[off] = nw;  // phi^{n+1} overwrites phi^{n-1}
           old = cur;
@@ -324,9 +353,8 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
     const C nh = mk<C>(uy, -ux);
     Nhat[off] = nh;
     if (MODE == CF_NHAT) continue;
-    const R kxx = (R)kx * (R)P.kf[0], kyy = (R)kfull(ky, N, P.kf[1]);
-    const R K2 = kxx * kxx + kyy * kyy;
-    const R invA = (R)1 / (c0 + (R)P.dt * K2 * ((R)P.a + K2 * K2));
+    const R K2 = sym_K2<R>(kx, ky, P);
+    const R invA = sym_invA<R>(K2, c0, P);
     C v;
     if (MODE == CF_BDF1) {
       v = snew[off];
@@ -386,17 +414,13 @@ __global__ void k2d_finalize(const Params P, Slots<R> S, const C_t<R>* __restric
       old[0] = mk<C>((R)z, (R)0);
       continue;
     }
-    const R kxx = (R)kx * (R)P.kf[0], kyy = (R)kfull(ky, N, P.kf[1]);
-    const R K2 = kxx * kxx + kyy * kyy;
+    const R K2 = sym_K2<R>(kx, ky, P);
     const C cu = cur[off], nh = Nhat[off];
     C nw;
     if (bdf1) {
-      const R invA = (R)1 / ((R)1 + (R)P.dt * K2 * ((R)P.a + K2 * K2));
-      const R bfac = -alpha * K2 * invA;
-      nw = mk<C>(bfac * nh.x + cu.x * invA, bfac * nh.y + cu.y * invA);
+      nw = bdf1_update<C, R>(cu, nh, K2, sym_invA<R>(K2, (R)1, P), alpha);
     } else {
-      const R invA = (R)1 / ((R)1.5 + (R)P.dt * K2 * ((R)P.a + K2 * K2));
-      nw = bdf2_update<C, R>(cu, old[off], nh, K2, invA, alpha);
+      nw = bdf2_update<C, R>(cu, old[off], nh, K2, sym_invA<R>(K2, (R)1.5, P), alpha);
     }
     old[off] = nw;
   }
@@ -414,8 +438,7 @@ __global__ void k2d_ghost(const Params P, Slots<R> S, const C_t<R>* __restrict__
   for (size_t off = blockIdx.x * (size_t)blockDim.x + threadIdx.x; off < total;
        off += (size_t)gridDim.x * blockDim.x) {
     const int ky = (int)(off / NH), kx = (int)(off % NH);
-    const R kxx = (R)kx * (R)P.kf[0], kyy = (R)kfull(ky, N, P.kf[1]);
-    const R K2 = kxx * kxx + kyy * kyy;
+    const R K2 = sym_K2<R>(kx, ky, P);
     const C cu = cur[off], nh = Nhat[off];
     const R L = (R)P.a + K2 * K2;
     const R f = (R)P.dt * K2;
