@@ -60,6 +60,7 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
   P.beta = beta;
   P.C = 1.0 + 1.0 / beta;
   P.dt = dt;
+  spfc::fill_float_params(&P);
   int status = 0;
   std::string err;
   SolverBase* s = (precision == SPFC_FP64)

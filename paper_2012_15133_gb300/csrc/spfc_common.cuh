@@ -85,22 +85,36 @@ template <typename C, int RAD, bool INV> __device__ __forceinline__ void dft_r(C
 // Largest twiddle table length; table[m] = exp(-2 pi i m / TW_N).
 constexpr int TW_N = 512;
 
-// Lanes per sequence for a length-N FFT: every lane owns N/T values (8 or 16).
-template <int N> struct fft_shape {
-  static constexpr int T = (N / 8 < 32) ? N / 8 : 32;
-  static constexpr int E = N / T;
-  static_assert(N >= 16 && N <= 512 && (N & (N - 1)) == 0, "FFT length must be a power of two in [16,512]");
-  static_assert(32 % T == 0, "a sequence must not straddle warps");
+// Shared-memory position of element i of an FFT sequence: one pad slot every
+// 8 elements spreads the strided writes of the first radix-8 stage over the
+// banks. A sequence of length N occupies sp_len(N) slots.
+__device__ __forceinline__ constexpr int sp(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int sp_len(int n) { return n + n / 8; }
+
+
+// A length-N FFT is done by T = N/E lanes, each owning E values per stage.
+// T <= 32: the lanes of a sequence sit in one warp (__syncwarp between
+// stages); T > 32: the sequence spans warps and every thread of the block
+// takes part in the same FFT call (__syncthreads between stages).
+template <int N, int E> struct fft_shape {
+  static constexpr int T = N / E;
+  static_assert(N >= 16 && N <= TW_N && (N & (N - 1)) == 0, "FFT length must be a power of two in [16,512]");
+  static_assert(E == 4 || E == 8 || E == 16, "4, 8 or 16 values per lane");
+  static_assert(T >= 1 && (T <= 32 ? 32 % T == 0 : T % 32 == 0), "a sequence must not straddle warps unevenly");
 };
+
+template <int N, int E> __device__ __forceinline__ void fft_sync() {
+  if constexpr (N / E <= 32) __syncwarp(); else __syncthreads();
+}
 
 // One Stockham stage of radix RAD (Govindaraju et al., SC'08 formulation):
 // butterfly j reads x[j + r N/RAD], twiddles by w^(r (j mod NS) N/(NS RAD)),
 // transforms, and writes x[(j/NS) NS RAD + (j mod NS) + r NS]. All lanes of a
-// sequence hold their inputs in registers across a __syncwarp, so the stage
+// sequence hold their inputs in registers across a barrier, so the stage
 // runs in place.
-template <typename C, int N, bool INV, int NS, int RAD>
+template <typename C, int N, int E, bool INV, int NS, int RAD>
 __device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* __restrict__ tw) {
-  constexpr int T = fft_shape<N>::T, E = fft_shape<N>::E;
+  constexpr int T = fft_shape<N, E>::T;
   constexpr int NB = E / RAD;
   constexpr int STRIDE = N / RAD;
   constexpr int TWS = TW_N / (NS * RAD);
@@ -109,9 +123,9 @@ __device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* 
   for (int m = 0; m < NB; ++m) {
     const int j = lane + m * T;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[(j + r * STRIDE) * es];
+    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sp(j + r * STRIDE) * es];
   }
-  __syncwarp();
+  fft_sync<N, E>();
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
     const int j = lane + m * T;
@@ -119,7 +133,7 @@ __device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* 
     if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = tw[r * k * TWS];
+        C w = __ldg(tw + r * k * TWS);
         if (INV) w.y = -w.y;
         v[m * RAD + r] = cmul(v[m * RAD + r], w);
       }
@@ -127,34 +141,43 @@ __device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* 
     dft_r<C, RAD, INV>(v + m * RAD);
     const int base = (j - k) * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) s[(base + r * NS) * es] = v[m * RAD + r];
+    for (int r = 0; r < RAD; ++r) s[sp(base + r * NS) * es] = v[m * RAD + r];
   }
-  __syncwarp();
+  fft_sync<N, E>();
 }
 
-template <typename C, int N, bool INV, int NS>
+template <typename C, int N, int E, bool INV, int NS>
 __device__ __forceinline__ void fft_stages(C* s, int es, int lane, const C* __restrict__ tw) {
   if constexpr (NS < N) {
-    constexpr int E = fft_shape<N>::E;
     constexpr int REM = N / NS;
     constexpr int RAD = (REM % 8 == 0 && E % 8 == 0) ? 8 : ((REM % 4 == 0 && E % 4 == 0) ? 4 : 2);
-    stockham_stage<C, N, INV, NS, RAD>(s, es, lane, tw);
-    fft_stages<C, N, INV, NS * RAD>(s, es, lane, tw);
+    stockham_stage<C, N, E, INV, NS, RAD>(s, es, lane, tw);
+    fft_stages<C, N, E, INV, NS * RAD>(s, es, lane, tw);
   }
 }
 
-// Unnormalised complex DFT of the length-N sequence s[0], s[es], .., s[(N-1) es]
-// in shared memory, in place, by the T lanes (lane = 0..T-1) of one warp
-// sub-group. Forward: exp(-2 pi i k j / N); INV: exp(+2 pi i k j / N).
-// Every lane of the warp must call it (it synchronises with __syncwarp).
-template <typename C, int N, bool INV>
+// Unnormalised complex DFT of the length-N sequence whose element i is at
+// s[sp(i) * es] in shared memory, in place, by the T = N/E lanes (lane = 0..T-1) of one
+// sequence. Forward: exp(-2 pi i k j / N); INV: exp(+2 pi i k j / N).
+// The caller has made the input visible (block or warp barrier as fft_sync);
+// on return the output is visible to the sequence's lanes.
+template <typename C, int N, int E, bool INV>
 __device__ __forceinline__ void fft_smem(C* s, int es, int lane, const C* __restrict__ tw) {
-  __syncwarp();
-  fft_stages<C, N, INV, 1>(s, es, lane, tw);
+  fft_stages<C, N, E, INV, 1>(s, es, lane, tw);
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic FP64 reductions
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor is still running; pdl_wait()
+// blocks until the predecessor grid has completed and its memory is visible,
+// pdl_trigger() lets the successor grid be scheduled. Both are no-ops for a
+// normal launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -183,8 +206,169 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
 // other blocks of the same grid (before a fence) are seen.
 __device__ __forceinline__ double warp_sum_array(const double* a, int n, int lane) {
   double t = 0.0;
-  for (int i = lane; i < n; i += 32) t += __ldcg(a + i);
+  for (int base = 0; base < n; base += 256) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + lane + 32 * u;
+      v[u] = (i < n) ? __ldcg(a + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += v[u];
+  }
   return warp_sum(t);
+}
+
+// Accumulators of the SAV inner products and of E_1.
+// float64 path: plain float64 sums.
+// float32-bulk path: float-float sums (hi + lo, Knuth's two-sum on every
+// addition), which carry the exact sum of the float32 products to ~2^-48
+// relative, i.e. what a float64 accumulator of those products gives, while
+// running on the float32 pipes (float64 issue is scarce on this GPU).
+template <typename R> struct Red;
+
+template <> struct Red<double> {
+  using acc = double;
+  using store = double;
+  __device__ static acc zero() { return 0.0; }
+  __device__ static acc add(acc a, double x) { return a + x; }
+  __device__ static acc add2(acc a, acc b) { return a + b; }
+  __device__ static acc shfl(acc a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  __device__ static double to_double(acc a) { return a; }
+};
+
+template <> struct Red<float> {
+  using acc = float2;   // (hi, lo)
+  using store = float2;
+  __device__ static acc zero() { return make_float2(0.f, 0.f); }
+  __device__ static acc add(acc a, float x) {
+    const float s = __fadd_rn(a.x, x);
+    const float bb = __fsub_rn(s, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    return make_float2(s, __fadd_rn(a.y, err));
+  }
+  __device__ static acc add2(acc a, acc b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    const float lo = __fadd_rn(__fadd_rn(a.y, b.y), err);
+    // renormalise (fast two-sum)
+    const float h = __fadd_rn(s, lo);
+    return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
+  }
+  __device__ static acc shfl(acc a, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+  }
+  __device__ static double to_double(acc a) { return (double)a.x + (double)a.y; }
+};
+
+template <typename R> __device__ __forceinline__ typename Red<R>::acc warp_red(typename Red<R>::acc v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = Red<R>::add2(v, Red<R>::shfl(v, o));
+  return v;
+}
+
+// Block reduction of accumulators (fixed order); result valid in thread 0.
+template <typename R>
+__device__ __forceinline__ typename Red<R>::acc block_red(typename Red<R>::acc v, typename Red<R>::acc* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_red<R>(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  typename Red<R>::acc t = Red<R>::zero();
+  if (wid == 0) {
+    t = (lane < nw) ? scratch[lane] : Red<R>::zero();
+    t = warp_red<R>(t);
+  }
+  return t;
+}
+
+// Sum of n stored accumulators by one warp, fixed order; returned as double
+// to every lane. L1 is bypassed (values written by other blocks).
+template <typename R>
+__device__ __forceinline__ double warp_red_array(const typename Red<R>::store* a, int n, int lane) {
+  using ST = typename Red<R>::store;
+  typename Red<R>::acc t = Red<R>::zero();
+  // batches of 8 independent loads per lane, so that the L2 round trips overlap
+  for (int base = 0; base < n; base += 256) {
+    ST v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + lane + 32 * u;
+      v[u] = (i < n) ? __ldcg(a + i) : Red<R>::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t = Red<R>::add2(t, v[u]);
+  }
+  return Red<R>::to_double(warp_red<R>(t));
+}
+
+// Grid-level reduction of NQ partial-sum arrays by a whole block, all NQ
+// chains interleaved: thread t sums entries t, t + blockDim, .. of each array
+// (L1 bypassed: the entries were written by other blocks of the grid), then a
+// shuffle tree and a shared-memory tree. Fixed order; results in thread 0.
+template <typename R, int NQ>
+__device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* const* arr, const int* n,
+                                                 typename Red<R>::acc* out,
+                                                 typename Red<R>::acc (*scratch)[32]) {
+  using RD = Red<R>;
+  typename RD::acc a[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) a[q] = RD::zero();
+  int nmax = 0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) nmax = n[q] > nmax ? n[q] : nmax;
+  for (int base = 0; base < nmax; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    typename RD::store v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = (i < n[q]) ? __ldcg(arr[q] + i) : RD::zero();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], v[q]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], RD::shfl(a[q], o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) scratch[q][wid] = a[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] = (lane < nw) ? scratch[q][lane] : RD::zero();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], RD::shfl(a[q], o));
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) out[q] = a[q];
+    }
+  }
+}
+
+// Sum of n stored float-float accumulators by one warp, fixed order, kept in
+// float-float (every lane gets the result).
+__device__ __forceinline__ float2 warp_red_array_ff(const float2* a, int n, int lane) {
+  float2 t = Red<float>::zero();
+  for (int base = 0; base < n; base += 256) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + lane + 32 * u;
+      v[u] = (i < n) ? __ldcg(a + i) : Red<float>::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t = Red<float>::add2(t, v[u]);
+  }
+  return warp_red<float>(t);
 }
 
 }  // namespace spfc

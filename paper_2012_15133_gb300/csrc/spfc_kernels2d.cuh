@@ -19,19 +19,37 @@
 #pragma once
 
 #include "spfc_common.cuh"
+#include "spfc_ff.cuh"
 #include "spfc_state.h"
 
 namespace spfc {
 
 // wave numbers --------------------------------------------------------------
 // index i in [0,N) in DFT order; Nyquist (i = N/2) keeps its full |k| in the
-// Laplacian but has first-derivative symbol 0.
-__device__ __forceinline__ double kfull(int i, int N, double kf) {
-  return (double)((i <= N / 2) ? i : i - N) * kf;
+// Laplacian but has first-derivative symbol 0. Evaluated in the working
+// precision R (no float64 arithmetic per element on the float32 path).
+template <typename R> __device__ __forceinline__ R kfull(int i, int N, R kf) {
+  return (R)((i <= N / 2) ? i : i - N) * kf;
 }
-__device__ __forceinline__ double kderiv(int i, int N, double kf) {
-  return (i == N / 2) ? 0.0 : (double)((i < N / 2) ? i : i - N) * kf;
+template <typename R> __device__ __forceinline__ R kderiv(int i, int N, R kf) {
+  return (i == N / 2) ? (R)0 : (R)((i < N / 2) ? i : i - N) * kf;
 }
+
+// Per-run constants in the working precision (read, never converted, per thread).
+template <typename R> struct PC;
+template <> struct PC<double> {
+  double kfx, kfy, kfz, dt, a, beta, invP;
+  __device__ __forceinline__ explicit PC(const Params& P)
+      : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP) {}
+};
+template <> struct PC<float> {
+  float kfx, kfy, kfz, dt, a, beta, invP;
+  __device__ __forceinline__ explicit PC(const Params& P)
+      : kfx(P.kf_f[0]), kfy(P.kf_f[1]), kfz(P.kf_f[2]), dt(P.dt_f), a(P.a_f), beta(P.beta_f), invP(P.invP_f) {}
+};
+template <typename R> __device__ __forceinline__ R read_alpha(const SavScal* sc);
+template <> __device__ __forceinline__ double read_alpha<double>(const SavScal* sc) { return sc->alpha; }
+template <> __device__ __forceinline__ float read_alpha<float>(const SavScal* sc) { return sc->alpha_f; }
 
 template <typename R> struct Slots {
   C_t<R>* s[2];
@@ -54,18 +72,25 @@ __device__ __forceinline__ double rn_fma(double a, double b, double c) { return 
 
 // |k|^2 (full wave numbers, Nyquist included) of half-spectrum index (kx, ky).
 template <typename R>
-__device__ __forceinline__ R sym_K2(int kx, int ky, const Params& P) {
-  const R kxx = rn_mul((R)kx, (R)P.kf[0]);
-  const R kyy = (R)kfull(ky, P.N, P.kf[1]);
+__device__ __forceinline__ R sym_K2(int kx, int ky, int N, const PC<R>& c) {
+  const R kxx = rn_mul((R)kx, c.kfx);
+  const R kyy = rn_mul((R)((ky <= N / 2) ? ky : ky - N), c.kfy);
   return rn_fma(kxx, kxx, rn_mul(kyy, kyy));
 }
 
 // 1 / (c0 + dt |k|^2 (a + |k|^4)): inverse symbol of A_N (c0 = 3/2, eq. solver-1)
 // or of the first-order operator (c0 = 1).
 template <typename R>
-__device__ __forceinline__ R sym_invA(R K2, R c0, const Params& P) {
-  const R A = rn_fma((R)P.dt, rn_mul(K2, rn_fma(K2, K2, (R)P.a)), c0);
+__device__ __forceinline__ R sym_invA(R K2, R c0, const PC<R>& c) {
+  const R A = rn_fma(c.dt, rn_mul(K2, rn_fma(K2, K2, c.a)), c0);
   return (R)1 / A;
+}
+
+// Zero mode of the BDF2 update: A_0 = 3/2 and Delta_N N has no mean, so
+// c_0 = (2 a - b/2) / (3/2) = a + (a - b)/3, written so that a == b gives a
+// exactly (mass conservation, Theorem SPFC solvability).
+__device__ __forceinline__ double zero_mode_update(double a, double b) {
+  return a + (a - b) * (1.0 / 3.0);
 }
 
 // BDF2 update of one spectral coefficient (eq. solver-6 in the form
@@ -86,26 +111,32 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha) {
 }
 
 // ---------------------------------------------------------------------------
-// Column inverse pass. Grid: ceil(NH/CT) blocks, each a tile of CT kx columns.
+// Column inverse pass. Grid: ceil(NH/CT) blocks, each a tile of CT kx columns;
+// NF * CT sequences of length N, T = N/E lanes each.
 // ---------------------------------------------------------------------------
-template <typename R, int N, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CI_FIELD ? 1 : 2) * CT * fft_shape<N>::T)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == CI_FIELD ? 1 : 2) * CT * (N / E))
 k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
             C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
   using C = C_t<R>;
-  constexpr int T = fft_shape<N>::T;
+  constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
   constexpr int NTH = NF * CT * T;
   constexpr int CTP = CT + 1;
   constexpr int NH = N / 2 + 1;
-  static_assert(NTH % 32 == 0, "tile must fill whole warps");
+  constexpr int IT = N * CT / NTH;  // elements per thread in the tile phases
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
 
+  pdl_wait();
+  pdl_trigger();
   if (sc->status != DEV_OK) return;
+  const PC<R> pc(P);
   const int p = sc->p;
   const int pending = (MODE == CI_STEP) ? sc->pending : 0;
-  const R alpha = (R)sc->alpha;
+  const R alpha = read_alpha<R>(sc);
   const int kx0 = blockIdx.x * CT;
   C* src_new;
   C* src_old;
@@ -116,132 +147,191 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
     src_new = S.at(which == 0 ? p : 1 - p);
     src_old = src_new;
   }
-  for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
+
+  // gather the tile (all loads first), then the pointwise spectral work
+  C vcur[IT], vold[IT], vnh[IT];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int ky = idx / CT, kx = kx0 + idx % CT;
+    if (kx < NH) {
+      const size_t off = (size_t)ky * NH + kx;
+      vcur[it] = src_new[off];
+      if (MODE == CI_STEP) {
+        vold[it] = src_old[off];
+        if (pending) vnh[it] = Nhat[off];
+      }
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
     const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
     C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
     if (kx < NH) {
       const size_t off = (size_t)ky * NH + kx;
-      const R ktx = (R)kderiv(kx, N, P.kf[0]), kty = (R)kderiv(ky, N, P.kf[1]);
-      C ph;
+      C ph = vcur[it];
       if (MODE == CI_STEP) {
-        C cur = src_new[off], old = src_old[off];
+        const C cur = vcur[it];
+        C old = vold[it];
         C nw = cur;
         if (pending) {
           if (off == 0) {
             // zero mode: c_0 = phi_0^n + (phi_0^n - phi_0^{n-1})/3 (A_0 = 3/2, Delta kills N)
-            const double z = sc->zm[p] + (sc->zm[p] - sc->zm[1 - p]) / 3.0;
+            const double z = zero_mode_update(sc->zm[p], sc->zm[1 - p]);
             sc->zm[1 - p] = z;
             nw = mk<C>((R)z, (R)0);
           } else {
-            const R K2 = sym_K2<R>(kx, ky, P);
-            nw = bdf2_update<C, R>(cur, old, Nhat[off], K2, sym_invA<R>(K2, (R)1.5, P), alpha);
+            const R K2 = sym_K2<R>(kx, ky, N, pc);
+            nw = bdf2_update<C, R>(cur, old, vnh[it], K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
           }
           src_old[off] = nw;  // phi^{n+1} overwrites phi^{n-1}
           old = cur;
         }
         ph = mk<C>((R)2 * nw.x - old.x, (R)2 * nw.y - old.y);  // phi* = 2 phi^{n+1} - phi^n
-      } else {
-        ph = src_new[off];
       }
       if (MODE == CI_FIELD) {
         g0 = ph;
       } else {
+        const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
         g0 = mk<C>(-ktx * ph.y, ktx * ph.x);  // i k~_x phi
         g1 = mk<C>(-kty * ph.y, kty * ph.x);  // i k~_y phi
       }
     }
-    sm[ky * CTP + c] = g0;
-    if (NF == 2) sm[N * CTP + ky * CTP + c] = g1;
+    sm[sp(ky) * CTP + c] = g0;
+    if (NF == 2) sm[SEQ * CTP + sp(ky) * CTP + c] = g1;
   }
   __syncthreads();
   {
     const int q = threadIdx.x / T, lane = threadIdx.x % T;
     const int f = q / CT, c = q % CT;
-    fft_smem<C, N, true>(sm + f * N * CTP + c, CTP, lane, tw);
+    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
     const int y = idx / CT, c = idx % CT, kx = kx0 + c;
     if (kx < NH) {
-      W0[(size_t)y * NH + kx] = sm[y * CTP + c];
-      if (NF == 2) W1[(size_t)y * NH + kx] = sm[N * CTP + y * CTP + c];
+      W0[(size_t)y * NH + kx] = sm[sp(y) * CTP + c];
+      if (NF == 2) W1[(size_t)y * NH + kx] = sm[SEQ * CTP + sp(y) * CTP + c];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Row pass. Grid: N/RPC blocks, RPC rows each, T lanes per row.
+// Row pass. Grid: N/RPC blocks, RPC rows each, T = N/E lanes per row.
 // part: 2 x gridDim.x doubles: sum s^2 and sum s per block (without h^d).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int RPC, int MODE>
-__global__ void __launch_bounds__(RPC * fft_shape<N>::T)
+template <typename R, int N, int E, int RPC, int MODE>
+__global__ void __launch_bounds__(RPC * (N / E))
 k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double* __restrict__ part,
         const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
   using C = C_t<R>;
-  constexpr int T = fft_shape<N>::T;
+  constexpr int T = fft_shape<N, E>::T;
   constexpr int NTH = RPC * T;
   constexpr int NH = N / 2 + 1;
-  static_assert(NTH % 32 == 0, "rows must fill whole warps");
+  constexpr int KH = (N / 2) / T;  // half-spectrum entries per lane, Nyquist aside
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0 && KH * T == N / 2, "rows must fill whole warps");
+  using RD = Red<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ double red[32];
+  __shared__ typename RD::acc red[32];
 
+  pdl_wait();
+  pdl_trigger();
   if (sc->status != DEV_OK) return;
   const int rloc = threadIdx.x / T, lane = threadIdx.x % T;
   const int row = blockIdx.x * RPC + rloc;
-  C* z = sm + rloc * (N + 1);
+  C* z = sm + rloc * (SEQ + 1);
   const size_t roff = (size_t)row * NH;
 
   if constexpr (MODE == RW_IN_REAL) {
-    for (int x = lane; x < N; x += T) z[x] = mk<C>((R)real_io[(size_t)row * N + x], (R)0);
-    fft_smem<C, N, false>(z, 1, lane, tw);
-    const R sc1 = (R)(1.0 / P.P);
-    for (int k = lane; k < NH; k += T) W0[roff + k] = cscale(z[k], sc1);
+    double v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = real_io[(size_t)row * N + lane + i * T];
+#pragma unroll
+    for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = mk<C>((R)v[i], (R)0);
+    __syncthreads();
+    fft_smem<C, N, E, false>(z, 1, lane, tw);
+    const R sc1 = PC<R>(P).invP;
+#pragma unroll
+    for (int i = 0; i < KH; ++i) W0[roff + lane + i * T] = cscale(z[sp(lane + i * T)], sc1);
+    if (lane == 0) W0[roff + N / 2] = cscale(z[sp(N / 2)], sc1);
   } else if constexpr (MODE == RW_OUT_REAL) {
-    for (int k = lane; k < NH; k += T) {
-      const C a = W0[roff + k];
-      z[k] = a;
-      if (k > 0 && k < N / 2) z[N - k] = cconj(a);
+    C a[KH];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) a[i] = W0[roff + lane + i * T];
+    const C ny = W0[roff + N / 2];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      const int k = lane + i * T;
+      z[sp(k)] = a[i];
+      if (k > 0) z[sp(N - k)] = cconj(a[i]);
     }
-    fft_smem<C, N, true>(z, 1, lane, tw);
-    for (int x = lane; x < N; x += T) real_io[(size_t)row * N + x] = (double)z[x].x;
+    if (lane == 0) z[sp(N / 2)] = ny;
+    __syncthreads();
+    fft_smem<C, N, E, true>(z, 1, lane, tw);
+#pragma unroll
+    for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
   } else {
-  // pack Z = G_x + i G_y over the full x-spectrum (Hermitian extension)
-  for (int k = lane; k < NH; k += T) {
-    const C a = W0[roff + k], b = W1[roff + k];
-    z[k] = mk<C>(a.x - b.y, a.y + b.x);
-    if (k > 0 && k < N / 2) z[N - k] = mk<C>(a.x + b.y, b.x - a.y);
-  }
-  fft_smem<C, N, true>(z, 1, lane, tw);
-  // pointwise: s = g_x^2 + g_y^2, partial sums, w = (beta s - 2) g
-  R acc2 = 0, acc1 = 0;
-  const R beta = (R)P.beta;
-  for (int x = lane; x < N; x += T) {
-    const C g = z[x];
-    const R s = g.x * g.x + g.y * g.y;
-    acc2 += s * s;
-    acc1 += s;
-    if (MODE == RW_NONLIN) {
-      const R fac = beta * s - (R)2;
-      z[x] = mk<C>(fac * g.x, fac * g.y);
+    // pack Z = G_x + i G_y over the full x-spectrum (Hermitian extension)
+    C a[KH], b[KH];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      a[i] = W0[roff + lane + i * T];
+      b[i] = W1[roff + lane + i * T];
     }
-  }
-  if (MODE == RW_NONLIN) {
-    fft_smem<C, N, false>(z, 1, lane, tw);
-    const R half = (R)(0.5 / P.P);
-    for (int k = lane; k < NH; k += T) {
-      const C zk = z[k], zm = cconj(z[(N - k) & (N - 1)]);
-      const C sx = cadd(zk, zm), dy = csub(zk, zm);
-      W0[roff + k] = cscale(sx, half);                      // W_x = (Z_k + conj Z_{N-k}) / 2
-      W1[roff + k] = mk<C>(dy.y * half, -dy.x * half);      // W_y = (Z_k - conj Z_{N-k}) / (2i)
+    C an = mk<C>(0, 0), bn = mk<C>(0, 0);
+    if (lane == 0) { an = W0[roff + N / 2]; bn = W1[roff + N / 2]; }
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      const int k = lane + i * T;
+      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
+      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
     }
-  }
-  const double t2 = block_sum((double)acc2, red);
-  const double t1 = block_sum((double)acc1, red);
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = t2;
-    part[gridDim.x + blockIdx.x] = t1;
-  }
+    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
+    __syncthreads();
+    fft_smem<C, N, E, true>(z, 1, lane, tw);
+    // pointwise: s = g_x^2 + g_y^2, partial sums, w = (beta s - 2) g
+    typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
+    const PC<R> pc(P);
+    const R beta = pc.beta;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = sp(lane + i * T);
+      const C g = z[x];
+      const R s = g.x * g.x + g.y * g.y;
+      acc2 = RD::add(acc2, s * s);
+      acc1 = RD::add(acc1, s);
+      if (MODE == RW_NONLIN) {
+        const R fac = beta * s - (R)2;
+        z[x] = mk<C>(fac * g.x, fac * g.y);
+      }
+    }
+    if constexpr (MODE == RW_NONLIN) {
+      __syncthreads();
+      fft_smem<C, N, E, false>(z, 1, lane, tw);
+      const R half = (R)0.5 * pc.invP;
+#pragma unroll
+      for (int i = 0; i < KH + 1; ++i) {
+        const int k = lane + i * T;
+        if (i == KH && lane != 0) break;
+        const int kk = (i == KH) ? N / 2 : k;
+        const C zk = z[sp(kk)], zm = cconj(z[sp((N - kk) & (N - 1))]);
+        const C sx = cadd(zk, zm), dy = csub(zk, zm);
+        W0[roff + kk] = cscale(sx, half);                      // W_x = (Z_k + conj Z_{N-k}) / 2
+        W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);      // W_y = (Z_k - conj Z_{N-k}) / (2i)
+      }
+    }
+    const typename RD::acc t2 = block_red<R>(acc2, red);
+    const typename RD::acc t1 = block_red<R>(acc1, red);
+    if (threadIdx.x == 0) {
+      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
+      ps[blockIdx.x] = t2;
+      ps[gridDim.x + blockIdx.x] = t1;
+    }
   }
 }
 
@@ -249,38 +339,84 @@ k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double
 // Scalar SAV solve (one warp): combine the partial sums in a fixed order and
 // solve eqs. solver-2 / solver-4 for r^{n+1}. BDF1 is the first-order start.
 // ---------------------------------------------------------------------------
-__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const double* partE, int nE,
-                                        const double* partG, int nG, bool bdf1, int newest, int lane) {
-  const double s2 = warp_sum_array(partE, nE, lane);
-  const double s1 = warp_sum_array(partE + nE, nE, lane);
-  const double gs = warp_sum_array(partG, nG, lane);
-  const double es = warp_sum_array(partG + nG, nG, lane);
-  const double ts = warp_sum_array(partG + 2 * nG, nG, lane);
-  if (lane != 0) return;
+// Scalar SAV solve (eqs. solver-2, solver-4 and solver-6 reduced to scalars),
+// run by one thread of the last block of the column forward pass. Inputs are
+// the grid-reduced sums: sum s^2, sum s (E_1), and the half-spectrum sums of
+// gamma, eta, theta (without |Omega|).
+template <typename R>
+__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const typename Red<R>::acc* q, bool bdf1,
+                                        int newest);
+
+// float64 path: float64 scalar algebra, one square root and two divisions.
+template <>
+__device__ inline void sav_scalar_solve<double>(const Params& P, SavScal* sc, const double* q, bool bdf1,
+                                                int newest) {
+  const double s2 = q[0], s1 = q[1], gs = q[2], es = q[3], ts = q[4];
   const double E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
   const double S = sqrt(E1);
+  const double iS = 1.0 / S;
   const double gamma = P.vol * gs, eta = P.vol * es, theta = P.vol * ts;
   const double dt = P.dt;
-  double rho, r_new, r_base_prev;
-  const double denom = 1.0 - dt * gamma / (2.0 * E1);
+  const double denom = 1.0 - 0.5 * dt * gamma * (iS * iS);
+  double rho, r_prev_new;
   if (bdf1) {
-    const double r0 = S;  // r^0 = sqrt(E_1(phi^0))
-    rho = r0 - theta / (2.0 * S);
-    r_base_prev = r0;
+    rho = S - 0.5 * theta * iS;          // r^0 = sqrt(E_1(phi^0))
+    r_prev_new = S;
   } else {
-    rho = (4.0 * sc->r1 - sc->r0) / 3.0 - theta / (3.0 * S);
-    r_base_prev = sc->r1;
+    rho = (4.0 * sc->r1 - sc->r0 - theta * iS) * (1.0 / 3.0);
+    r_prev_new = sc->r1;
   }
-  const double LHS = (dt * rho * gamma / S + eta) / denom;
-  r_new = rho + LHS / (2.0 * S);
+  const double LHS = (dt * rho * gamma * iS + eta) / denom;
+  const double r_new = rho + 0.5 * LHS * iS;
   const bool ok = isfinite(E1) && E1 > 0.0 && isfinite(gamma) && isfinite(eta) && isfinite(theta) &&
                   denom > 0.0 && isfinite(r_new);
   sc->E1 = E1; sc->S = S; sc->gamma = gamma; sc->eta = eta; sc->theta = theta;
-  sc->denom = denom; sc->LHS = LHS; sc->xi = r_new / S;
+  sc->denom = denom; sc->LHS = LHS; sc->xi = r_new * iS;
   if (!ok) { sc->status = DEV_NONFINITE; return; }
-  sc->r0 = r_base_prev;
+  sc->r0 = r_prev_new;
   sc->r1 = r_new;
-  sc->alpha = dt * r_new / S;
+  sc->alpha = dt * r_new * iS;
+  sc->p = newest;
+  sc->pending = bdf1 ? PEND_BDF1 : PEND_BDF2;
+  sc->nsteps += 1;
+}
+
+__device__ __forceinline__ ff ffp(const float* v) { return ff{v[0], v[1]}; }
+__device__ __forceinline__ void ffs(float* o, ff x) { o[0] = x.hi; o[1] = x.lo; }
+
+// float32-bulk path: the same algebra in float-float (float32 pipes; about
+// 48 significant bits, float64-class for these well-conditioned formulas).
+template <>
+__device__ inline void sav_scalar_solve<float>(const Params& P, SavScal* sc, const float2* q, bool bdf1,
+                                               int newest) {
+  const ff s2{q[0].x, q[0].y}, s1{q[1].x, q[1].y}, gs{q[2].x, q[2].y}, es{q[3].x, q[3].y}, ts{q[4].x, q[4].y};
+  const ff vol = ffp(P.vol_ff), dt = ffp(P.dt_ff);
+  const ff E1 = ff_add(ff_mul(ffp(P.hd_ff), ff_sub(ff_mul(ffp(P.qbeta_ff), s2), s1)), ffp(P.Cvol_ff));
+  const ff S = ff_sqrt(E1);
+  const ff iS = ff_div(ff_make(1.f), S);
+  const ff gamma = ff_mul(vol, gs), eta = ff_mul(vol, es), theta = ff_mul(vol, ts);
+  const ff denom = ff_sub(ff_make(1.f), ff_mulf(ff_mul(ff_mul(dt, gamma), ff_mul(iS, iS)), 0.5f));
+  ff rho, r_prev_new;
+  if (bdf1) {
+    rho = ff_sub(S, ff_mulf(ff_mul(theta, iS), 0.5f));
+    r_prev_new = S;
+  } else {
+    const ff r1 = ffp(sc->r1f), r0 = ffp(sc->r0f);
+    rho = ff_div(ff_sub(ff_sub(ff_mulf(r1, 4.f), r0), ff_mul(theta, iS)), ff_make(3.f));
+    r_prev_new = r1;
+  }
+  const ff LHS = ff_div(ff_add(ff_mul(ff_mul(ff_mul(dt, rho), gamma), iS), eta), denom);
+  const ff r_new = ff_add(rho, ff_mulf(ff_mul(LHS, iS), 0.5f));
+  const ff xi = ff_mul(r_new, iS);
+  const bool ok = ff_isfinite(E1) && E1.hi > 0.f && ff_isfinite(gamma) && ff_isfinite(eta) &&
+                  ff_isfinite(theta) && denom.hi > 0.f && ff_isfinite(r_new);
+  ffs(sc->E1f, E1); ffs(sc->Sf, S); ffs(sc->gammaf, gamma); ffs(sc->etaf, eta); ffs(sc->thetaf, theta);
+  ffs(sc->denomf, denom); ffs(sc->LHSf, LHS); ffs(sc->xif, xi);
+  if (!ok) { sc->status = DEV_NONFINITE; return; }
+  ffs(sc->r0f, r_prev_new);
+  ffs(sc->r1f, r_new);
+  const ff alpha = ff_mul(ff_mul(dt, r_new), iS);
+  sc->alpha_f = alpha.hi;
   sc->p = newest;
   sc->pending = bdf1 ? PEND_BDF1 : PEND_BDF2;
   sc->nsteps += 1;
@@ -290,102 +426,147 @@ __device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const doub
 // Column forward pass. Grid: ceil(NH/CT) blocks.
 // partG: 3 x gridDim.x doubles (gamma, eta, theta partial sums, without |Omega|).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CF_TO_STATE ? 1 : 2) * CT * fft_shape<N>::T)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == CF_TO_STATE ? 1 : 2) * CT * (N / E))
 k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
             C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const double* __restrict__ partE, int nE,
             SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
             int target) {
   using C = C_t<R>;
-  constexpr int T = fft_shape<N>::T;
+  constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
   constexpr int NTH = NF * CT * T;
   constexpr int CTP = CT + 1;
   constexpr int NH = N / 2 + 1;
+  constexpr int IT = N * CT / NTH;
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  using RD = Red<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ double red[32];
+  __shared__ typename RD::acc red[32];
+  __shared__ typename RD::acc red5[5][32];
+  __shared__ typename RD::acc qres[5];
   __shared__ bool am_last;
 
+  pdl_wait();
+  pdl_trigger();
   if (sc->status != DEV_OK) return;
   const int kx0 = blockIdx.x * CT;
-  for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
-    const int y = idx / CT, c = idx % CT, kx = kx0 + c;
-    C a = mk<C>(0, 0), b = mk<C>(0, 0);
-    if (kx < NH) {
-      a = W0[(size_t)y * NH + kx];
-      if (NF == 2) b = W1[(size_t)y * NH + kx];
+  {
+    C va[IT], vb[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int y = idx / CT, kx = kx0 + idx % CT;
+      va[it] = mk<C>(0, 0);
+      vb[it] = mk<C>(0, 0);
+      if (kx < NH) {
+        va[it] = W0[(size_t)y * NH + kx];
+        if (NF == 2) vb[it] = W1[(size_t)y * NH + kx];
+      }
     }
-    sm[y * CTP + c] = a;
-    if (NF == 2) sm[N * CTP + y * CTP + c] = b;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int y = idx / CT, c = idx % CT;
+      sm[sp(y) * CTP + c] = va[it];
+      if (NF == 2) sm[SEQ * CTP + sp(y) * CTP + c] = vb[it];
+    }
   }
   __syncthreads();
   {
     const int q = threadIdx.x / T, lane = threadIdx.x % T;
     const int f = q / CT, c = q % CT;
-    fft_smem<C, N, false>(sm + f * N * CTP + c, CTP, lane, tw);
+    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
   }
   __syncthreads();
 
-  if (MODE == CF_TO_STATE) {
+  if constexpr (MODE == CF_TO_STATE) {
     C* dst = S.at(target);
-    for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
       const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
-      if (kx < NH) dst[(size_t)ky * NH + kx] = sm[ky * CTP + c];
+      if (kx < NH) dst[(size_t)ky * NH + kx] = sm[sp(ky) * CTP + c];
     }
-    return;
-  }
-
-  const int p = sc->p;
-  const int newest = (sc->pending == PEND_BDF2) ? 1 - p : p;
-  const C* snew = S.at(newest);
-  const C* sold = S.at(1 - newest);
-  const R c0 = (MODE == CF_BDF1) ? (R)1 : (R)1.5;
-  R ag = 0, ae = 0, at = 0;
-  for (int idx = threadIdx.x; idx < N * CT; idx += NTH) {
-    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
-    if (kx >= NH) continue;
-    const size_t off = (size_t)ky * NH + kx;
-    const C wx = sm[ky * CTP + c], wy = sm[N * CTP + ky * CTP + c];
-    const R ktx = (R)kderiv(kx, N, P.kf[0]), kty = (R)kderiv(ky, N, P.kf[1]);
-    // N_hat = -i (k~_x W_x + k~_y W_y)
-    const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
-    const C nh = mk<C>(uy, -ux);
-    Nhat[off] = nh;
-    if (MODE == CF_NHAT) continue;
-    const R K2 = sym_K2<R>(kx, ky, P);
-    const R invA = sym_invA<R>(K2, c0, P);
-    C v;
-    if (MODE == CF_BDF1) {
-      v = snew[off];
-    } else {
-      const C cu = snew[off], ol = sold[off];
-      v = mk<C>((R)2 * cu.x - (R)0.5 * ol.x, (R)2 * cu.y - (R)0.5 * ol.y);
+  } else {
+    const PC<R> pc(P);
+    const int p = sc->p;
+    const int newest = (sc->pending == PEND_BDF2) ? 1 - p : p;
+    const C* snew = S.at(newest);
+    const C* sold = S.at(1 - newest);
+    const R c0 = (MODE == CF_BDF1) ? (R)1 : (R)1.5;
+    C vn[IT], vo[IT];
+    if (MODE != CF_NHAT) {
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        const int idx = threadIdx.x + it * NTH;
+        const int ky = idx / CT, kx = kx0 + idx % CT;
+        if (kx < NH) {
+          const size_t off = (size_t)ky * NH + kx;
+          vn[it] = snew[off];
+          if (MODE == CF_BDF2) vo[it] = sold[off];
+        }
+      }
     }
-    const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
-    const R n2 = nh.x * nh.x + nh.y * nh.y;
-    const R nv = nh.x * v.x + nh.y * v.y;
-    ag += w * (-K2 * invA) * n2;   // <N, A^{-1} Delta N>
-    ae += w * nv * invA;           // <N, A^{-1} v>
-    at += w * nv;                  // <N, v>
-  }
-  if (MODE == CF_NHAT) return;
-  const double tg = block_sum((double)ag, red);
-  const double te = block_sum((double)ae, red);
-  const double tt = block_sum((double)at, red);
-  if (threadIdx.x == 0) {
-    partG[blockIdx.x] = tg;
-    partG[gridDim.x + blockIdx.x] = te;
-    partG[2 * gridDim.x + blockIdx.x] = tt;
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    am_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (am_last && threadIdx.x < 32) {
-    __threadfence();
-    sav_scalar_solve(P, sc, partE, nE, partG, gridDim.x, MODE == CF_BDF1, newest, threadIdx.x);
-    if (threadIdx.x == 0) *counter = 0u;
+    typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
+      if (kx >= NH) continue;
+      const size_t off = (size_t)ky * NH + kx;
+      const C wx = sm[sp(ky) * CTP + c], wy = sm[SEQ * CTP + sp(ky) * CTP + c];
+      const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
+      // N_hat = -i (k~_x W_x + k~_y W_y)
+      const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
+      const C nh = mk<C>(uy, -ux);
+      Nhat[off] = nh;
+      if (MODE == CF_NHAT) continue;
+      const R K2 = sym_K2<R>(kx, ky, N, pc);
+      const R invA = sym_invA<R>(K2, c0, pc);
+      C v;
+      if (MODE == CF_BDF1) {
+        v = vn[it];
+      } else {
+        v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+      }
+      const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
+      const R n2 = nh.x * nh.x + nh.y * nh.y;
+      const R nv = nh.x * v.x + nh.y * v.y;
+      ag = RD::add(ag, w * (-K2 * invA) * n2);   // <N, A^{-1} Delta N>
+      ae = RD::add(ae, w * nv * invA);           // <N, A^{-1} v>
+      at = RD::add(at, w * nv);                  // <N, v>
+    }
+    if constexpr (MODE != CF_NHAT) {
+      const typename RD::acc tg = block_red<R>(ag, red);
+      const typename RD::acc te = block_red<R>(ae, red);
+      const typename RD::acc tt = block_red<R>(at, red);
+      if (threadIdx.x == 0) {
+        typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
+        ps[blockIdx.x] = tg;
+        ps[gridDim.x + blockIdx.x] = te;
+        ps[2 * gridDim.x + blockIdx.x] = tt;
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+      }
+      __syncthreads();
+      if (am_last) {
+        __threadfence();
+        using ST = typename RD::store;
+        const ST* pe = reinterpret_cast<const ST*>(partE);
+        const ST* pg = reinterpret_cast<const ST*>(partG);
+        const ST* arr[5] = {pe, pe + nE, pg, pg + gridDim.x, pg + 2 * gridDim.x};
+        const int cnt[5] = {nE, nE, (int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
+        block_red_arrays<R, 5>(arr, cnt, qres, red5);
+        if (threadIdx.x == 0) {
+          sav_scalar_solve<R>(P, sc, qres, MODE == CF_BDF1, newest);
+          *counter = 0u;
+        }
+      }
+    }
   }
 }
 
@@ -401,7 +582,8 @@ __global__ void k2d_finalize(const Params P, Slots<R> S, const C_t<R>* __restric
   const int N = P.N, NH = P.NH;
   const int p = sc->p;
   const bool bdf1 = sc->pending == PEND_BDF1;
-  const R alpha = (R)sc->alpha;
+  const R alpha = read_alpha<R>(sc);
+  const PC<R> pc(P);
   C* cur = S.at(p);
   C* old = S.at(1 - p);
   const size_t total = (size_t)N * NH;
@@ -409,18 +591,18 @@ __global__ void k2d_finalize(const Params P, Slots<R> S, const C_t<R>* __restric
        off += (size_t)gridDim.x * blockDim.x) {
     const int ky = (int)(off / NH), kx = (int)(off % NH);
     if (off == 0) {
-      const double z = bdf1 ? sc->zm[p] : sc->zm[p] + (sc->zm[p] - sc->zm[1 - p]) / 3.0;
+      const double z = bdf1 ? sc->zm[p] : zero_mode_update(sc->zm[p], sc->zm[1 - p]);
       sc->zm[1 - p] = z;
       old[0] = mk<C>((R)z, (R)0);
       continue;
     }
-    const R K2 = sym_K2<R>(kx, ky, P);
+    const R K2 = sym_K2<R>(kx, ky, N, pc);
     const C cu = cur[off], nh = Nhat[off];
     C nw;
     if (bdf1) {
-      nw = bdf1_update<C, R>(cu, nh, K2, sym_invA<R>(K2, (R)1, P), alpha);
+      nw = bdf1_update<C, R>(cu, nh, K2, sym_invA<R>(K2, (R)1, pc), alpha);
     } else {
-      nw = bdf2_update<C, R>(cu, old[off], nh, K2, sym_invA<R>(K2, (R)1.5, P), alpha);
+      nw = bdf2_update<C, R>(cu, old[off], nh, K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
     }
     old[off] = nw;
   }
@@ -434,14 +616,15 @@ __global__ void k2d_ghost(const Params P, Slots<R> S, const C_t<R>* __restrict__
   const int p = sc->p;
   const C* cur = S.at(p);
   C* dst = S.at(1 - p);
+  const PC<R> pc(P);
   const size_t total = (size_t)N * NH;
   for (size_t off = blockIdx.x * (size_t)blockDim.x + threadIdx.x; off < total;
        off += (size_t)gridDim.x * blockDim.x) {
     const int ky = (int)(off / NH), kx = (int)(off % NH);
-    const R K2 = sym_K2<R>(kx, ky, P);
+    const R K2 = sym_K2<R>(kx, ky, N, pc);
     const C cu = cur[off], nh = Nhat[off];
-    const R L = (R)P.a + K2 * K2;
-    const R f = (R)P.dt * K2;
+    const R L = pc.a + K2 * K2;
+    const R f = pc.dt * K2;
     dst[off] = mk<C>(cu.x + f * (nh.x + L * cu.x), cu.y + f * (nh.y + L * cu.y));
     if (off == 0) sc->zm[1 - p] = sc->zm[p];
   }
@@ -465,7 +648,7 @@ __global__ void k2d_norms(const Params P, Slots<R> S, const SavScal* sc, double*
        off += (size_t)gridDim.x * blockDim.x) {
     if (off == 0) continue;
     const int ky = (int)(off / NH), kx = (int)(off % NH);
-    const double kxx = kx * P.kf[0], kyy = kfull(ky, N, P.kf[1]);
+    const double kxx = kx * P.kf[0], kyy = kfull<double>(ky, N, P.kf[1]);
     const double K2 = kxx * kxx + kyy * kyy;
     const double w = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
     const C u = nw[off], v = ol[off];
@@ -514,7 +697,26 @@ enum ScalarOp : int {
 };
 
 // One-warp scalar operations on the record.
-static __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a, int na, const double* b,
+// r of the newest / previous level in the record's working representation
+template <typename R> __device__ __forceinline__ void set_r1(SavScal* sc, double v) {
+  sc->r1 = v;
+  if (sizeof(R) == 4) { sc->r1f[0] = (float)v; sc->r1f[1] = (float)(v - (double)sc->r1f[0]); }
+}
+template <typename R> __device__ __forceinline__ void set_r0(SavScal* sc, double v) {
+  sc->r0 = v;
+  if (sizeof(R) == 4) { sc->r0f[0] = (float)v; sc->r0f[1] = (float)(v - (double)sc->r0f[0]); }
+}
+template <typename R> __device__ __forceinline__ double get_r1(const SavScal* sc) {
+  return sizeof(R) == 4 ? (double)sc->r1f[0] + (double)sc->r1f[1] : sc->r1;
+}
+template <typename R> __device__ __forceinline__ double get_r0(const SavScal* sc) {
+  return sizeof(R) == 4 ? (double)sc->r0f[0] + (double)sc->r0f[1] : sc->r0;
+}
+
+// `a` holds E_1 partial sums (accumulators of precision R) for the ops that
+// need them, or float64 sums for SO_ZM_SLOT; `b` holds float64 norm partials.
+template <typename R>
+__global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a, int na, const double* b,
                             int nb, int arg, double x0, double x1) {
   const int lane = threadIdx.x;
   if (op == SO_FLIP) {
@@ -525,7 +727,7 @@ static __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const do
     return;
   }
   if (op == SO_SET_R) {
-    if (lane == 0) { sc->r1 = x0; sc->r0 = x1; }
+    if (lane == 0) { set_r1<R>(sc, x0); set_r0<R>(sc, x1); }
     return;
   }
   if (op == SO_ZM_SLOT) {
@@ -533,13 +735,14 @@ static __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const do
     if (lane == 0) sc->zm[arg == 0 ? sc->p : 1 - sc->p] = s / P.P;
     return;
   }
-  const double s2 = warp_sum_array(a, na, lane);
-  const double s1 = warp_sum_array(a + na, na, lane);
+  using ST = typename Red<R>::store;
+  const double s2 = warp_red_array<R>(reinterpret_cast<const ST*>(a), na, lane);
+  const double s1 = warp_red_array<R>(reinterpret_cast<const ST*>(a) + na, na, lane);
   if (op == SO_R_NEWEST || op == SO_R_PREV) {
     if (lane == 0) {
       const double E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
       if (!(isfinite(E1) && E1 > 0.0)) { sc->status = DEV_NONFINITE; return; }
-      if (op == SO_R_NEWEST) sc->r1 = sqrt(E1); else sc->r0 = sqrt(E1);
+      if (op == SO_R_NEWEST) set_r1<R>(sc, sqrt(E1)); else set_r0<R>(sc, sqrt(E1));
     }
     return;
   }
@@ -556,7 +759,7 @@ static __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const do
       const double Lpsi = P.vol * (n2 + P.a * zp * zp);     // ||L^{1/2} psi||^2
       const double Lphi = P.a * phi2 + lap2;
       const double grad4 = P.hd * s2, grad2 = P.hd * s1;
-      const double r1 = sc->r1, r0 = sc->r0;
+      const double r1 = get_r1<R>(sc), r0 = get_r0<R>(sc);
       sc->E_orig = 0.25 * P.beta * grad4 + 0.5 * P.a * phi2 - grad2 + 0.5 * lap2;
       sc->E_mod = 0.25 * (Lphi + Lpsi) + 0.5 * (r1 * r1 + (2.0 * r1 - r0) * (2.0 * r1 - r0));
       sc->E_breve = 0.5 * P.a * phi2 + 0.5 * lap2 + r1 * r1;

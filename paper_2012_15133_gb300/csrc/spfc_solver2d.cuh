@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -22,15 +23,38 @@ namespace spfc {
     }                                                                              \
   } while (0)
 
-// Launch shape per grid size: CT kx columns per column-pass block, RPC rows
-// per row-pass block. Every block fills whole warps.
+// Launch shape per grid size: E values per FFT lane (T = N/E lanes per
+// sequence), CT kx columns per column-pass block, RPC rows per row-pass block.
+// Every block fills whole warps.
 template <int N> struct Shape2D {
-  static constexpr int T = fft_shape<N>::T;
-  static constexpr int CT = (32 / T > 4) ? 32 / T : 4;
+  static constexpr int E = 8;
+  static constexpr int T = N / E;
+  static constexpr int CT = (N >= 256) ? 2 : ((32 / T > 4) ? 32 / T : 4);
   static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
   static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
-  static_assert(N % RPC == 0 && (RPC * T) % 32 == 0, "row tile must divide N and fill warps");
+  static_assert(sizeof(Red<float>::store) == sizeof(double) && sizeof(Red<double>::store) == sizeof(double),
+                "partial-sum buffers hold 8-byte entries");
+  static_assert(N % RPC == 0 && (RPC * T) % 32 == 0 && (2 * CT * T) % 32 == 0 && (CT * T) % 32 == 0,
+                "tiles must divide N and fill warps");
 };
+
+// Kernel launch, optionally with programmatic stream serialization (the
+// kernel may begin while its predecessor finishes; it waits with pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
   tw.resize(TW_N);
@@ -47,13 +71,18 @@ class Solver2D final : public SolverBase {
   using C = C_t<R>;
   using SH = Shape2D<N>;
   static constexpr int NH = N / 2 + 1;
-  static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T;
+  static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T, E = SH::E;
   static constexpr int GCOL = (NH + CT - 1) / CT;
   static constexpr int GROW = N / RPC;
   static constexpr int PW_THREADS = 256;
 
  public:
-  Solver2D(const Params& p, cudaStream_t s) : st_(s) { P = p; }
+  Solver2D(const Params& p, cudaStream_t s) : st_(s) {
+    P = p;
+    // Programmatic dependent launch measured slower for these short kernels
+    // (20.5 vs 33.6 us per 512^2 step); SPFC_PDL=1 enables it for A/B timing.
+    use_pdl_ = std::getenv("SPFC_PDL") != nullptr;
+  }
 
   int setup() {
     const size_t sb = (size_t)N * NH * sizeof(C);
@@ -95,17 +124,17 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaMemset(S_.s[1], 0, sb));
     SPFC_CK(cudaMemset(Nhat_, 0, sb));
     // opt in to > 48 KB dynamic shared memory where a tile needs it
-    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_STEP>, smem_col(2)));
-    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_GRAD>, smem_col(2)));
-    SPFC_CK(set_smem(k2d_col_inv<R, N, CT, CI_FIELD>, smem_col(1)));
-    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_NONLIN>, smem_row()));
-    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_ENERGY>, smem_row()));
-    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_OUT_REAL>, smem_row()));
-    SPFC_CK(set_smem(k2d_row<R, N, RPC, RW_IN_REAL>, smem_row()));
-    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_BDF2>, smem_col(2)));
-    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_BDF1>, smem_col(2)));
-    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_NHAT>, smem_col(2)));
-    SPFC_CK(set_smem(k2d_col_fwd<R, N, CT, CF_TO_STATE>, smem_col(1)));
+    SPFC_CK(set_smem(k2d_col_inv<R, N, E, CT, CI_STEP>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_inv<R, N, E, CT, CI_GRAD>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_inv<R, N, E, CT, CI_FIELD>, smem_col(1)));
+    SPFC_CK(set_smem(k2d_row<R, N, E, RPC, RW_NONLIN>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, E, RPC, RW_ENERGY>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, E, RPC, RW_OUT_REAL>, smem_row()));
+    SPFC_CK(set_smem(k2d_row<R, N, E, RPC, RW_IN_REAL>, smem_row()));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_BDF2>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_BDF1>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_NHAT>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_TO_STATE>, smem_col(1)));
     SPFC_CK(cudaStreamCreateWithFlags(&cap_st_, cudaStreamNonBlocking));
     return 0;
   }
@@ -169,6 +198,7 @@ class Solver2D final : public SolverBase {
   int dt_change(double dt) override {
     int rc = finalize(); if (rc) return rc;
     P.dt = dt;
+    fill_float_params(&P);
     drop_graphs();
     rc = copy_newest_to_prev(); if (rc) return rc;
     rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
@@ -239,6 +269,7 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaStreamSynchronize(st_));
     SavScal h;
     SPFC_CK(cudaMemcpy(&h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost));
+    if (sizeof(R) == 4) scal_from_ff(&h);
     if (h.status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
       return h.status;
@@ -304,19 +335,20 @@ class Solver2D final : public SolverBase {
   template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
-  static constexpr size_t smem_col(int nf) { return (size_t)nf * N * (CT + 1) * sizeof(C); }
-  static constexpr size_t smem_row() { return (size_t)RPC * (N + 1) * sizeof(C); }
+  static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * (CT + 1) * sizeof(C); }
+  static constexpr size_t smem_row() { return (size_t)RPC * (sp_len(N) + 1) * sizeof(C); }
 
   int launch_col_inv(int mode, int which) {
     switch (mode) {
       case CI_STEP:
-        k2d_col_inv<R, N, CT, CI_STEP><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, P, S_, Nhat_,
+                         W_[0], W_[1], sc_, tw_, which));
         break;
       case CI_GRAD:
-        k2d_col_inv<R, N, CT, CI_GRAD><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        k2d_col_inv<R, N, E, CT, CI_GRAD><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
         break;
       default:
-        k2d_col_inv<R, N, CT, CI_FIELD><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        k2d_col_inv<R, N, E, CT, CI_FIELD><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
     }
     SPFC_CK(cudaGetLastError());
     return 0;
@@ -324,16 +356,17 @@ class Solver2D final : public SolverBase {
   int launch_row(int mode) {
     switch (mode) {
       case RW_NONLIN:
-        k2d_row<R, N, RPC, RW_NONLIN><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        SPFC_CK(launch_k(k2d_row<R, N, E, RPC, RW_NONLIN>, GROW, RPC * T, smem_row(), st_, pdl_, P, W_[0], W_[1],
+                         partE_, sc_, tw_, real_));
         break;
       case RW_ENERGY:
-        k2d_row<R, N, RPC, RW_ENERGY><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        k2d_row<R, N, E, RPC, RW_ENERGY><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
         break;
       case RW_OUT_REAL:
-        k2d_row<R, N, RPC, RW_OUT_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        k2d_row<R, N, E, RPC, RW_OUT_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
         break;
       default:
-        k2d_row<R, N, RPC, RW_IN_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
+        k2d_row<R, N, E, RPC, RW_IN_REAL><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], W_[1], partE_, sc_, tw_, real_);
     }
     SPFC_CK(cudaGetLastError());
     return 0;
@@ -341,28 +374,30 @@ class Solver2D final : public SolverBase {
   int launch_col_fwd(int mode, int target) {
     switch (mode) {
       case CF_BDF2:
-        k2d_col_fwd<R, N, CT, CF_BDF2><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, P, S_, W_[0],
+                         W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target));
         break;
       case CF_BDF1:
-        k2d_col_fwd<R, N, CT, CF_BDF1><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        k2d_col_fwd<R, N, E, CT, CF_BDF1><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
         break;
       case CF_NHAT:
-        k2d_col_fwd<R, N, CT, CF_NHAT><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        k2d_col_fwd<R, N, E, CT, CF_NHAT><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
         break;
       default:
-        k2d_col_fwd<R, N, CT, CF_TO_STATE><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        k2d_col_fwd<R, N, E, CT, CF_TO_STATE><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
     }
     SPFC_CK(cudaGetLastError());
     return 0;
   }
   int scalar_op(int op, const double* a, int na, const double* b, int nb, int arg, double x0 = 0, double x1 = 0) {
-    k_scalar_op<<<1, 32, 0, st_>>>(P, sc_, op, a, na, b, nb, arg, x0, x1);
+    k_scalar_op<R><<<1, 32, 0, st_>>>(P, sc_, op, a, na, b, nb, arg, x0, x1);
     SPFC_CK(cudaGetLastError());
     return 0;
   }
   int read_scal(SavScal* h) {
     SPFC_CK(cudaMemcpyAsync(h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
+    if (sizeof(R) == 4) scal_from_ff(h);
     if (h->status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
       return h->status;
@@ -425,12 +460,14 @@ class Solver2D final : public SolverBase {
   int capture(int nsteps, cudaGraphExec_t* out) {
     cudaStream_t keep = st_;
     st_ = cap_st_;
+    pdl_ = use_pdl_;
     cudaGraph_t g = nullptr;
     SPFC_CK(cudaStreamBeginCapture(cap_st_, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
     for (int i = 0; i < nsteps && rc == 0; ++i) rc = launch_step_kernels();
     cudaError_t e = cudaStreamEndCapture(cap_st_, &g);
     st_ = keep;
+    pdl_ = false;
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) { err = std::string("graph capture: ") + cudaGetErrorString(e); return 3; }
     e = cudaGraphInstantiate(out, g, 0);
@@ -486,6 +523,8 @@ class Solver2D final : public SolverBase {
   size_t spec_bytes_ = 0, total_ = 0;
   cudaGraphExec_t g1_ = nullptr, g16_ = nullptr;
   bool timing_ = false;
+  bool pdl_ = false;                // launch the step kernels with programmatic serialization
+  bool use_pdl_ = false;
   std::vector<cudaEvent_t> evpool_;
   int evnext_ = 0;
   std::vector<TRec> trecs_;

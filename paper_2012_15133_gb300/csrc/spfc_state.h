@@ -19,6 +19,12 @@ struct Params {
   double beta;    // coefficient of 1/4 |grad phi|^4
   double C;       // C_beta = 1 + 1/beta (E_1 >= |Omega|)
   double dt;
+  double invP;    // 1 / P
+  // float32 copies for the float32-bulk kernels (no float64 work per thread)
+  float kf_f[3];
+  float dt_f, a_f, beta_f, invP_f;
+  // float-float (hi, lo) copies for the float32-bulk scalar algebra
+  float hd_ff[2], vol_ff[2], Cvol_ff[2], qbeta_ff[2], dt_ff[2];
 };
 
 enum PendingKind : int { PEND_NONE = 0, PEND_BDF2 = 1, PEND_BDF1 = 2 };
@@ -34,6 +40,8 @@ enum DevStatus : int { DEV_OK = 0, DEV_NONFINITE = 4, DEV_TIMEOUT = 5 };
 struct SavScal {
   double r1, r0;        // r of the newest level and of the one before
   double alpha;         // dt r^{n+1} / sqrt(E1) of the pending update
+  float alpha_f;        // the same, rounded to float32 (read by float32-bulk kernels)
+  int pad0_;
   double zm[2];         // FP64 zero mode of each slot (mean of phi)
   // last SAV solve (diagnostics)
   double E1, S, gamma, eta, theta, denom, LHS, xi;
@@ -41,6 +49,11 @@ struct SavScal {
   double E_orig, E_mod, E_breve;
   int p, pending, status, pad_;
   long long nsteps;
+  // float32-bulk path: the scalar algebra runs in float-float (hi, lo); these
+  // are its state (r) and diagnostics, converted to the float64 fields above
+  // by the host when read.
+  float r1f[2], r0f[2];
+  float E1f[2], Sf[2], gammaf[2], etaf[2], thetaf[2], denomf[2], LHSf[2], xif[2];
 };
 
 }  // namespace spfc
