@@ -135,6 +135,31 @@ int64_t spfc_device_bytes(spfc_t h);
 
 void spfc_destroy(spfc_t h);
 
+/* Allocation-free energy diagnostics of one 2D field (float64).
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory -- code whose device memory is owned by another allocator or
+ * a fixed budget, and code that must not risk the device synchronisation
+ * that cudaMalloc / cudaFree can cause. It allocates nothing: its scratch
+ * lives in one fixed device array of about 1.6 MB inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ * n: points per axis, one of 16, 32, 64, 128, 256 (larger N is rejected with
+ *    SPFC_EINVAL: the scratch array is sized for 256 x 256);
+ * L[2]: box lengths; eps, beta as in spfc_create;
+ * phi_dev: the field, n*n float64 values on the current device (x fastest);
+ * out[3] (host): E_N(phi) (eq. energy-discrete-spectral), 1/2 ||L_N^{1/2} phi||^2,
+ *    and the mass h^2 sum phi;
+ * cuda_stream: the stream to run on (synchronised before returning).
+ * The first call on a device, with that device current, looks up the
+ * scratch array's device address and writes a twiddle table into it; make
+ * that first call before any stream capture. All calls share the one array
+ * and leave their contents in it; calls that overlap on the GPU (other host
+ * threads, other streams) race and must be serialised by the caller.
+ * Errors: SPFC_EINVAL, SPFC_ECUDA, SPFC_ENONFINITE; message in
+ * spfc_noalloc_last_error(). */
+int spfc_field_energy_noalloc(int n, const double* L, double eps, double beta, const double* phi_dev,
+                              double* out, void* cuda_stream);
+const char* spfc_noalloc_last_error(void);
+
 /* Message of the last failed call on this handle (or of the last failed
  * spfc_create on this thread when h is NULL). Never NULL. */
 const char* spfc_last_error(spfc_t h);

@@ -44,6 +44,8 @@ _SIGS = {
     "spfc_device_bytes": (ct.c_int64, [_P]),
     "spfc_destroy": (None, [_P]),
     "spfc_last_error": (ct.c_char_p, [_P]),
+    "spfc_field_energy_noalloc": (_I, [_I, _DP, _D, _D, _P, _DP, _P]),
+    "spfc_noalloc_last_error": (ct.c_char_p, []),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -86,6 +88,24 @@ def _is_torch(x):
 def _current_stream_ptr():
     import torch
     return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def field_energy_noalloc(phi, L, eps, beta, stream=None):
+    """Energy diagnostics of one 2D float64 CUDA field through the allocation-free
+    entry point (see include/spfc.h): returns (E_N, 1/2 ||L^{1/2} phi||^2, mass)."""
+    import torch
+    lib = load_library()
+    if not (phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.dim() == 2
+            and phi.shape[0] == phi.shape[1]):
+        raise ValueError("phi must be a square, contiguous float64 CUDA tensor")
+    Ls = [float(L)] * 2 if np.isscalar(L) else [float(v) for v in L]
+    out = (ct.c_double * 3)()
+    sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None else stream)
+    rc = lib.spfc_field_energy_noalloc(int(phi.shape[0]), (ct.c_double * 2)(*Ls), float(eps), float(beta),
+                                       ct.c_void_p(phi.data_ptr()), out, sp)
+    if rc != 0:
+        raise SPFCError(rc, lib.spfc_noalloc_last_error().decode())
+    return out[0], out[1], out[2]
 
 
 class Solver:
