@@ -221,7 +221,7 @@ def run_ours(args):
     # --- roofline of the dominant kernel (algorithmic bytes: spectrum passes)
     csize = 8 if args.precision == "fp32" else 16
     SB = N_GRID * (N_GRID // 2 + 1) * csize
-    passes = {"col_inv": 6, "row": 4, "col_fwd": 5}
+    passes = {"row": 4, "col_fused": 7}
     dom = max(kt, key=lambda k: kt[k][1])
     nl, ms = kt[dom]
     avg_s = ms / nl * 1e-3
@@ -297,6 +297,24 @@ def run_ours(args):
     return 0
 
 
+def run_driver(args):
+    """Profiling driver (for ncu): init, then K steps of the workload with the
+    kernels launched one by one; no timing, no flush."""
+    import torch
+    from paper_2012_15133_gb300 import Solver, build
+    build.build()
+    from seeded_inputs import crystal_2d_case
+    c = crystal_2d_case(args.n)
+    s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+    s.init(c["phi0"], "bdf1")
+    s.set_timing(True)
+    s.step(args.steps)
+    s.sync()
+    print(json.dumps({"driver": True, "n": args.n, "precision": args.precision, "steps": args.steps,
+                      "kernels": s.kernel_times()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,7 +324,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-driver", action="store_true",
+                    help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
+    ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
     args = ap.parse_args()
+    if args.ncu_driver:
+        return run_driver(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

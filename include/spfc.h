@@ -74,6 +74,16 @@ typedef enum {
 int spfc_create(int d, const int* n, const double* L, double eps, double beta, double dt,
                 int precision, void* cuda_stream, spfc_t* out);
 
+/* Kernel launch schedules (tile shapes) compiled for a grid: spfc_create uses
+ * schedule 0; spfc_create_scheduled picks one explicitly (0 <= schedule <
+ * spfc_num_schedules(d, n)), which is how the autotuner times the choices.
+ * All schedules compute the same step; results agree to rounding.
+ * spfc_schedule returns the handle's schedule. */
+int spfc_num_schedules(int d, int n);
+int spfc_create_scheduled(int d, const int* n, const double* L, double eps, double beta, double dt,
+                          int precision, void* cuda_stream, int schedule, spfc_t* out);
+int spfc_schedule(spfc_t h);
+
 /* Load phi^0 (N^d float64 values) and start the scheme with `mode` (spfc_start).
  * After BDF1 the handle holds (phi^1, phi^0, r^1, r^0); after GHOST/COPY it
  * holds (phi^0, phi^{-1}, r^0, r^{-1}) with r = sqrt(E_{1,N}) as in the line

@@ -7,7 +7,9 @@ module) and builds it (``build`` module). There is no CPU fallback: using the
 solver without the built library raises.
 """
 from .spfc import (Solver, SPFCError, lib_path, load_library, FP64, FP32_BULK,
-                   START_BDF1, START_GHOST, START_COPY, EXPORTED_SYMBOLS, field_energy_noalloc)
+                   START_BDF1, START_GHOST, START_COPY, EXPORTED_SYMBOLS, field_energy_noalloc,
+                   num_schedules)
 
 __all__ = ["Solver", "SPFCError", "lib_path", "load_library", "FP64", "FP32_BULK",
-           "START_BDF1", "START_GHOST", "START_COPY", "EXPORTED_SYMBOLS", "field_energy_noalloc"]
+           "START_BDF1", "START_GHOST", "START_COPY", "EXPORTED_SYMBOLS", "field_energy_noalloc",
+           "num_schedules"]

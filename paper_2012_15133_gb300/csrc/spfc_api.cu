@@ -30,6 +30,15 @@ extern "C" {
 
 int spfc_create(int d, const int* n, const double* L, double eps, double beta, double dt, int precision,
                 void* cuda_stream, spfc_t* out) {
+  return spfc_create_scheduled(d, n, L, eps, beta, dt, precision, cuda_stream, -1, out);
+}
+
+int spfc_num_schedules(int d, int n) { return spfc::num_schedules(d, n); }
+
+int spfc_schedule(spfc_t h) { return h ? h->s->schedule : -1; }
+
+int spfc_create_scheduled(int d, const int* n, const double* L, double eps, double beta, double dt, int precision,
+                          void* cuda_stream, int schedule, spfc_t* out) {
   if (!out) return fail(nullptr, SPFC_EINVAL, "out is NULL");
   *out = nullptr;
   if (d != 2 && d != 3) return fail(nullptr, SPFC_EINVAL, "d must be 2 or 3");
@@ -63,9 +72,10 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
   spfc::fill_float_params(&P);
   int status = 0;
   std::string err;
+  if (schedule < 0) schedule = 0;
   SolverBase* s = (precision == SPFC_FP64)
-                      ? spfc::make_solver_f64(P, (cudaStream_t)cuda_stream, &status, &err)
-                      : spfc::make_solver_f32(P, (cudaStream_t)cuda_stream, &status, &err);
+                      ? spfc::make_solver_f64(P, (cudaStream_t)cuda_stream, schedule, &status, &err)
+                      : spfc::make_solver_f32(P, (cudaStream_t)cuda_stream, schedule, &status, &err);
   if (!s) return fail(nullptr, status ? status : SPFC_ECUDA, err);
   s->precision = precision;
   spfc_t h = new spfc_s;
@@ -192,7 +202,7 @@ int spfc_set_timing(spfc_t h, int on) {
 
 int spfc_kernel_times(spfc_t h, int max, const char** names, int64_t* launches, double* ms) {
   if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
-  static const char* kNames[] = {"col_inv", "row", "col_fwd", "col_z", "col_y", "k4", "k5", "k6"};
+  static const char* kNames[] = {"col_inv", "row", "col_fwd", "col_fused", "col_z", "col_y", "k4", "k5", "k6"};
   spfc::KernelTimes kt;
   int rc = h->s->kernel_times(&kt);
   if (rc) return wrap(h, rc);

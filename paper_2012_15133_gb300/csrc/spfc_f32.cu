@@ -2,8 +2,8 @@
 #include "spfc_solver2d.cuh"
 
 namespace spfc {
-SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int* status, std::string* err) {
-  if (P.d == 2) return make_solver_2d<float>(P, st, status, err);
+SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err) {
+  if (P.d == 2) return make_solver_2d<float>(P, st, schedule, status, err);
   *status = 1;
   *err = "3D is not available in this build";
   return nullptr;

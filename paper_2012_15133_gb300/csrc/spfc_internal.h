@@ -38,6 +38,7 @@ class SolverBase {
 
   Params P{};
   int precision = 0;
+  int schedule = 0;
   bool inited = false;
   std::string err;
 };
@@ -84,7 +85,8 @@ inline void scal_from_ff(SavScal* h) {
 }
 
 // Factories (one translation unit per precision); return nullptr and set err on failure.
-SolverBase* make_solver_f64(const Params& P, cudaStream_t st, int* status, std::string* err);
-SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int* status, std::string* err);
+SolverBase* make_solver_f64(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err);
+SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err);
+int num_schedules(int d, int N);
 
 }  // namespace spfc

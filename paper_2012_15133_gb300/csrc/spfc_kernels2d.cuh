@@ -122,7 +122,7 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
   constexpr int NTH = NF * CT * T;
-  constexpr int CTP = CT + 1;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
   constexpr int IT = N * CT / NTH;  // elements per thread in the tile phases
   constexpr int SEQ = sp_len(N);
@@ -339,87 +339,121 @@ k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double
 // Scalar SAV solve (one warp): combine the partial sums in a fixed order and
 // solve eqs. solver-2 / solver-4 for r^{n+1}. BDF1 is the first-order start.
 // ---------------------------------------------------------------------------
-// Scalar SAV solve (eqs. solver-2, solver-4 and solver-6 reduced to scalars),
-// run by one thread of the last block of the column forward pass. Inputs are
-// the grid-reduced sums: sum s^2, sum s (E_1), and the half-spectrum sums of
-// gamma, eta, theta (without |Omega|).
-template <typename R>
-__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const typename Red<R>::acc* q, bool bdf1,
-                                        int newest);
-
-// float64 path: float64 scalar algebra, one square root and two divisions.
-template <>
-__device__ inline void sav_scalar_solve<double>(const Params& P, SavScal* sc, const double* q, bool bdf1,
-                                                int newest) {
-  const double s2 = q[0], s1 = q[1], gs = q[2], es = q[3], ts = q[4];
-  const double E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
-  const double S = sqrt(E1);
-  const double iS = 1.0 / S;
-  const double gamma = P.vol * gs, eta = P.vol * es, theta = P.vol * ts;
-  const double dt = P.dt;
-  const double denom = 1.0 - 0.5 * dt * gamma * (iS * iS);
-  double rho, r_prev_new;
-  if (bdf1) {
-    rho = S - 0.5 * theta * iS;          // r^0 = sqrt(E_1(phi^0))
-    r_prev_new = S;
-  } else {
-    rho = (4.0 * sc->r1 - sc->r0 - theta * iS) * (1.0 / 3.0);
-    r_prev_new = sc->r1;
-  }
-  const double LHS = (dt * rho * gamma * iS + eta) / denom;
-  const double r_new = rho + 0.5 * LHS * iS;
-  const bool ok = isfinite(E1) && E1 > 0.0 && isfinite(gamma) && isfinite(eta) && isfinite(theta) &&
-                  denom > 0.0 && isfinite(r_new);
-  sc->E1 = E1; sc->S = S; sc->gamma = gamma; sc->eta = eta; sc->theta = theta;
-  sc->denom = denom; sc->LHS = LHS; sc->xi = r_new * iS;
-  if (!ok) { sc->status = DEV_NONFINITE; return; }
-  sc->r0 = r_prev_new;
-  sc->r1 = r_new;
-  sc->alpha = dt * r_new * iS;
-  sc->p = newest;
-  sc->pending = bdf1 ? PEND_BDF1 : PEND_BDF2;
-  sc->nsteps += 1;
-}
-
+// Scalar SAV solve (eqs. solver-2, solver-4 and solver-6 reduced to scalars).
+// Inputs are the grid-reduced sums q = {sum s^2, sum s (E_1), and the
+// half-spectrum sums of gamma, eta, theta without |Omega|} and r of the two
+// current levels; BDF1 is the first-order start (r^0 = sqrt(E_1(phi^0))).
+// sav_solve computes, sav_commit writes the record.
+template <typename R> struct SolveOut;
+template <> struct SolveOut<double> {
+  double E1, S, gamma, eta, theta, denom, LHS, xi, r_new, r_prev_new, alpha;
+  bool ok;
+};
+template <> struct SolveOut<float> {
+  ff E1, S, gamma, eta, theta, denom, LHS, xi, r_new, r_prev_new;
+  float alpha;
+  bool ok;
+};
+template <typename R> struct RIn;
+template <> struct RIn<double> {
+  double r1, r0;
+  __device__ explicit RIn(const SavScal* sc) : r1(sc->r1), r0(sc->r0) {}
+  __device__ RIn() : r1(0), r0(0) {}
+};
 __device__ __forceinline__ ff ffp(const float* v) { return ff{v[0], v[1]}; }
 __device__ __forceinline__ void ffs(float* o, ff x) { o[0] = x.hi; o[1] = x.lo; }
+template <> struct RIn<float> {
+  ff r1, r0;
+  __device__ explicit RIn(const SavScal* sc) : r1(ffp(sc->r1f)), r0(ffp(sc->r0f)) {}
+  __device__ RIn() : r1{0.f, 0.f}, r0{0.f, 0.f} {}
+};
+
+// float64 path: float64 scalar algebra, one square root and two divisions.
+__device__ inline SolveOut<double> sav_solve(const Params& P, const double* q, bool bdf1, const RIn<double>& rin) {
+  SolveOut<double> o;
+  const double s2 = q[0], s1 = q[1], gs = q[2], es = q[3], ts = q[4];
+  o.E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
+  o.S = sqrt(o.E1);
+  const double iS = 1.0 / o.S;
+  o.gamma = P.vol * gs; o.eta = P.vol * es; o.theta = P.vol * ts;
+  const double dt = P.dt;
+  o.denom = 1.0 - 0.5 * dt * o.gamma * (iS * iS);
+  double rho;
+  if (bdf1) {
+    rho = o.S - 0.5 * o.theta * iS;
+    o.r_prev_new = o.S;
+  } else {
+    rho = (4.0 * rin.r1 - rin.r0 - o.theta * iS) * (1.0 / 3.0);
+    o.r_prev_new = rin.r1;
+  }
+  o.LHS = (dt * rho * o.gamma * iS + o.eta) / o.denom;
+  o.r_new = rho + 0.5 * o.LHS * iS;
+  o.xi = o.r_new * iS;
+  o.alpha = dt * o.r_new * iS;
+  o.ok = isfinite(o.E1) && o.E1 > 0.0 && isfinite(o.gamma) && isfinite(o.eta) && isfinite(o.theta) &&
+         o.denom > 0.0 && isfinite(o.r_new);
+  return o;
+}
 
 // float32-bulk path: the same algebra in float-float (float32 pipes; about
 // 48 significant bits, float64-class for these well-conditioned formulas).
-template <>
-__device__ inline void sav_scalar_solve<float>(const Params& P, SavScal* sc, const float2* q, bool bdf1,
-                                               int newest) {
+__device__ inline SolveOut<float> sav_solve(const Params& P, const float2* q, bool bdf1, const RIn<float>& rin) {
+  SolveOut<float> o;
   const ff s2{q[0].x, q[0].y}, s1{q[1].x, q[1].y}, gs{q[2].x, q[2].y}, es{q[3].x, q[3].y}, ts{q[4].x, q[4].y};
   const ff vol = ffp(P.vol_ff), dt = ffp(P.dt_ff);
-  const ff E1 = ff_add(ff_mul(ffp(P.hd_ff), ff_sub(ff_mul(ffp(P.qbeta_ff), s2), s1)), ffp(P.Cvol_ff));
-  const ff S = ff_sqrt(E1);
-  const ff iS = ff_div(ff_make(1.f), S);
-  const ff gamma = ff_mul(vol, gs), eta = ff_mul(vol, es), theta = ff_mul(vol, ts);
-  const ff denom = ff_sub(ff_make(1.f), ff_mulf(ff_mul(ff_mul(dt, gamma), ff_mul(iS, iS)), 0.5f));
-  ff rho, r_prev_new;
+  o.E1 = ff_add(ff_mul(ffp(P.hd_ff), ff_sub(ff_mul(ffp(P.qbeta_ff), s2), s1)), ffp(P.Cvol_ff));
+  o.S = ff_sqrt(o.E1);
+  const ff iS = ff_div(ff_make(1.f), o.S);
+  o.gamma = ff_mul(vol, gs); o.eta = ff_mul(vol, es); o.theta = ff_mul(vol, ts);
+  o.denom = ff_sub(ff_make(1.f), ff_mulf(ff_mul(ff_mul(dt, o.gamma), ff_mul(iS, iS)), 0.5f));
+  ff rho;
   if (bdf1) {
-    rho = ff_sub(S, ff_mulf(ff_mul(theta, iS), 0.5f));
-    r_prev_new = S;
+    rho = ff_sub(o.S, ff_mulf(ff_mul(o.theta, iS), 0.5f));
+    o.r_prev_new = o.S;
   } else {
-    const ff r1 = ffp(sc->r1f), r0 = ffp(sc->r0f);
-    rho = ff_div(ff_sub(ff_sub(ff_mulf(r1, 4.f), r0), ff_mul(theta, iS)), ff_make(3.f));
-    r_prev_new = r1;
+    rho = ff_div(ff_sub(ff_sub(ff_mulf(rin.r1, 4.f), rin.r0), ff_mul(o.theta, iS)), ff_make(3.f));
+    o.r_prev_new = rin.r1;
   }
-  const ff LHS = ff_div(ff_add(ff_mul(ff_mul(ff_mul(dt, rho), gamma), iS), eta), denom);
-  const ff r_new = ff_add(rho, ff_mulf(ff_mul(LHS, iS), 0.5f));
-  const ff xi = ff_mul(r_new, iS);
-  const bool ok = ff_isfinite(E1) && E1.hi > 0.f && ff_isfinite(gamma) && ff_isfinite(eta) &&
-                  ff_isfinite(theta) && denom.hi > 0.f && ff_isfinite(r_new);
-  ffs(sc->E1f, E1); ffs(sc->Sf, S); ffs(sc->gammaf, gamma); ffs(sc->etaf, eta); ffs(sc->thetaf, theta);
-  ffs(sc->denomf, denom); ffs(sc->LHSf, LHS); ffs(sc->xif, xi);
-  if (!ok) { sc->status = DEV_NONFINITE; return; }
-  ffs(sc->r0f, r_prev_new);
-  ffs(sc->r1f, r_new);
-  const ff alpha = ff_mul(ff_mul(dt, r_new), iS);
-  sc->alpha_f = alpha.hi;
-  sc->p = newest;
-  sc->pending = bdf1 ? PEND_BDF1 : PEND_BDF2;
+  o.LHS = ff_div(ff_add(ff_mul(ff_mul(ff_mul(dt, rho), o.gamma), iS), o.eta), o.denom);
+  o.r_new = ff_add(rho, ff_mulf(ff_mul(o.LHS, iS), 0.5f));
+  o.xi = ff_mul(o.r_new, iS);
+  o.alpha = ff_mul(ff_mul(dt, o.r_new), iS).hi;
+  o.ok = ff_isfinite(o.E1) && o.E1.hi > 0.f && ff_isfinite(o.gamma) && ff_isfinite(o.eta) &&
+         ff_isfinite(o.theta) && o.denom.hi > 0.f && ff_isfinite(o.r_new);
+  return o;
+}
+
+// Write a solve into the record: r shifts, p and pending as given.
+__device__ inline void sav_commit(SavScal* sc, const SolveOut<double>& o, int p_new, int pending) {
+  sc->E1 = o.E1; sc->S = o.S; sc->gamma = o.gamma; sc->eta = o.eta; sc->theta = o.theta;
+  sc->denom = o.denom; sc->LHS = o.LHS; sc->xi = o.xi;
+  if (!o.ok) { sc->status = DEV_NONFINITE; return; }
+  sc->r0 = o.r_prev_new;
+  sc->r1 = o.r_new;
+  sc->alpha = o.alpha;
+  sc->p = p_new;
+  sc->pending = pending;
   sc->nsteps += 1;
+}
+__device__ inline void sav_commit(SavScal* sc, const SolveOut<float>& o, int p_new, int pending) {
+  ffs(sc->E1f, o.E1); ffs(sc->Sf, o.S); ffs(sc->gammaf, o.gamma); ffs(sc->etaf, o.eta); ffs(sc->thetaf, o.theta);
+  ffs(sc->denomf, o.denom); ffs(sc->LHSf, o.LHS); ffs(sc->xif, o.xi);
+  if (!o.ok) { sc->status = DEV_NONFINITE; return; }
+  ffs(sc->r0f, o.r_prev_new);
+  ffs(sc->r1f, o.r_new);
+  sc->alpha_f = o.alpha;
+  sc->p = p_new;
+  sc->pending = pending;
+  sc->nsteps += 1;
+}
+
+// Lazy-update form used by the separate forward column pass: newest holds
+// phi^n, the update stays pending (materialised later into slot 1-newest).
+template <typename R>
+__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const typename Red<R>::acc* q, bool bdf1,
+                                        int newest) {
+  const SolveOut<R> o = sav_solve(P, q, bdf1, RIn<R>(sc));
+  sav_commit(sc, o, newest, bdf1 ? PEND_BDF1 : PEND_BDF2);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +470,7 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
   constexpr int NTH = NF * CT * T;
-  constexpr int CTP = CT + 1;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
   constexpr int IT = N * CT / NTH;
   constexpr int SEQ = sp_len(N);
@@ -566,6 +600,209 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
           *counter = 0u;
         }
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused column pass: the end of step n and the start of step n+1 for one tile
+// of CT kx columns, with one grid-wide barrier in between.
+//   A: forward DFT in y of W (the row pass output), N_hat = -i k~ . W_hat
+//      (kept in registers), partial sums of gamma, eta, theta with the state
+//      (phi^n, phi^{n-1}) held in registers.
+//   barrier: every block publishes its partial sums and arrives; the last
+//      block reduces all of them and solves the scalar system for r^{n+1}
+//      and alpha = dt r^{n+1} / sqrt(E_1); the others wait (bounded).
+//   B: phi^{n+1} = alpha A^{-1} Delta N_hat + A^{-1} v (eq. solver-6) written
+//      over phi^{n-1}, phi* = 2 phi^{n+1} - phi^n, i k~ phi*, inverse DFT in y
+//      into W for the next row pass.
+// Launched cooperatively (all blocks co-resident).
+// ---------------------------------------------------------------------------
+constexpr long long kSpinLimit = 1ll << 22;  // x ~100 ns sleep: about half a second
+
+template <typename R, int N, int E, int CT, bool BDF1>
+__global__ void __launch_bounds__(2 * CT * (N / E))
+k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
+              double* __restrict__ partG, const double* __restrict__ partE, int nE, SavScal* __restrict__ sc,
+              unsigned long long* __restrict__ sync64, const C_t<R>* __restrict__ tw) {
+  using C = C_t<R>;
+  using RD = Red<R>;
+  constexpr int T = fft_shape<N, E>::T;
+  constexpr int NTH = 2 * CT * T;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
+  constexpr int NH = N / 2 + 1;
+  constexpr int IT = N * CT / NTH;
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  __shared__ typename RD::acc red[32];
+  __shared__ typename RD::acc red5[5][32];
+  __shared__ typename RD::acc qres[5];
+  __shared__ int bar_ok;
+
+  if (sc->status != DEV_OK) return;
+  const PC<R> pc(P);
+  const int p = sc->p;  // phi^n in slot p, phi^{n-1} in slot 1-p (nothing pending)
+  const RIn<R> rin(sc);  // read before arriving at the barrier (block 0 rewrites them after it)
+  C* scur = S.at(p);
+  C* sold = S.at(1 - p);
+  const int kx0 = blockIdx.x * CT;
+
+  // ---- A: gather W tile and the state tile
+  C vn[IT], vo[IT], nh[IT];
+  {
+    C va[IT], vb[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int y = idx / CT, kx = kx0 + idx % CT;
+      va[it] = mk<C>(0, 0);
+      vb[it] = mk<C>(0, 0);
+      vn[it] = mk<C>(0, 0);
+      vo[it] = mk<C>(0, 0);
+      if (kx < NH) {
+        const size_t off = (size_t)y * NH + kx;  // y doubles as ky: same tile mapping
+        va[it] = W0[off];
+        vb[it] = W1[off];
+        vn[it] = scur[off];
+        vo[it] = sold[off];
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int y = idx / CT, c = idx % CT;
+      sm[sp(y) * CTP + c] = va[it];
+      sm[SEQ * CTP + sp(y) * CTP + c] = vb[it];
+    }
+  }
+  __syncthreads();
+  {
+    const int q = threadIdx.x / T, lane = threadIdx.x % T;
+    const int f = q / CT, c = q % CT;
+    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
+  }
+  __syncthreads();
+  const R c0 = BDF1 ? (R)1 : (R)1.5;
+  typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
+    nh[it] = mk<C>(0, 0);
+    if (kx >= NH) continue;
+    const C wx = sm[sp(ky) * CTP + c], wy = sm[SEQ * CTP + sp(ky) * CTP + c];
+    const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
+    const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
+    nh[it] = mk<C>(uy, -ux);  // N_hat = -i (k~_x W_x + k~_y W_y)
+    const R K2 = sym_K2<R>(kx, ky, N, pc);
+    const R invA = sym_invA<R>(K2, c0, pc);
+    C v;
+    if (BDF1) v = vn[it];
+    else v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+    const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
+    const R n2 = nh[it].x * nh[it].x + nh[it].y * nh[it].y;
+    const R nv = nh[it].x * v.x + nh[it].y * v.y;
+    ag = RD::add(ag, w * (-K2 * invA) * n2);
+    ae = RD::add(ae, w * nv * invA);
+    at = RD::add(at, w * nv);
+  }
+  const typename RD::acc tg = block_red<R>(ag, red);
+  const typename RD::acc te = block_red<R>(ae, red);
+  const typename RD::acc tt = block_red<R>(at, red);
+
+  // ---- grid barrier: publish the partial sums, arrive, wait for all blocks
+  // (bounded); then every block reduces all partial sums in the same fixed
+  // order and solves the scalar system itself (identical results), and block
+  // 0 alone writes the record. sync64[0] counts arrivals monotonically, so it
+  // never needs a reset: this launch's target is the next multiple of the grid.
+  if (threadIdx.x == 0) {
+    typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
+    ps[blockIdx.x] = tg;
+    ps[gridDim.x + blockIdx.x] = te;
+    ps[2 * gridDim.x + blockIdx.x] = tt;
+    __threadfence();
+    const unsigned long long prev = atomicAdd(sync64, 1ull);
+    const unsigned long long target = (prev / gridDim.x + 1ull) * gridDim.x;
+    int ok = 1;
+    long long it = 0;
+    while (*((volatile unsigned long long*)sync64) < target) {
+      if (++it > kSpinLimit) {
+        atomicExch(&sc->status, (int)DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    bar_ok = ok;
+  }
+  __syncthreads();
+  if (!bar_ok) return;
+  {
+    using ST = typename RD::store;
+    const ST* pe = reinterpret_cast<const ST*>(partE);
+    const ST* pg = reinterpret_cast<const ST*>(partG);
+    const ST* arr[5] = {pe, pe + nE, pg, pg + gridDim.x, pg + 2 * gridDim.x};
+    const int cnt[5] = {nE, nE, (int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
+    block_red_arrays<R, 5>(arr, cnt, qres, red5);
+  }
+  __shared__ R alpha_s;
+  __shared__ int solve_ok;
+  if (threadIdx.x == 0) {
+    const SolveOut<R> o = sav_solve(P, qres, BDF1, rin);
+    alpha_s = (R)o.alpha;
+    solve_ok = o.ok;
+    if (blockIdx.x == 0) sav_commit(sc, o, 1 - p, PEND_NONE);
+  }
+  __syncthreads();
+  if (!solve_ok) return;
+  const R al = alpha_s;
+
+  // ---- B: update, next extrapolation and its gradients, inverse DFT in y
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
+    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
+    if (kx < NH) {
+      const size_t off = (size_t)ky * NH + kx;
+      const C cur = vn[it];
+      C nw;
+      if (off == 0) {
+        // zero mode: A_0 = c0 and Delta kills N; BDF1 keeps phi_0, BDF2 gives a + (a - b)/3
+        const double z = BDF1 ? sc->zm[p] : zero_mode_update(sc->zm[p], sc->zm[1 - p]);
+        sc->zm[1 - p] = z;
+        nw = mk<C>((R)z, (R)0);
+      } else {
+        const R K2 = sym_K2<R>(kx, ky, N, pc);
+        if (BDF1) nw = bdf1_update<C, R>(cur, nh[it], K2, sym_invA<R>(K2, (R)1, pc), al);
+        else nw = bdf2_update<C, R>(cur, vo[it], nh[it], K2, sym_invA<R>(K2, (R)1.5, pc), al);
+      }
+      sold[off] = nw;  // phi^{n+1} over phi^{n-1}
+      const C ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
+      const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
+      g0 = mk<C>(-ktx * ph.y, ktx * ph.x);
+      g1 = mk<C>(-kty * ph.y, kty * ph.x);
+    }
+    sm[sp(ky) * CTP + c] = g0;
+    sm[SEQ * CTP + sp(ky) * CTP + c] = g1;
+  }
+  __syncthreads();
+  {
+    const int q = threadIdx.x / T, lane = threadIdx.x % T;
+    const int f = q / CT, c = q % CT;
+    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int y = idx / CT, c = idx % CT, kx = kx0 + c;
+    if (kx < NH) {
+      W0[(size_t)y * NH + kx] = sm[sp(y) * CTP + c];
+      W1[(size_t)y * NH + kx] = sm[SEQ * CTP + sp(y) * CTP + c];
     }
   }
 }

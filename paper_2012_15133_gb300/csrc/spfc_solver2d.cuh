@@ -23,13 +23,18 @@ namespace spfc {
     }                                                                              \
   } while (0)
 
-// Launch shape per grid size: E values per FFT lane (T = N/E lanes per
-// sequence), CT kx columns per column-pass block, RPC rows per row-pass block.
-// Every block fills whole warps.
-template <int N> struct Shape2D {
-  static constexpr int E = 8;
+// Launch shape ("schedule") per grid size: E values per FFT lane (T = N/E
+// lanes per sequence), CT kx columns per column-pass block, RPC rows per
+// row-pass block. Every block fills whole warps. Schedule 0 is the default;
+// the others are alternatives for N >= 128 that the autotuner times:
+//   1: one column per block (twice the blocks), 2: 4 values per lane
+//   (twice the threads per sequence), 3: 16 values per lane, 4 columns.
+template <int N, int SCHED = 0> struct Shape2D {
+  static constexpr int E = (SCHED == 2) ? 4 : ((SCHED == 3) ? 16 : 8);
   static constexpr int T = N / E;
-  static constexpr int CT = (N >= 256) ? 2 : ((32 / T > 4) ? 32 / T : 4);
+  static constexpr int CT0 = (N >= 256) ? 2 : ((32 / T > 4) ? 32 / T : 4);
+  static constexpr int CT1 = (32 / T > 1) ? 32 / T : 1;  // fewest columns that fill a warp
+  static constexpr int CT = (SCHED == 1) ? CT1 : ((SCHED == 3) ? 4 : CT0);
   static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
   static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
   static_assert(sizeof(Red<float>::store) == sizeof(double) && sizeof(Red<double>::store) == sizeof(double),
@@ -40,19 +45,31 @@ template <int N> struct Shape2D {
 
 // Kernel launch, optionally with programmatic stream serialization (the
 // kernel may begin while its predecessor finishes; it waits with pdl_wait).
+// Cooperative launch (coop) guarantees that all blocks are co-resident, as
+// the grid barrier of the fused column pass requires; it fails instead of
+// deadlocking when they cannot be.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
-                            Args... args) {
+                            bool coop, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (coop) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
@@ -66,10 +83,10 @@ template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
   }
 }
 
-template <typename R, int N>
+template <typename R, int N, int SCHED = 0>
 class Solver2D final : public SolverBase {
   using C = C_t<R>;
-  using SH = Shape2D<N>;
+  using SH = Shape2D<N, SCHED>;
   static constexpr int NH = N / 2 + 1;
   static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T, E = SH::E;
   static constexpr int GCOL = (NH + CT - 1) / CT;
@@ -108,7 +125,8 @@ class Solver2D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
-    if (e == cudaSuccess) e = al((void**)&counter_, sizeof(unsigned));
+    if (e == cudaSuccess) e = al((void**)&counter_, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = al((void**)&sync64_, sizeof(unsigned long long));
     if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -117,7 +135,8 @@ class Solver2D final : public SolverBase {
     std::vector<C> tw;
     host_twiddles<R>(tw);
     SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
-    SPFC_CK(cudaMemset(counter_, 0, sizeof(unsigned)));
+    SPFC_CK(cudaMemset(counter_, 0, 4 * sizeof(unsigned)));
+    SPFC_CK(cudaMemset(sync64_, 0, sizeof(unsigned long long)));
     SavScal z{};
     SPFC_CK(cudaMemcpy(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(S_.s[0], 0, sb));
@@ -135,6 +154,20 @@ class Solver2D final : public SolverBase {
     SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_BDF1>, smem_col(2)));
     SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_NHAT>, smem_col(2)));
     SPFC_CK(set_smem(k2d_col_fwd<R, N, E, CT, CF_TO_STATE>, smem_col(1)));
+    SPFC_CK(set_smem(k2d_col_fused<R, N, E, CT, false>, smem_col(2)));
+    SPFC_CK(set_smem(k2d_col_fused<R, N, E, CT, true>, smem_col(2)));
+    {
+      // the fused pass needs all of its blocks co-resident
+      int dev = 0, nsm = 0, per = 0;
+      SPFC_CK(cudaGetDevice(&dev));
+      SPFC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_col_fused<R, N, E, CT, false>, 2 * CT * T,
+                                                             smem_col(2)));
+      if (per * nsm < GCOL) {
+        err = "the fused column pass does not fit co-resident on this GPU";
+        return 3;
+      }
+    }
     SPFC_CK(cudaStreamCreateWithFlags(&cap_st_, cudaStreamNonBlocking));
     return 0;
   }
@@ -144,7 +177,8 @@ class Solver2D final : public SolverBase {
     if (g16_) cudaGraphExecDestroy(g16_);
     for (auto ev : evpool_) cudaEventDestroy(ev);
     if (cap_st_) cudaStreamDestroy(cap_st_);
-    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], real_, partE_, partG_, partN_, partS_, sc_, counter_, tw_};
+    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], real_, partE_, partG_, partN_, partS_, sc_, counter_,
+                    sync64_, tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -155,11 +189,13 @@ class Solver2D final : public SolverBase {
   int init(const double* phi0, bool on_device, int mode) override {
     int rc = load_field(phi0, on_device, /*slot_rel=*/0, /*reset=*/true);
     if (rc) return rc;
-    if (mode == 0) {  // BDF1
+    if (mode == 0) {  // BDF1: the first step, which also prepares W for the second
       rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
       rc = launch_row(RW_NONLIN); if (rc) return rc;
-      rc = launch_col_fwd(CF_BDF1, 0); if (rc) return rc;
-      rc = finalize(); if (rc) return rc;
+      rc = launch_fused(true); if (rc) return rc;
+      w_ready_ = true;
+      inited = true;
+      return sync();
     } else if (mode == 1) {  // ghost
       rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
       rc = launch_row(RW_NONLIN); if (rc) return rc;
@@ -180,6 +216,7 @@ class Solver2D final : public SolverBase {
       err = "unknown start mode";
       return 1;
     }
+    w_ready_ = false;
     inited = true;
     return 0;
   }
@@ -191,6 +228,7 @@ class Solver2D final : public SolverBase {
     if (rc) return rc;
     rc = scalar_op(SO_SET_R, nullptr, 0, nullptr, 0, 0, r, r_prev);
     if (rc) return rc;
+    w_ready_ = false;
     inited = true;
     return 0;
   }
@@ -205,12 +243,19 @@ class Solver2D final : public SolverBase {
     rc = launch_row(RW_ENERGY); if (rc) return rc;
     rc = scalar_op(SO_R_NEWEST, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
     rc = scalar_op(SO_R_PREV, partE_, nE_, nullptr, 0, 0); if (rc) return rc;
+    w_ready_ = false;
     return 0;
   }
 
   // ---- stepping ------------------------------------------------------------
   int step(long long n) override {
     if (n <= 0) return 0;
+    if (!w_ready_) {
+      // W <- inverse DFT in y of i k~ (2 phi^n - phi^{n-1}): the first half of a step
+      int rc = finalize(); if (rc) return rc;
+      rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
+      w_ready_ = true;
+    }
     if (timing_) {
       for (long long i = 0; i < n; ++i) {
         int rc = timed_step();
@@ -229,6 +274,7 @@ class Solver2D final : public SolverBase {
   // ---- diagnostics ----------------------------------------------------------
   int energy(double* E_orig, double* E_mod, double* E_breve) override {
     int rc = finalize(); if (rc) return rc;
+    w_ready_ = false;  // W is used as scratch below
     k2d_norms<R><<<gpw_, PW_THREADS, 0, st_>>>(P, S_, sc_, partN_);
     SPFC_CK(cudaGetLastError());
     rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
@@ -258,6 +304,7 @@ class Solver2D final : public SolverBase {
 
   int get_field(double* out, bool on_device, int which) override {
     int rc = finalize(); if (rc) return rc;
+    w_ready_ = false;  // W is used as scratch below
     rc = launch_col_inv(CI_FIELD, which); if (rc) return rc;
     rc = launch_row(RW_OUT_REAL); if (rc) return rc;
     const size_t bytes = (size_t)N * N * sizeof(double);
@@ -291,6 +338,7 @@ class Solver2D final : public SolverBase {
 
   int restore(const std::string& blob) override {
     if (blob.size() != sizeof(SavScal) + 2 * spec_bytes_) { err = "checkpoint size mismatch"; return 1; }
+    w_ready_ = false;
     SavScal h;
     std::memcpy(&h, blob.data(), sizeof(SavScal));
     const int p = h.p;
@@ -324,9 +372,9 @@ class Solver2D final : public SolverBase {
     }
     trecs_.clear();
     evnext_ = 0;
-    kt->names = {"col_inv", "row", "col_fwd"};
-    kt->launches.assign(tcount_, tcount_ + 3);
-    kt->ms.assign(tms_, tms_ + 3);
+    kt->names = {"row", "col_fused"};
+    kt->launches.assign(tcount_, tcount_ + 2);
+    kt->ms.assign(tms_, tms_ + 2);
     for (int i = 0; i < 3; ++i) { tcount_[i] = 0; tms_[i] = 0.0; }
     return 0;
   }
@@ -335,13 +383,14 @@ class Solver2D final : public SolverBase {
   template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
-  static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * (CT + 1) * sizeof(C); }
+  static constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * CTP * sizeof(C); }
   static constexpr size_t smem_row() { return (size_t)RPC * (sp_len(N) + 1) * sizeof(C); }
 
   int launch_col_inv(int mode, int which) {
     switch (mode) {
       case CI_STEP:
-        SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, P, S_, Nhat_,
+        SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, false, P, S_, Nhat_,
                          W_[0], W_[1], sc_, tw_, which));
         break;
       case CI_GRAD:
@@ -356,7 +405,7 @@ class Solver2D final : public SolverBase {
   int launch_row(int mode) {
     switch (mode) {
       case RW_NONLIN:
-        SPFC_CK(launch_k(k2d_row<R, N, E, RPC, RW_NONLIN>, GROW, RPC * T, smem_row(), st_, pdl_, P, W_[0], W_[1],
+        SPFC_CK(launch_k(k2d_row<R, N, E, RPC, RW_NONLIN>, GROW, RPC * T, smem_row(), st_, pdl_, false, P, W_[0], W_[1],
                          partE_, sc_, tw_, real_));
         break;
       case RW_ENERGY:
@@ -374,7 +423,7 @@ class Solver2D final : public SolverBase {
   int launch_col_fwd(int mode, int target) {
     switch (mode) {
       case CF_BDF2:
-        SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, P, S_, W_[0],
+        SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, false, P, S_, W_[0],
                          W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target));
         break;
       case CF_BDF1:
@@ -446,10 +495,21 @@ class Solver2D final : public SolverBase {
     return 0;
   }
 
+  // one step with W prepared: row pass, then the fused column pass (which
+  // prepares W for the next step)
   int launch_step_kernels() {
-    int rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
-    rc = launch_row(RW_NONLIN); if (rc) return rc;
-    return launch_col_fwd(CF_BDF2, 0);
+    int rc = launch_row(RW_NONLIN); if (rc) return rc;
+    return launch_fused(false);
+  }
+
+  int launch_fused(bool bdf1) {
+    if (bdf1)
+      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, true>, GCOL, 2 * CT * T, smem_col(2), st_, false, true, P, S_,
+                       W_[0], W_[1], partG_, partE_, nE_, sc_, sync64_, tw_));
+    else
+      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, false>, GCOL, 2 * CT * T, smem_col(2), st_, false, true, P, S_,
+                       W_[0], W_[1], partG_, partE_, nE_, sc_, sync64_, tw_));
+    return 0;
   }
 
   void drop_graphs() {
@@ -493,18 +553,15 @@ class Solver2D final : public SolverBase {
   }
 
   int timed_step() {
-    int e0, e1, e2, e3, rc;
-    if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2)) || (rc = ev(&e3))) return rc;
+    int e0, e1, e2, rc;
+    if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2))) return rc;
     SPFC_CK(cudaEventRecord(evpool_[e0], st_));
-    if ((rc = launch_col_inv(CI_STEP, 0))) return rc;
-    SPFC_CK(cudaEventRecord(evpool_[e1], st_));
     if ((rc = launch_row(RW_NONLIN))) return rc;
+    SPFC_CK(cudaEventRecord(evpool_[e1], st_));
+    if ((rc = launch_fused(false))) return rc;
     SPFC_CK(cudaEventRecord(evpool_[e2], st_));
-    if ((rc = launch_col_fwd(CF_BDF2, 0))) return rc;
-    SPFC_CK(cudaEventRecord(evpool_[e3], st_));
     trecs_.push_back({0, e0, e1});
     trecs_.push_back({1, e1, e2});
-    trecs_.push_back({2, e2, e3});
     return 0;
   }
 
@@ -518,11 +575,13 @@ class Solver2D final : public SolverBase {
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
   SavScal* sc_ = nullptr;
   unsigned* counter_ = nullptr;
+  unsigned long long* sync64_ = nullptr;  // arrival counter of the fused pass's grid barrier
   C* tw_ = nullptr;
   int gpw_ = 0, nE_ = 0, nG_ = 0;
   size_t spec_bytes_ = 0, total_ = 0;
   cudaGraphExec_t g1_ = nullptr, g16_ = nullptr;
   bool timing_ = false;
+  bool w_ready_ = false;            // W holds the first half of the next step
   bool pdl_ = false;                // launch the step kernels with programmatic serialization
   bool use_pdl_ = false;
   std::vector<cudaEvent_t> evpool_;
@@ -532,37 +591,65 @@ class Solver2D final : public SolverBase {
   double tms_[3] = {0, 0, 0};
 };
 
-template <typename R>
-SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
-  SolverBase* s = nullptr;
-  switch (P.N) {
-    case 16: s = new Solver2D<R, 16>(P, st); break;
-    case 32: s = new Solver2D<R, 32>(P, st); break;
-    case 64: s = new Solver2D<R, 64>(P, st); break;
-    case 128: s = new Solver2D<R, 128>(P, st); break;
-    case 256: s = new Solver2D<R, 256>(P, st); break;
-    case 512: s = new Solver2D<R, 512>(P, st); break;
-    default:
-      *status = 1;
-      *err = "2D grid size must be one of 16, 32, 64, 128, 256, 512";
-      return nullptr;
-  }
-  int rc = 0;
-  switch (P.N) {
-    case 16: rc = static_cast<Solver2D<R, 16>*>(s)->setup(); break;
-    case 32: rc = static_cast<Solver2D<R, 32>*>(s)->setup(); break;
-    case 64: rc = static_cast<Solver2D<R, 64>*>(s)->setup(); break;
-    case 128: rc = static_cast<Solver2D<R, 128>*>(s)->setup(); break;
-    case 256: rc = static_cast<Solver2D<R, 256>*>(s)->setup(); break;
-    case 512: rc = static_cast<Solver2D<R, 512>*>(s)->setup(); break;
-  }
+// Number of launch schedules compiled for a 2D grid size.
+inline int num_schedules_2d(int N) { return (N >= 256) ? 4 : ((N == 128) ? 2 : 1); }
+
+template <typename R, int N, int SCHED>
+SolverBase* new_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
+  auto* s = new Solver2D<R, N, SCHED>(P, st);
+  int rc = s->setup();
   if (rc) {
     *status = rc;
     *err = s->err;
     delete s;
     return nullptr;
   }
+  s->schedule = SCHED;
   return s;
+}
+
+// Factory for one grid size N >= 256 (each in its own translation unit so
+// that the build compiles them in parallel).
+template <typename R, int N>
+SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err) {
+  switch (schedule) {
+    case 1: return new_solver_2d<R, N, 1>(P, st, status, err);
+    case 2: return new_solver_2d<R, N, 2>(P, st, status, err);
+    case 3: return new_solver_2d<R, N, 3>(P, st, status, err);
+    default: return new_solver_2d<R, N, 0>(P, st, status, err);
+  }
+}
+
+SolverBase* make_solver_2d_f64_256(const Params&, cudaStream_t, int, int*, std::string*);
+SolverBase* make_solver_2d_f64_512(const Params&, cudaStream_t, int, int*, std::string*);
+SolverBase* make_solver_2d_f32_256(const Params&, cudaStream_t, int, int*, std::string*);
+SolverBase* make_solver_2d_f32_512(const Params&, cudaStream_t, int, int*, std::string*);
+
+template <typename R>
+SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err) {
+  const bool known = P.N == 16 || P.N == 32 || P.N == 64 || P.N == 128 || P.N == 256 || P.N == 512;
+  if (!known) {
+    *status = 1;
+    *err = "2D grid size must be one of 16, 32, 64, 128, 256, 512";
+    return nullptr;
+  }
+  if (schedule < 0 || schedule >= num_schedules_2d(P.N)) {
+    *status = 1;
+    *err = "schedule index out of range for this grid size";
+    return nullptr;
+  }
+  constexpr bool F64 = sizeof(R) == 8;
+  switch (P.N) {
+    case 16: return new_solver_2d<R, 16, 0>(P, st, status, err);
+    case 32: return new_solver_2d<R, 32, 0>(P, st, status, err);
+    case 64: return new_solver_2d<R, 64, 0>(P, st, status, err);
+    case 128:
+      return schedule == 1 ? new_solver_2d<R, 128, 1>(P, st, status, err) : new_solver_2d<R, 128, 0>(P, st, status, err);
+    case 256:
+      return F64 ? make_solver_2d_f64_256(P, st, schedule, status, err) : make_solver_2d_f32_256(P, st, schedule, status, err);
+    default:
+      return F64 ? make_solver_2d_f64_512(P, st, schedule, status, err) : make_solver_2d_f32_512(P, st, schedule, status, err);
+  }
 }
 
 }  // namespace spfc

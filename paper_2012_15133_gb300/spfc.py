@@ -28,6 +28,9 @@ _DP = ct.POINTER(ct.c_double)
 # name -> (restype, argtypes), one entry per function of include/spfc.h
 _SIGS = {
     "spfc_create": (_I, [_I, ct.POINTER(_I), _DP, _D, _D, _D, _I, _P, ct.POINTER(_P)]),
+    "spfc_num_schedules": (_I, [_I, _I]),
+    "spfc_create_scheduled": (_I, [_I, ct.POINTER(_I), _DP, _D, _D, _D, _I, _P, _I, ct.POINTER(_P)]),
+    "spfc_schedule": (_I, [_P]),
     "spfc_init": (_I, [_P, _P, _I, _I]),
     "spfc_set_state": (_I, [_P, _P, _P, _D, _D, _I]),
     "spfc_step": (_I, [_P, ct.c_int64]),
@@ -108,6 +111,10 @@ def field_energy_noalloc(phi, L, eps, beta, stream=None):
     return out[0], out[1], out[2]
 
 
+def num_schedules(d, n):
+    return int(load_library().spfc_num_schedules(int(d), int(n)))
+
+
 class Solver:
     """One SPFC run on the current CUDA device (see include/spfc.h).
 
@@ -115,7 +122,7 @@ class Solver:
     axis); device arrays are contiguous float64 torch CUDA tensors.
     """
 
-    def __init__(self, d, n, L, eps, beta, dt, precision="fp64", stream=None):
+    def __init__(self, d, n, L, eps, beta, dt, precision="fp64", stream=None, schedule=None):
         self._lib = load_library()
         self.d = int(d)
         n = [int(n)] * self.d if np.isscalar(n) else [int(v) for v in n]
@@ -131,9 +138,12 @@ class Solver:
             sp = ct.c_void_p(stream.cuda_stream)
         self._stream = sp
         h = ct.c_void_p()
-        rc = self._lib.spfc_create(self.d, (ct.c_int * self.d)(*n), (ct.c_double * self.d)(*L),
-                                   float(eps), float(beta), float(dt), self.precision, sp,
-                                   ct.byref(h))
+        if schedule == "auto":
+            from .autotune import lookup
+            schedule = lookup(self.d, n[0], self.precision)
+        rc = self._lib.spfc_create_scheduled(self.d, (ct.c_int * self.d)(*n), (ct.c_double * self.d)(*L),
+                                             float(eps), float(beta), float(dt), self.precision, sp,
+                                             -1 if schedule is None else int(schedule), ct.byref(h))
         if rc != 0:
             raise SPFCError(rc, self._lib.spfc_last_error(None).decode())
         self._h = h
@@ -225,6 +235,10 @@ class Solver:
         if n < 0:
             self._check(n)
         return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+    @property
+    def schedule(self):
+        return int(self._lib.spfc_schedule(self._h))
 
     def device_bytes(self):
         return int(self._lib.spfc_device_bytes(self._h))
