@@ -227,10 +227,16 @@ def run_ours(args):
     avg_s = ms / nl * 1e-3
     achieved = passes[dom] * SB / avg_s / 1e9
     peak, peak_kind = _peaks()
+    # DRAM bytes (read + write) per launch of each kernel from the committed ncu
+    # capture (profiles/step2d_512_kernels_ncu_full.md); set to None whenever the
+    # kernel changes after the capture
+    traffic_ncu = {("fp32", "col_fused"): 3232000, ("fp32", "row"): 2136064,
+                   ("fp64", "col_fused"): 6408704, ("fp64", "row"): 4272640}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,
-            "traffic": None,
+            "traffic": traffic_ncu.get((args.precision, dom)),
+            "note": "per-kernel CUDA-event times include each kernel's launch latency (launched one by one)",
             "kernels": {k: {"launches": v[0], "avg_us": v[1] / v[0] * 1e3,
                             "share": v[1] / sum(x[1] for x in kt.values())} for k, v in kt.items()}}
 
