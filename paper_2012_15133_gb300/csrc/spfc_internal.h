@@ -88,5 +88,7 @@ inline void scal_from_ff(SavScal* h) {
 SolverBase* make_solver_f64(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err);
 SolverBase* make_solver_f32(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err);
 int num_schedules(int d, int N);
+SolverBase* make_solver_3d_f64(const Params& P, cudaStream_t st, int* status, std::string* err);
+SolverBase* make_solver_3d_f32(const Params& P, cudaStream_t st, int* status, std::string* err);
 
 }  // namespace spfc

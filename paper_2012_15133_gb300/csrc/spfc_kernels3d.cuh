@@ -1,0 +1,582 @@
+// 3D kernels of the BDF2-SAV Fourier pseudo-spectral step (Sec. 2.2-2.3).
+//
+// Layout: real fields phi[z][y][x] (x fastest); half spectra F[kz][ky][kx],
+// kx in [0, N/2] (NH = N/2 + 1 entries per row), PS = N * NH entries per plane.
+// Work arrays W0, W1, W2 hold data that is transformed along some axes only.
+//
+// One step (W prepared by the previous step: the y- and z-inverse transforms
+// of i k~_d phi*):
+//   row    : per pair of x-rows, inverse DFT in x of the three gradients
+//            (G_x + i G_y of each row, G_z of both rows packed as one complex
+//            sequence), s = |grad phi*|^2, E_1 partial sums, w = (beta s - 2) g,
+//            forward DFTs, split back into W_x, W_y, W_z;
+//   y-fwd  : forward DFT in y; Q1 = k~_x W_x + k~_y W_y, Q2 = W_z;
+//   z-fwd  : forward DFT in z; N_hat = -i (Q1 + k~_z Q2); gamma, eta, theta partial sums;
+//   scalar : one block reduces all partial sums and solves for r^{n+1} (eqs. solver-2, -4);
+//   z-inv  : phi^{n+1} = alpha A^{-1} Delta N_hat + A^{-1} v (eq. solver-6), phi* =
+//            2 phi^{n+1} - phi^n, inverse DFT in z of phi* and of i k~_z phi*;
+//   y-inv  : inverse DFT in y of i k~_y F, F and G_z; W_x = i k~_x (.) of F's.
+#pragma once
+
+#include "spfc_kernels2d.cuh"
+
+namespace spfc {
+
+template <typename R>
+__device__ __forceinline__ R sym_K2_3d(int kx, int ky, int kz, int N, const PC<R>& c) {
+  const R kxx = rn_mul((R)kx, c.kfx);
+  const R kyy = rn_mul((R)((ky <= N / 2) ? ky : ky - N), c.kfy);
+  const R kzz = rn_mul((R)((kz <= N / 2) ? kz : kz - N), c.kfz);
+  return rn_fma(kxx, kxx, rn_fma(kyy, kyy, rn_mul(kzz, kzz)));
+}
+
+enum Y3Mode : int { Y3_FWD = 0, Y3_INV = 1, Y3_INV_FIELD = 2, Y3_FWD_FIELD = 3 };
+enum Z3Mode : int { Z3F_BDF2 = 0, Z3F_BDF1 = 1, Z3F_NHAT = 2, Z3F_TO_STATE = 3 };
+enum Z3IMode : int { Z3I_STEP = 0, Z3I_STEP_BDF1 = 1, Z3I_PREP = 2, Z3I_GRAD = 3, Z3I_FIELD = 4 };
+
+template <int MODE> struct y3_nf { static constexpr int in = (MODE == Y3_FWD) ? 3 : ((MODE == Y3_INV) ? 2 : 1);
+                                   static constexpr int fft = (MODE == Y3_FWD || MODE == Y3_INV) ? 3 : 1; };
+
+// ---------------------------------------------------------------------------
+// y pass. Grid (ceil(NH/CT), N): tile of CT kx columns in plane z = blockIdx.y.
+// ---------------------------------------------------------------------------
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(y3_nf<MODE>::fft * CT * (N / E))
+k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+          const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
+  using C = C_t<R>;
+  constexpr int T = fft_shape<N, E>::T;
+  constexpr int NF = y3_nf<MODE>::fft;
+  constexpr int NTH = NF * CT * T;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int NH = N / 2 + 1;
+  constexpr int IT = (N * CT + NTH - 1) / NTH;  // three sequences per column: N*CT need not divide NTH
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0, "tile must fill whole warps");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  if (sc->status != DEV_OK) return;
+  const PC<R> pc(P);
+  const int kx0 = blockIdx.x * CT;
+  const size_t base = (size_t)blockIdx.y * N * NH;
+
+  // load: FWD reads U_x, U_y, U_z; INV reads F, G_z and forms (i k~_y F, F, G_z);
+  // the field modes read one array
+  C va[IT], vb[IT], vc[IT];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int i = idx / CT, kx = kx0 + idx % CT;
+    va[it] = vb[it] = vc[it] = mk<C>(0, 0);
+    if (idx < N * CT && kx < NH) {
+      const size_t off = base + (size_t)i * NH + kx;
+      va[it] = W0[off];
+      if (MODE == Y3_FWD || MODE == Y3_INV) vb[it] = W1[off];
+      if (MODE == Y3_FWD) vc[it] = W2[off];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int i = idx / CT, c = idx % CT;
+    if (idx >= N * CT) continue;
+    if (MODE == Y3_INV) {
+      const R kty = kderiv<R>(i, N, pc.kfy);
+      const C F = va[it];
+      sm[sp(i) * CTP + c] = mk<C>(-kty * F.y, kty * F.x);     // i k~_y F
+      sm[SEQ * CTP + sp(i) * CTP + c] = F;                     // F
+      sm[2 * SEQ * CTP + sp(i) * CTP + c] = vb[it];            // G_z
+    } else {
+      sm[sp(i) * CTP + c] = va[it];
+      if (NF == 3) {
+        sm[SEQ * CTP + sp(i) * CTP + c] = vb[it];
+        sm[2 * SEQ * CTP + sp(i) * CTP + c] = vc[it];
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int q = threadIdx.x / T, lane = threadIdx.x % T;
+    const int f = q / CT, c = q % CT;
+    constexpr bool INV = (MODE == Y3_INV || MODE == Y3_INV_FIELD);
+    fft_smem<C, N, E, INV>(sm + f * SEQ * CTP + c, CTP, lane, tw);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int i = idx / CT, c = idx % CT, kx = kx0 + c;
+    if (idx >= N * CT || kx >= NH) continue;
+    const size_t off = base + (size_t)i * NH + kx;
+    if (MODE == Y3_FWD) {
+      const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(i, N, pc.kfy);
+      const C a = sm[sp(i) * CTP + c], b = sm[SEQ * CTP + sp(i) * CTP + c];
+      W0[off] = mk<C>(ktx * a.x + kty * b.x, ktx * a.y + kty * b.y);  // Q1
+      W1[off] = sm[2 * SEQ * CTP + sp(i) * CTP + c];                  // Q2
+    } else if (MODE == Y3_INV) {
+      const R ktx = kderiv<R>(kx, N, pc.kfx);
+      const C Fy = sm[SEQ * CTP + sp(i) * CTP + c];
+      W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);        // W_x = i k~_x Y^-1 F
+      W1[off] = sm[sp(i) * CTP + c];                    // W_y
+      W2[off] = sm[2 * SEQ * CTP + sp(i) * CTP + c];    // W_z
+    } else {
+      W0[off] = sm[sp(i) * CTP + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z forward pass. Grid (ceil(NH/CT), N): tile of CT kx columns at ky = blockIdx.y.
+// ---------------------------------------------------------------------------
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == Z3F_TO_STATE ? 1 : 2) * CT * (N / E))
+k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
+         C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const SavScal* __restrict__ sc,
+         const C_t<R>* __restrict__ tw, int target) {
+  using C = C_t<R>;
+  using RD = Red<R>;
+  constexpr int T = fft_shape<N, E>::T;
+  constexpr int NF = (MODE == Z3F_TO_STATE) ? 1 : 2;
+  constexpr int NTH = NF * CT * T;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int NH = N / 2 + 1;
+  constexpr int IT = N * CT / NTH;
+  constexpr int SEQ = sp_len(N);
+  constexpr size_t PS = (size_t)N * NH;
+  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  __shared__ typename RD::acc red[32];
+  if (sc->status != DEV_OK) return;
+  const PC<R> pc(P);
+  const int kx0 = blockIdx.x * CT, ky = blockIdx.y;
+  const size_t base = (size_t)ky * NH;
+  {
+    C va[IT], vb[IT];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int i = idx / CT, kx = kx0 + idx % CT;
+      va[it] = vb[it] = mk<C>(0, 0);
+      if (kx < NH) {
+        va[it] = W0[base + i * PS + kx];
+        if (NF == 2) vb[it] = W1[base + i * PS + kx];
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int i = idx / CT, c = idx % CT;
+      sm[sp(i) * CTP + c] = va[it];
+      if (NF == 2) sm[SEQ * CTP + sp(i) * CTP + c] = vb[it];
+    }
+  }
+  __syncthreads();
+  {
+    const int q = threadIdx.x / T, lane = threadIdx.x % T;
+    const int f = q / CT, c = q % CT;
+    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
+  }
+  __syncthreads();
+  if constexpr (MODE == Z3F_TO_STATE) {
+    C* dst = S.at(target);
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int i = idx / CT, c = idx % CT, kx = kx0 + c;
+      if (kx < NH) dst[base + i * PS + kx] = sm[sp(i) * CTP + c];
+    }
+  } else {
+    const int p = sc->p;
+    const C* scur = S.at(p);
+    const C* sold = S.at(1 - p);
+    const R c0 = (MODE == Z3F_BDF1) ? (R)1 : (R)1.5;
+    C vn[IT], vo[IT];
+    if (MODE != Z3F_NHAT) {
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        const int idx = threadIdx.x + it * NTH;
+        const int i = idx / CT, kx = kx0 + idx % CT;
+        vn[it] = vo[it] = mk<C>(0, 0);
+        if (kx < NH) {
+          vn[it] = scur[base + i * PS + kx];
+          if (MODE == Z3F_BDF2) vo[it] = sold[base + i * PS + kx];
+        }
+      }
+    }
+    typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int kz = idx / CT, c = idx % CT, kx = kx0 + c;
+      if (kx >= NH) continue;
+      const size_t off = base + kz * PS + kx;
+      const C q1 = sm[sp(kz) * CTP + c], q2 = sm[SEQ * CTP + sp(kz) * CTP + c];
+      const R ktz = kderiv<R>(kz, N, pc.kfz);
+      const R ux = q1.x + ktz * q2.x, uy = q1.y + ktz * q2.y;
+      const C nh = mk<C>(uy, -ux);  // -i (k~_x W_x + k~_y W_y + k~_z W_z)
+      Nhat[off] = nh;
+      if (MODE == Z3F_NHAT) continue;
+      const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
+      const R invA = sym_invA<R>(K2, c0, pc);
+      C v;
+      if (MODE == Z3F_BDF1) v = vn[it];
+      else v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+      const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;
+      const R n2 = nh.x * nh.x + nh.y * nh.y;
+      const R nv = nh.x * v.x + nh.y * v.y;
+      ag = RD::add(ag, w * (-K2 * invA) * n2);
+      ae = RD::add(ae, w * nv * invA);
+      at = RD::add(at, w * nv);
+    }
+    if constexpr (MODE != Z3F_NHAT) {
+      const typename RD::acc tg = block_red<R>(ag, red);
+      const typename RD::acc te = block_red<R>(ae, red);
+      const typename RD::acc tt = block_red<R>(at, red);
+      if (threadIdx.x == 0) {
+        const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+        typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
+        ps[b] = tg;
+        ps[nb + b] = te;
+        ps[2 * nb + b] = tt;
+      }
+    }
+  }
+}
+
+// One block: reduce the E_1 and gamma/eta/theta partial sums and solve the
+// scalar system; the update is then applied by the z-inverse pass into slot
+// 1 - p_old, so p flips here.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k3d_scalar(const Params P, SavScal* __restrict__ sc, const double* __restrict__ partE, int nE,
+           const double* __restrict__ partG, int nG, int bdf1) {
+  using RD = Red<R>;
+  using ST = typename RD::store;
+  __shared__ typename RD::acc red5[5][32];
+  __shared__ typename RD::acc qres[5];
+  if (sc->status != DEV_OK) return;
+  const ST* pe = reinterpret_cast<const ST*>(partE);
+  const ST* pg = reinterpret_cast<const ST*>(partG);
+  const ST* arr[5] = {pe, pe + nE, pg, pg + nG, pg + 2 * nG};
+  const int cnt[5] = {nE, nE, nG, nG, nG};
+  block_red_arrays<R, 5>(arr, cnt, qres, red5);
+  if (threadIdx.x == 0) {
+    const SolveOut<R> o = sav_solve(P, qres, bdf1 != 0, RIn<R>(sc));
+    sav_commit(sc, o, 1 - sc->p, PEND_NONE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z inverse pass. Grid (ceil(NH/CT), N): tile of CT kx columns at ky = blockIdx.y.
+// STEP: after k3d_scalar (p already points at the slot being written):
+//   phi^{n+1} -> slot p, phi* = 2 phi^{n+1} - phi^n; PREP: phi* = 2 S[p] - S[1-p];
+//   GRAD: phi* = S[p] (which 0) or S[1-p]; FIELD: one output, the field itself.
+// Outputs: W0 = Z^-1 phi*, W1 = Z^-1 (i k~_z phi*).
+// ---------------------------------------------------------------------------
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == Z3I_FIELD ? 1 : 2) * CT * (N / E))
+k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
+         C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
+  using C = C_t<R>;
+  constexpr int T = fft_shape<N, E>::T;
+  constexpr int NF = (MODE == Z3I_FIELD) ? 1 : 2;
+  constexpr int NTH = NF * CT * T;
+  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int NH = N / 2 + 1;
+  constexpr int IT = N * CT / NTH;
+  constexpr int SEQ = sp_len(N);
+  constexpr size_t PS = (size_t)N * NH;
+  constexpr bool STEP = (MODE == Z3I_STEP || MODE == Z3I_STEP_BDF1);
+  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  if (sc->status != DEV_OK) return;
+  const PC<R> pc(P);
+  const int kx0 = blockIdx.x * CT, ky = blockIdx.y;
+  const size_t base = (size_t)ky * NH;
+  const int p = sc->p;
+  C* A;  // STEP: phi^n; PREP: S[p]; GRAD/FIELD: the chosen slot
+  C* B;  // STEP: the slot receiving phi^{n+1} (holds phi^{n-1}); PREP: S[1-p]
+  if (STEP) { A = S.at(1 - p); B = S.at(p); }
+  else if (MODE == Z3I_PREP) { A = S.at(p); B = S.at(1 - p); }
+  else { A = S.at(which == 0 ? p : 1 - p); B = A; }
+  const R al = read_alpha<R>(sc);
+  C va[IT], vb[IT], vn[IT];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int i = idx / CT, kx = kx0 + idx % CT;
+    va[it] = vb[it] = vn[it] = mk<C>(0, 0);
+    if (kx < NH) {
+      const size_t off = base + i * PS + kx;
+      va[it] = A[off];
+      if (STEP || MODE == Z3I_PREP) vb[it] = B[off];
+      if (STEP) vn[it] = Nhat[off];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int kz = idx / CT, c = idx % CT, kx = kx0 + c;
+    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
+    if (kx < NH) {
+      const size_t off = base + kz * PS + kx;
+      C ph;
+      if (STEP) {
+        const C cur = va[it];
+        C nw;
+        if (off == 0) {
+          const double z = (MODE == Z3I_STEP_BDF1) ? sc->zm[1 - p] : zero_mode_update(sc->zm[1 - p], sc->zm[p]);
+          sc->zm[p] = z;
+          nw = mk<C>((R)z, (R)0);
+        } else {
+          const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
+          if (MODE == Z3I_STEP_BDF1) nw = bdf1_update<C, R>(cur, vn[it], K2, sym_invA<R>(K2, (R)1, pc), al);
+          else nw = bdf2_update<C, R>(cur, vb[it], vn[it], K2, sym_invA<R>(K2, (R)1.5, pc), al);
+        }
+        B[off] = nw;
+        ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
+      } else if (MODE == Z3I_PREP) {
+        ph = mk<C>((R)2 * va[it].x - vb[it].x, (R)2 * va[it].y - vb[it].y);
+      } else {
+        ph = va[it];
+      }
+      g0 = ph;
+      const R ktz = kderiv<R>(kz, N, pc.kfz);
+      g1 = mk<C>(-ktz * ph.y, ktz * ph.x);
+    }
+    sm[sp(kz) * CTP + c] = g0;
+    if (NF == 2) sm[SEQ * CTP + sp(kz) * CTP + c] = g1;
+  }
+  __syncthreads();
+  {
+    const int q = threadIdx.x / T, lane = threadIdx.x % T;
+    const int f = q / CT, c = q % CT;
+    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * NTH;
+    const int z = idx / CT, c = idx % CT, kx = kx0 + c;
+    if (kx < NH) {
+      W0[base + z * PS + kx] = sm[sp(z) * CTP + c];
+      if (NF == 2) W1[base + z * PS + kx] = sm[SEQ * CTP + sp(z) * CTP + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x row pass over pairs of rows (flat row index z*N + y; N even, so a pair
+// shares z). Grid: N*N/(2*RP) blocks of RP row pairs.
+// NONLIN / ENERGY: three sequences per pair: G_x + i G_y of each row and
+// G_z(row 0) + i G_z(row 1). IN_REAL / OUT_REAL: one sequence per pair,
+// f(row 0) + i f(row 1).
+// part: 2 x gridDim.x accumulators (sum s^2, sum s).
+// ---------------------------------------------------------------------------
+template <typename R, int N, int E, int RP, int MODE>
+__global__ void __launch_bounds__(((MODE == RW_NONLIN || MODE == RW_ENERGY) ? 3 : 1) * RP * (N / E))
+k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+        double* __restrict__ part, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw,
+        double* __restrict__ real_io) {
+  using C = C_t<R>;
+  using RD = Red<R>;
+  constexpr int T = fft_shape<N, E>::T;
+  constexpr int NS = (MODE == RW_NONLIN || MODE == RW_ENERGY) ? 3 : 1;
+  constexpr int NTH = NS * RP * T;
+  constexpr int NH = N / 2 + 1;
+  constexpr int KH = (N / 2) / T;
+  constexpr int SEQ = sp_len(N);
+  static_assert(NTH % 32 == 0 && KH * T == N / 2, "rows must fill whole warps");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  __shared__ typename RD::acc red[32];
+  if (sc->status != DEV_OK) return;
+  const int q = threadIdx.x / T, lane = threadIdx.x % T;
+  const int pl = q / NS, kind = q % NS;            // local pair, sequence kind
+  const size_t row0 = 2 * ((size_t)blockIdx.x * RP + pl);
+  C* z = sm + q * (SEQ + 1);
+
+  if constexpr (MODE == RW_IN_REAL) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = lane + i * T;
+      z[sp(x)] = mk<C>((R)real_io[row0 * N + x], (R)real_io[(row0 + 1) * N + x]);
+    }
+    __syncthreads();
+    fft_smem<C, N, E, false>(z, 1, lane, tw);
+    const R h = (R)0.5 * PC<R>(P).invP;
+#pragma unroll
+    for (int i = 0; i < KH + 1; ++i) {
+      if (i == KH && lane != 0) break;
+      const int k = (i == KH) ? N / 2 : lane + i * T;
+      const C zk = z[sp(k)], zm = cconj(z[sp((N - k) & (N - 1))]);
+      const C a = cadd(zk, zm), b = csub(zk, zm);
+      W0[row0 * NH + k] = cscale(a, h);
+      W0[(row0 + 1) * NH + k] = mk<C>(b.y * h, -b.x * h);
+    }
+  } else if constexpr (MODE == RW_OUT_REAL) {
+    C a[KH], b[KH];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      a[i] = W0[row0 * NH + lane + i * T];
+      b[i] = W0[(row0 + 1) * NH + lane + i * T];
+    }
+    const C an = W0[row0 * NH + N / 2], bn = W0[(row0 + 1) * NH + N / 2];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      const int k = lane + i * T;
+      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
+      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
+    }
+    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
+    __syncthreads();
+    fft_smem<C, N, E, true>(z, 1, lane, tw);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = lane + i * T;
+      real_io[row0 * N + x] = (double)z[sp(x)].x;
+      real_io[(row0 + 1) * N + x] = (double)z[sp(x)].y;
+    }
+  } else {
+    // pack: kind 0/1 = G_x + i G_y of row 0/1, kind 2 = G_z(row 0) + i G_z(row 1)
+    const C* Aa = (kind == 2) ? W2 : W0;
+    const C* Bb = (kind == 2) ? W2 : W1;
+    const size_t ra = row0 + (kind == 1 ? 1 : 0);
+    const size_t rb = (kind == 2) ? row0 + 1 : ra;
+    C a[KH], b[KH];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      a[i] = Aa[ra * NH + lane + i * T];
+      b[i] = Bb[rb * NH + lane + i * T];
+    }
+    const C an = Aa[ra * NH + N / 2], bn = Bb[rb * NH + N / 2];
+#pragma unroll
+    for (int i = 0; i < KH; ++i) {
+      const int k = lane + i * T;
+      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
+      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
+    }
+    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
+    __syncthreads();
+    fft_smem<C, N, E, true>(z, 1, lane, tw);
+    __syncthreads();
+    // pointwise (kinds 0 and 1 own row 0 and row 1; kind 2 lanes only wait)
+    typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
+    const PC<R> pc(P);
+    C* zxy = sm + (pl * NS + kind) * (SEQ + 1);
+    C* zz = sm + (pl * NS + 2) * (SEQ + 1);
+    if (kind < 2) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = sp(lane + i * T);
+        const C g = zxy[x];
+        const C gzc = zz[x];
+        const R gz = (kind == 0) ? gzc.x : gzc.y;
+        const R s = g.x * g.x + g.y * g.y + gz * gz;
+        acc2 = RD::add(acc2, s * s);
+        acc1 = RD::add(acc1, s);
+        if (MODE == RW_NONLIN) {
+          const R fac = pc.beta * s - (R)2;
+          zxy[x] = mk<C>(fac * g.x, fac * g.y);
+          if (kind == 0) zz[x].x = fac * gz; else zz[x].y = fac * gz;
+        }
+      }
+    }
+    if constexpr (MODE == RW_NONLIN) {
+      __syncthreads();
+      fft_smem<C, N, E, false>(z, 1, lane, tw);
+      const R h = (R)0.5 * pc.invP;
+      C* Oa = (kind == 2) ? W2 : W0;
+      C* Ob = (kind == 2) ? W2 : W1;
+#pragma unroll
+      for (int i = 0; i < KH + 1; ++i) {
+        if (i == KH && lane != 0) break;
+        const int k = (i == KH) ? N / 2 : lane + i * T;
+        const C zk = z[sp(k)], zm = cconj(z[sp((N - k) & (N - 1))]);
+        const C sx = cadd(zk, zm), dy = csub(zk, zm);
+        Oa[ra * NH + k] = cscale(sx, h);
+        Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);
+      }
+    }
+    const typename RD::acc t2 = block_red<R>(acc2, red);
+    const typename RD::acc t1 = block_red<R>(acc1, red);
+    if (threadIdx.x == 0) {
+      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
+      ps[blockIdx.x] = t2;
+      ps[gridDim.x + blockIdx.x] = t1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise 3D kernels over the half spectrum (grid-stride)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void idx3(size_t off, int N, int NH, int& kx, int& ky, int& kz) {
+  kx = (int)(off % NH);
+  const size_t r = off / NH;
+  ky = (int)(r % N);
+  kz = (int)(r / N);
+}
+
+// Ghost point (eq. scheme-SAV-initial-1): slot 1-p = phi^0 + dt |k|^2 (N_hat + (a + |k|^4) phi^0).
+template <typename R>
+__global__ void k3d_ghost(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, SavScal* sc) {
+  using C = C_t<R>;
+  const int N = P.N, NH = P.NH;
+  const int p = sc->p;
+  const C* cur = S.at(p);
+  C* dst = S.at(1 - p);
+  const PC<R> pc(P);
+  const size_t total = (size_t)N * N * NH;
+  for (size_t off = blockIdx.x * (size_t)blockDim.x + threadIdx.x; off < total;
+       off += (size_t)gridDim.x * blockDim.x) {
+    int kx, ky, kz;
+    idx3(off, N, NH, kx, ky, kz);
+    const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
+    const C cu = cur[off], nh = Nhat[off];
+    const R L = pc.a + K2 * K2;
+    const R f = pc.dt * K2;
+    dst[off] = mk<C>(cu.x + f * (nh.x + L * cu.x), cu.y + f * (nh.y + L * cu.y));
+    if (off == 0) sc->zm[1 - p] = sc->zm[p];
+  }
+}
+
+// Spectral norms of phi = slot p and psi = 2 phi - slot (1-p), zero mode excluded.
+template <typename R>
+__global__ void k3d_norms(const Params P, Slots<R> S, const SavScal* sc, double* part) {
+  using C = C_t<R>;
+  __shared__ double red[32];
+  const int N = P.N, NH = P.NH;
+  const int p = sc->p;
+  const C* nw = S.at(p);
+  const C* ol = S.at(1 - p);
+  const size_t total = (size_t)N * N * NH;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (size_t off = blockIdx.x * (size_t)blockDim.x + threadIdx.x; off < total;
+       off += (size_t)gridDim.x * blockDim.x) {
+    if (off == 0) continue;
+    int kx, ky, kz;
+    idx3(off, N, NH, kx, ky, kz);
+    const double kxx = kx * P.kf[0], kyy = kfull<double>(ky, N, P.kf[1]), kzz = kfull<double>(kz, N, P.kf[2]);
+    const double K2 = kxx * kxx + kyy * kyy + kzz * kzz;
+    const double w = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+    const C u = nw[off], v = ol[off];
+    const double n2 = (double)u.x * u.x + (double)u.y * u.y;
+    const double px = 2.0 * u.x - v.x, py = 2.0 * u.y - v.y;
+    a0 += w * n2;
+    a1 += w * K2 * K2 * n2;
+    a2 += w * (P.a + K2 * K2) * (px * px + py * py);
+  }
+  const double t0 = block_sum(a0, red);
+  const double t1 = block_sum(a1, red);
+  const double t2 = block_sum(a2, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = t0;
+    part[gridDim.x + blockIdx.x] = t1;
+    part[2 * gridDim.x + blockIdx.x] = t2;
+  }
+}
+
+}  // namespace spfc
