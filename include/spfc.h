@@ -145,6 +145,36 @@ int64_t spfc_device_bytes(spfc_t h);
 
 void spfc_destroy(spfc_t h);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: many independent 2D runs of uneven grid sizes and
+ * parameters stepped together (each run is the scheme of spfc_create).
+ * Runs of equal N share batched kernel launches; the size classes run as
+ * parallel branches of one CUDA graph per step. The paper runs single grids;
+ * the runs here do not interact.
+ * ------------------------------------------------------------------------- */
+typedef struct spfc_batch_s* spfc_batch_t;
+
+/* nruns runs; per run: n[r] in {16..512} (power of two), square box of side
+ * L[r], eps[r] (1 - eps > 0), beta[r] > 0; dt and precision shared. */
+int spfc_batch_create(int nruns, const int* n, const double* L, const double* eps, const double* beta, double dt,
+                      int precision, void* cuda_stream, spfc_batch_t* out);
+/* Start run `run` from phi0 (host, n[run]^2 float64 values) with spfc_start `mode`. */
+int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode);
+/* Advance every run by nsteps (asynchronous; a run whose device status
+ * latches an error stops, the others continue). */
+int spfc_batch_step(spfc_batch_t b, int64_t nsteps);
+int spfc_batch_sync(spfc_batch_t b);
+/* phi^n (which = 0) or phi^{n-1} (which = 1) of one run to host memory. */
+int spfc_batch_get_field(spfc_batch_t b, int run, double* out, int which);
+/* out[0..8): r^n, r^{n-1}, xi, gamma, E_1, steps, mean of phi, device status. */
+int spfc_batch_scalars(spfc_batch_t b, int run, double* out, int nout);
+/* E3 = {E_N, modified energy, E_breve} of one run (as spfc_energy). */
+int spfc_batch_energy(spfc_batch_t b, int run, double* E3);
+/* Total grid points over all runs. */
+int64_t spfc_batch_points(spfc_batch_t b);
+void spfc_batch_destroy(spfc_batch_t b);
+const char* spfc_batch_last_error(spfc_batch_t b);
+
 /* Allocation-free energy diagnostics of one 2D field (float64).
  * The paper has no counterpart: this exists for callers that cannot allocate
  * device memory -- code whose device memory is owned by another allocator or

@@ -1,0 +1,9 @@
+// float64 batched ensemble classes.
+#include "spfc_batch.cuh"
+
+namespace spfc {
+BatchClassBase* make_batch_class_f64(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
+                                      std::string* err) {
+  return make_batch_class<double>(N, params, st, status, err);
+}
+}  // namespace spfc

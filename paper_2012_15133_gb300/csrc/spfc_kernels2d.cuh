@@ -57,9 +57,9 @@ template <typename R> struct Slots {
   __device__ __forceinline__ C_t<R>* at(int i) const { return i ? s[1] : s[0]; }
 };
 
-enum ColInvMode : int { CI_STEP = 0, CI_GRAD = 1, CI_FIELD = 2 };
+enum ColInvMode : int { CI_STEP = 0, CI_GRAD = 1, CI_FIELD = 2, CI_STEP_COMMITTED = 3 };
 enum RowMode : int { RW_NONLIN = 0, RW_ENERGY = 1, RW_OUT_REAL = 2, RW_IN_REAL = 3 };
-enum ColFwdMode : int { CF_BDF2 = 0, CF_BDF1 = 1, CF_NHAT = 2, CF_TO_STATE = 3 };
+enum ColFwdMode : int { CF_BDF2 = 0, CF_BDF1 = 1, CF_NHAT = 2, CF_TO_STATE = 3, CF_PART = 4 };
 
 // Explicitly rounded arithmetic for the spectral symbols and the update, so
 // that every kernel that evaluates them (the lazy update in the column pass,
@@ -115,9 +115,9 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha) {
 // NF * CT sequences of length N, T = N/E lanes each.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CI_FIELD ? 1 : 2) * CT * (N / E))
-k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
-            C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
+__device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
+                                                 C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
+                                                 SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
@@ -125,6 +125,7 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
   constexpr int IT = N * CT / NTH;  // elements per thread in the tile phases
+  constexpr bool COMMITTED = (MODE == CI_STEP_COMMITTED);
   constexpr int SEQ = sp_len(N);
   static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -135,7 +136,10 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
   const int p = sc->p;
-  const int pending = (MODE == CI_STEP) ? sc->pending : 0;
+  // CI_STEP: a pending update (lazy form) is applied into slot 1-p.
+  // CI_STEP_COMMITTED: the scalar solve has already flipped p; the update is
+  // applied into slot p (holding phi^{n-1}) from phi^n in slot 1-p.
+  const int pending = (MODE == CI_STEP) ? sc->pending : (COMMITTED ? 1 : 0);
   const R alpha = read_alpha<R>(sc);
   const int kx0 = blockIdx.x * CT;
   C* src_new;
@@ -143,6 +147,9 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   if (MODE == CI_STEP) {
     src_new = S.at(p);
     src_old = S.at(1 - p);
+  } else if (COMMITTED) {
+    src_new = S.at(1 - p);
+    src_old = S.at(p);
   } else {
     src_new = S.at(which == 0 ? p : 1 - p);
     src_old = src_new;
@@ -157,7 +164,7 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
     if (kx < NH) {
       const size_t off = (size_t)ky * NH + kx;
       vcur[it] = src_new[off];
-      if (MODE == CI_STEP) {
+      if (MODE == CI_STEP || COMMITTED) {
         vold[it] = src_old[off];
         if (pending) vnh[it] = Nhat[off];
       }
@@ -171,15 +178,16 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
     if (kx < NH) {
       const size_t off = (size_t)ky * NH + kx;
       C ph = vcur[it];
-      if (MODE == CI_STEP) {
+      if (MODE == CI_STEP || COMMITTED) {
         const C cur = vcur[it];
         C old = vold[it];
         C nw = cur;
         if (pending) {
           if (off == 0) {
             // zero mode: c_0 = phi_0^n + (phi_0^n - phi_0^{n-1})/3 (A_0 = 3/2, Delta kills N)
-            const double z = zero_mode_update(sc->zm[p], sc->zm[1 - p]);
-            sc->zm[1 - p] = z;
+            const int sn = COMMITTED ? 1 - p : p;  // slot of phi^n
+            const double z = zero_mode_update(sc->zm[sn], sc->zm[1 - sn]);
+            sc->zm[1 - sn] = z;
             nw = mk<C>((R)z, (R)0);
           } else {
             const R K2 = sym_K2<R>(kx, ky, N, pc);
@@ -219,14 +227,21 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   }
 }
 
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == CI_FIELD ? 1 : 2) * CT * (N / E))
+k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
+            C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
+  k2d_col_inv_body<R, N, E, CT, MODE>(P, S, Nhat, W0, W1, sc, tw, which);
+}
+
 // ---------------------------------------------------------------------------
 // Row pass. Grid: N/RPC blocks, RPC rows each, T = N/E lanes per row.
 // part: 2 x gridDim.x doubles: sum s^2 and sum s per block (without h^d).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int RPC, int MODE>
-__global__ void __launch_bounds__(RPC * (N / E))
-k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double* __restrict__ part,
-        const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
+__device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
+                                             double* __restrict__ part, const SavScal* __restrict__ sc,
+                                             const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NTH = RPC * T;
@@ -339,6 +354,13 @@ k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double
 // Scalar SAV solve (one warp): combine the partial sums in a fixed order and
 // solve eqs. solver-2 / solver-4 for r^{n+1}. BDF1 is the first-order start.
 // ---------------------------------------------------------------------------
+template <typename R, int N, int E, int RPC, int MODE>
+__global__ void __launch_bounds__(RPC * (N / E))
+k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double* __restrict__ part,
+        const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
+  k2d_row_body<R, N, E, RPC, MODE>(P, W0, W1, part, sc, tw, real_io);
+}
+
 // Scalar SAV solve (eqs. solver-2, solver-4 and solver-6 reduced to scalars).
 // Inputs are the grid-reduced sums q = {sum s^2, sum s (E_1), and the
 // half-spectrum sums of gamma, eta, theta without |Omega|} and r of the two
@@ -461,11 +483,11 @@ __device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const type
 // partG: 3 x gridDim.x doubles (gamma, eta, theta partial sums, without |Omega|).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CF_TO_STATE ? 1 : 2) * CT * (N / E))
-k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
-            C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const double* __restrict__ partE, int nE,
-            SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
-            int target) {
+__device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ W0,
+                                                 const C_t<R>* __restrict__ W1, C_t<R>* __restrict__ Nhat,
+                                                 double* __restrict__ partG, const double* __restrict__ partE,
+                                                 int nE, SavScal* __restrict__ sc, unsigned* __restrict__ counter,
+                                                 const C_t<R>* __restrict__ tw, int target) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
@@ -540,7 +562,7 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
         if (kx < NH) {
           const size_t off = (size_t)ky * NH + kx;
           vn[it] = snew[off];
-          if (MODE == CF_BDF2) vo[it] = sold[off];
+          if (MODE == CF_BDF2 || MODE == CF_PART) vo[it] = sold[off];
         }
       }
     }
@@ -582,9 +604,13 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
         ps[blockIdx.x] = tg;
         ps[gridDim.x + blockIdx.x] = te;
         ps[2 * gridDim.x + blockIdx.x] = tt;
-        __threadfence();
-        const unsigned prev = atomicAdd(counter, 1u);
-        am_last = (prev == gridDim.x - 1);
+        if (MODE != CF_PART) {
+          __threadfence();
+          const unsigned prev = atomicAdd(counter, 1u);
+          am_last = (prev == gridDim.x - 1);
+        } else {
+          am_last = false;
+        }
       }
       __syncthreads();
       if (am_last) {
@@ -602,6 +628,15 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
       }
     }
   }
+}
+
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__((MODE == CF_TO_STATE ? 1 : 2) * CT * (N / E))
+k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
+            C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const double* __restrict__ partE, int nE,
+            SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
+            int target) {
+  k2d_col_fwd_body<R, N, E, CT, MODE>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, target);
 }
 
 // ---------------------------------------------------------------------------

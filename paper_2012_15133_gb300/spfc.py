@@ -47,6 +47,16 @@ _SIGS = {
     "spfc_device_bytes": (ct.c_int64, [_P]),
     "spfc_destroy": (None, [_P]),
     "spfc_last_error": (ct.c_char_p, [_P]),
+    "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
+    "spfc_batch_init": (_I, [_P, _I, _P, _I]),
+    "spfc_batch_step": (_I, [_P, ct.c_int64]),
+    "spfc_batch_sync": (_I, [_P]),
+    "spfc_batch_get_field": (_I, [_P, _I, _P, _I]),
+    "spfc_batch_scalars": (_I, [_P, _I, _DP, _I]),
+    "spfc_batch_energy": (_I, [_P, _I, _DP]),
+    "spfc_batch_points": (ct.c_int64, [_P]),
+    "spfc_batch_destroy": (None, [_P]),
+    "spfc_batch_last_error": (ct.c_char_p, [_P]),
     "spfc_field_energy_noalloc": (_I, [_I, _DP, _D, _D, _P, _DP, _P]),
     "spfc_noalloc_last_error": (ct.c_char_p, []),
 }
@@ -246,6 +256,82 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.spfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched ensemble of independent 2D runs (see include/spfc.h).
+
+    runs: sequence of dicts with keys n, L, eps, beta (square boxes)."""
+
+    def __init__(self, runs, dt, precision="fp32", stream=None):
+        self._lib = load_library()
+        self.runs = [dict(r) for r in runs]
+        k = len(self.runs)
+        ns = (ct.c_int * k)(*[int(r["n"]) for r in self.runs])
+        Ls = (ct.c_double * k)(*[float(r["L"]) for r in self.runs])
+        es = (ct.c_double * k)(*[float(r["eps"]) for r in self.runs])
+        bs = (ct.c_double * k)(*[float(r["beta"]) for r in self.runs])
+        sp = _current_stream_ptr() if stream is None else ct.c_void_p(
+            stream if isinstance(stream, int) else stream.cuda_stream)
+        h = ct.c_void_p()
+        rc = self._lib.spfc_batch_create(k, ns, Ls, es, bs, float(dt), _PREC[precision], sp, ct.byref(h))
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_batch_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_batch_last_error(self._h).decode())
+
+    def init(self, run, phi0, mode="bdf1"):
+        arr = np.ascontiguousarray(phi0, dtype=np.float64)
+        n = int(self.runs[run]["n"])
+        if arr.size != n * n:
+            raise ValueError("field has the wrong size")
+        self._check(self._lib.spfc_batch_init(self._h, int(run), arr.ctypes.data_as(ct.c_void_p), _START[mode]))
+        return self
+
+    def step(self, nsteps=1):
+        self._check(self._lib.spfc_batch_step(self._h, int(nsteps)))
+        return self
+
+    def sync(self):
+        self._check(self._lib.spfc_batch_sync(self._h))
+
+    def get_field(self, run, which=0):
+        n = int(self.runs[run]["n"])
+        out = np.empty((n, n), dtype=np.float64)
+        self._check(self._lib.spfc_batch_get_field(self._h, int(run), out.ctypes.data_as(ct.c_void_p), int(which)))
+        return out
+
+    def scalars(self, run):
+        out = (ct.c_double * 8)()
+        rc = self._lib.spfc_batch_scalars(self._h, int(run), out, 8)
+        keys = ("r", "r_prev", "xi", "gamma", "E1", "nsteps", "mean", "status")
+        d = dict(zip(keys, list(out)))
+        if rc != 0 and d["status"] == 0:
+            self._check(rc)
+        return d
+
+    def energy(self, run):
+        out = (ct.c_double * 3)()
+        self._check(self._lib.spfc_batch_energy(self._h, int(run), out))
+        return out[0], out[1], out[2]
+
+    @property
+    def points(self):
+        return int(self._lib.spfc_batch_points(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.spfc_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,84 @@
+"""Batched ensemble (uneven grid sizes and parameters) against single runs and
+the oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from seeded_inputs import ensemble_run, noisy_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the gpu tests")
+    from paper_2012_15133_gb300 import build
+    build.build()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _runs(sizes, count, dt=0.02):
+    return [ensemble_run(i, sizes=sizes) for i in range(count)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_small_ensemble_matches_oracle(precision, tol):
+    """Six runs over grids 16, 32, 64 (h = 0.5), drawn eps/beta/mean, 4 steps."""
+    from paper_2012_15133_gb300 import Batch
+    runs = _runs((16, 32, 64), 6)
+    b = Batch(runs, 0.02, precision)
+    for i, r in enumerate(runs):
+        b.init(i, r["phi0"], "bdf1")
+    b.step(4)
+    for i, r in enumerate(runs):
+        o = Oracle(2, r["n"], r["L"], r["eps"], r["beta"], r["dt"]).start(r["phi0"], "bdf1")
+        o.step(4)
+        assert rel_l2(b.get_field(i), o.phi) < 10 * tol, i
+        sc = b.scalars(i)
+        assert abs(sc["r"] - o.r) / o.r < 10 * tol
+        assert sc["nsteps"] == 5  # the BDF1 start plus four steps
+
+
+def test_ensemble_workload_sizes_match_single_runs():
+    """Two runs of each of 64, 128, 256, 512 (the ensemble workload's sizes and
+    parameter draws), FP32 bulk, against independent single-run solvers."""
+    from paper_2012_15133_gb300 import Batch, Solver
+    runs = _runs((64, 128, 256, 512), 8)
+    b = Batch(runs, 0.02, "fp32")
+    for i, r in enumerate(runs):
+        b.init(i, r["phi0"], "bdf1")
+    b.step(10)
+    for i, r in enumerate(runs):
+        s = Solver(2, r["n"], r["L"], r["eps"], r["beta"], r["dt"], "fp32").init(r["phi0"], "bdf1")
+        s.step(10)
+        assert rel_l2(b.get_field(i), s.get_field(0)) < 1e-5, i
+        assert b.scalars(i)["mean"] == s.mass()[1]
+        Eb, Es = b.energy(i)[1], s.energy()[1]
+        assert abs(Eb - Es) / abs(Es) < 1e-6
+
+
+def test_one_failing_run_does_not_stop_the_others():
+    from paper_2012_15133_gb300 import Batch, SPFCError
+    runs = _runs((32, 64), 4)
+    b = Batch(runs, 0.02, "fp64")
+    for i, r in enumerate(runs):
+        phi = r["phi0"].copy()
+        if i == 1:
+            phi[2, 3] = np.inf  # failure injected on the host
+            with pytest.raises(SPFCError) as ei:
+                b.init(i, phi, "bdf1")
+            assert ei.value.code == 4
+        else:
+            b.init(i, phi, "bdf1")
+    b.step(3)
+    b.sync()
+    assert b.scalars(1)["status"] == 4
+    for i in (0, 2, 3):
+        sc = b.scalars(i)
+        assert sc["status"] == 0 and sc["nsteps"] == 4
+        assert np.all(np.isfinite(b.get_field(i)))
