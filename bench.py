@@ -159,6 +159,70 @@ def run_reference(args):
     return 0
 
 
+def measure_ensemble(steps, warmup, precision, peak):
+    """The batched ensemble: 256 independent 2D runs, 64 each of 64^2, 128^2,
+    256^2 and 512^2 (L = N/2), eps ~ U[0.05,0.35], beta ~ U[0.5,1.5], mean ~
+    U[0.1,0.3], noise 0.05, seeds 100-355, dt 0.02, BDF1 start; graph-replayed
+    steps (1.3 GB of spectrum traffic per step, larger than the L2)."""
+    import torch
+    from paper_2012_15133_gb300 import Batch
+    from seeded_inputs import ensemble_run
+    runs = [ensemble_run(i) for i in range(256)]
+    b = Batch(runs, 0.02, precision)
+    for i, r in enumerate(runs):
+        b.init(i, r["phi0"], "bdf1")
+    b.step(max(3, warmup))
+    b.sync()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    csize = 8 if precision == "fp32" else 16
+    bytes_step = sum(15 * r["n"] * (r["n"] // 2 + 1) * csize for r in runs)
+    ok = all(b.scalars(i)["status"] == 0 for i in (0, 1, 2, 3, 255))
+    return {"workload": "256-run 2D ensemble (64 each of 64^2..512^2), dt 0.02", "runs": 256,
+            "points": b.points, "value": b.points / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "l2": "working set 1.3 GB > L2, no flush",
+            "roofline": {"bound": "hbm", "achieved": bytes_step / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_step / (ms * 1e-3) / 1e9 / peak,
+                         "algorithmic_bytes_per_step": bytes_step,
+                         "note": "step level: 15 half-spectrum passes per run and step"},
+            "status_ok": ok}
+
+
+def measure_cube(steps, warmup, precision, peak, flush):
+    """The 3D workload: 128^3 on [0,64]^3, eps 0.2, beta 1, dt 0.02,
+    phi0 = 0.15 + 0.05 U (seed 2); L2 flushed before each timed step."""
+    import torch
+    from paper_2012_15133_gb300 import Solver
+    from seeded_inputs import cube_3d_case
+    c = cube_3d_case(128)
+    s = Solver(3, 128, c["L"], c["eps"], c["beta"], c["dt"], precision)
+    s.init(c["phi0"], "bdf1")
+    s.step(max(3, warmup))
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(st)
+        s.step(1)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    s.sync()
+    csize = 8 if precision == "fp32" else 16
+    bytes_step = 27 * 128 * 128 * 65 * csize
+    P = 128 ** 3
+    return {"workload": "3D SPFC 128^3, L=64, eps=0.2, dt=0.02, phi0=0.15+0.05U seed 2", "value": P / (ms * 1e-3) / 1e6,
+            "unit": UNIT, "ms_per_step": ms, "steps": steps, "l2": "flushed before every timed step",
+            "roofline": {"bound": "hbm", "achieved": bytes_step / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_step / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_step": bytes_step,
+                         "note": "step level: 27 half-spectrum passes (6 kernels)"}}
+
+
 def run_ours(args):
     rank, local, world, dist = _dist_init(args.gpus)
     import numpy as np
@@ -273,6 +337,11 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = world * P * (args.steps + 1) / float(t.item()) / 1e6
 
+    extras = {}
+    if not args.no_extras:
+        extras["ensemble"] = measure_ensemble(min(args.steps, 200), args.warmup, args.precision, peak)
+        extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, k, secs = oracle_sample(budget_s=args.cpu_budget)
@@ -295,7 +364,8 @@ def run_ours(args):
                         "note": "init from pinned host field, per step spfc_step(1) + scalar read-back, final field read-back"},
                 "gpu_launches": 3 * args.steps,
                 "l2_resident_value": resident,
-                "clocks": clk.summary()}
+                "clocks": clk.summary(),
+                **extras}
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -305,10 +375,32 @@ def run_ours(args):
 
 def run_driver(args):
     """Profiling driver (for ncu): init, then K steps of the workload with the
-    kernels launched one by one; no timing, no flush."""
+    kernels launched one by one (single runs) or graph-replayed (ensemble);
+    no timing, no flush. --workload crystal (2D, --n), cube (3D 128^3) or
+    ensemble (256 runs)."""
     import torch
-    from paper_2012_15133_gb300 import Solver, build
+    from paper_2012_15133_gb300 import Solver, Batch, build
     build.build()
+    if args.workload == "ensemble":
+        from seeded_inputs import ensemble_run
+        runs = [ensemble_run(i) for i in range(256)]
+        b = Batch(runs, 0.02, args.precision)
+        for i, r in enumerate(runs):
+            b.init(i, r["phi0"], "bdf1")
+        b.step(args.steps)
+        b.sync()
+        print(json.dumps({"driver": True, "workload": "ensemble", "steps": args.steps}))
+        return 0
+    if args.workload == "cube":
+        from seeded_inputs import cube_3d_case
+        c = cube_3d_case(128)
+        s = Solver(3, 128, c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+        s.init(c["phi0"], "bdf1")
+        s.set_timing(True)
+        s.step(args.steps)
+        s.sync()
+        print(json.dumps({"driver": True, "workload": "cube", "kernels": s.kernel_times()}))
+        return 0
     from seeded_inputs import crystal_2d_case
     c = crystal_2d_case(args.n)
     s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision)
@@ -330,9 +422,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble and 3D measurements")
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
+    ap.add_argument("--workload", default="crystal", choices=["crystal", "cube", "ensemble"],
+                    help="workload of --ncu-driver")
     args = ap.parse_args()
     if args.ncu_driver:
         return run_driver(args)

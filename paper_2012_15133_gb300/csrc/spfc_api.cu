@@ -202,7 +202,7 @@ int spfc_set_timing(spfc_t h, int on) {
 
 int spfc_kernel_times(spfc_t h, int max, const char** names, int64_t* launches, double* ms) {
   if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
-  static const char* kNames[] = {"col_inv", "row", "col_fwd", "col_fused", "col_z", "col_y", "k4", "k5", "k6"};
+  static const char* kNames[] = {"col_inv", "row", "col_fwd", "col_fused", "y_fwd", "z_fwd", "scalar", "z_inv", "y_inv"};
   spfc::KernelTimes kt;
   int rc = h->s->kernel_times(&kt);
   if (rc) return wrap(h, rc);

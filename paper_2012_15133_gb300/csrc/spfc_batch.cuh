@@ -95,10 +95,15 @@ class BatchClassBase {
   std::string err;
 };
 
+// The batch uses 4-column tiles for N >= 256 (schedule 4): with many runs the
+// column passes stream from HBM, and 4 float32 complex values fill a 32-byte
+// sector per row.
+template <int N> constexpr int batch_sched() { return N >= 256 ? 4 : 0; }
+
 template <typename R, int N_>
 class BatchClass final : public BatchClassBase {
   using C = C_t<R>;
-  using SH = Shape2D<N_, 0>;
+  using SH = Shape2D<N_, batch_sched<N_>()>;
   static constexpr int NH = N_ / 2 + 1;
   static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RPC = SH::RPC, CTP = (CT == 1) ? 1 : CT + 1;
   static constexpr int GCOL = (NH + CT - 1) / CT, GROW = N_ / RPC;

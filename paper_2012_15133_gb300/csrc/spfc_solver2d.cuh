@@ -28,13 +28,14 @@ namespace spfc {
 // row-pass block. Every block fills whole warps. Schedule 0 is the default;
 // the others are alternatives for N >= 128 that the autotuner times:
 //   1: one column per block (twice the blocks), 2: 4 values per lane
-//   (twice the threads per sequence), 3: 16 values per lane, 4 columns.
+//   (twice the threads per sequence), 3: 16 values per lane, 4 columns,
+//   4: 8 values per lane, 4 columns (full 32-byte sectors per row in float32).
 template <int N, int SCHED = 0> struct Shape2D {
-  static constexpr int E = (SCHED == 2) ? 4 : ((SCHED == 3) ? 16 : 8);
+  static constexpr int E = (SCHED == 2) ? 4 : ((SCHED == 3) ? 16 : 8);  // 0, 1 and 4 use 8
   static constexpr int T = N / E;
   static constexpr int CT0 = (N >= 256) ? 2 : ((32 / T > 4) ? 32 / T : 4);
   static constexpr int CT1 = (32 / T > 1) ? 32 / T : 1;  // fewest columns that fill a warp
-  static constexpr int CT = (SCHED == 1) ? CT1 : ((SCHED == 3) ? 4 : CT0);
+  static constexpr int CT = (SCHED == 1) ? CT1 : ((SCHED == 3 || SCHED == 4) ? 4 : CT0);
   static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
   static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
   static_assert(sizeof(Red<float>::store) == sizeof(double) && sizeof(Red<double>::store) == sizeof(double),
@@ -592,7 +593,7 @@ class Solver2D final : public SolverBase {
 };
 
 // Number of launch schedules compiled for a 2D grid size.
-inline int num_schedules_2d(int N) { return (N >= 256) ? 4 : ((N == 128) ? 2 : 1); }
+inline int num_schedules_2d(int N) { return (N >= 256) ? 5 : ((N == 128) ? 2 : 1); }
 
 template <typename R, int N, int SCHED>
 SolverBase* new_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
@@ -616,6 +617,7 @@ SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int
     case 1: return new_solver_2d<R, N, 1>(P, st, status, err);
     case 2: return new_solver_2d<R, N, 2>(P, st, status, err);
     case 3: return new_solver_2d<R, N, 3>(P, st, status, err);
+    case 4: return new_solver_2d<R, N, 4>(P, st, status, err);
     default: return new_solver_2d<R, N, 0>(P, st, status, err);
   }
 }

@@ -10,7 +10,7 @@ namespace spfc {
 template <int N> struct Shape3D {
   static constexpr int E = 8;
   static constexpr int T = N / E;
-  static constexpr int CT = (32 / T > 2) ? 32 / T : 2;  // kx columns per column-pass block
+  static constexpr int CT = (32 / T > 4) ? 32 / T : 4;  // kx columns per column-pass block (>= 32 B per row)
   static constexpr int RP = 32 / T > 1 ? 32 / T : 1;    // row pairs per row-pass block
   static_assert((CT * T) % 32 == 0 && (3 * RP * T) % 32 == 0 && (RP * T) % 32 == 0, "tiles must fill warps");
 };
