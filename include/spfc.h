@@ -175,6 +175,35 @@ int64_t spfc_batch_points(spfc_batch_t b);
 void spfc_batch_destroy(spfc_batch_t b);
 const char* spfc_batch_last_error(spfc_batch_t b);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate: a Fourier neural operator (Li et al. 2020; the paper has
+ * none) mapping (phi^{n-1}, phi^n, eps, beta) on an n x n periodic grid to
+ * phi^{n+K}: lift 4 -> width, `layers` spectral-conv layers (truncated DFT
+ * to kx < modes1 and |ky| <= modes2 as BF16 tensor-core GEMMs, per-mode
+ * complex channel mixing, inverse truncated DFT, 1x1 conv, GELU), projection
+ * width -> proj -> 1, output phi^n + 0.1 (d - mean d) (mass kept exactly).
+ * Weights: float32 master and bfloat16 copy; products in BF16 with float32
+ * accumulation. Fields are float32 device arrays [batch][n][n].
+ * ------------------------------------------------------------------------- */
+typedef struct spfc_fno_s* spfc_fno_t;
+
+int spfc_fno_create(int n, int width, int modes1, int modes2, int layers, int proj, int max_batch,
+                    void* cuda_stream, spfc_fno_t* out);
+int64_t spfc_fno_num_params(spfc_fno_t f);
+/* parameters as float32 host arrays in the documented order (lift, layers, projection) */
+int spfc_fno_set_params(spfc_fno_t f, const float* host);
+int spfc_fno_get_params(spfc_fno_t f, float* host);
+/* out = phi^{n+K} prediction; eps, beta: host arrays of `batch` values */
+int spfc_fno_predict(spfc_fno_t f, int batch, const float* phi_n, const float* phi_nm1, const double* eps,
+                     const double* beta, float* out);
+/* Mean-square loss against target (device), gradient kept on the device for
+ * spfc_fno_adam_step and optionally copied to grad_host. */
+int spfc_fno_loss_grad(spfc_fno_t f, int batch, const float* phi_n, const float* phi_nm1, const double* eps,
+                       const double* beta, const float* target, double* loss, float* grad_host);
+int spfc_fno_adam_step(spfc_fno_t f, float lr, float beta1, float beta2, float epsilon, float weight_decay);
+void spfc_fno_destroy(spfc_fno_t f);
+const char* spfc_fno_last_error(spfc_fno_t f);
+
 /* Allocation-free energy diagnostics of one 2D field (float64).
  * The paper has no counterpart: this exists for callers that cannot allocate
  * device memory -- code whose device memory is owned by another allocator or

@@ -24,6 +24,8 @@ _P = ct.c_void_p
 _D = ct.c_double
 _I = ct.c_int
 _DP = ct.POINTER(ct.c_double)
+_F = ct.c_float
+_FP = ct.POINTER(ct.c_float)
 
 # name -> (restype, argtypes), one entry per function of include/spfc.h
 _SIGS = {
@@ -59,6 +61,15 @@ _SIGS = {
     "spfc_batch_last_error": (ct.c_char_p, [_P]),
     "spfc_field_energy_noalloc": (_I, [_I, _DP, _D, _D, _P, _DP, _P]),
     "spfc_noalloc_last_error": (ct.c_char_p, []),
+    "spfc_fno_create": (_I, [_I, _I, _I, _I, _I, _I, _I, _P, ct.POINTER(_P)]),
+    "spfc_fno_num_params": (ct.c_int64, [_P]),
+    "spfc_fno_set_params": (_I, [_P, _FP]),
+    "spfc_fno_get_params": (_I, [_P, _FP]),
+    "spfc_fno_predict": (_I, [_P, _I, _P, _P, _DP, _DP, _P]),
+    "spfc_fno_loss_grad": (_I, [_P, _I, _P, _P, _DP, _DP, _P, _DP, _FP]),
+    "spfc_fno_adam_step": (_I, [_P, _F, _F, _F, _F, _F]),
+    "spfc_fno_destroy": (None, [_P]),
+    "spfc_fno_last_error": (ct.c_char_p, [_P]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -138,6 +149,7 @@ class Solver:
         n = [int(n)] * self.d if np.isscalar(n) else [int(v) for v in n]
         L = [float(L)] * self.d if np.isscalar(L) else [float(v) for v in L]
         self.n, self.L = n, L
+        self.eps, self.beta, self.dt = float(eps), float(beta), float(dt)
         self.shape = tuple(reversed(n))
         self.precision = _PREC[precision]
         if stream is None:
@@ -222,6 +234,7 @@ class Solver:
 
     def dt_change(self, dt):
         self._check(self._lib.spfc_dt_change(self._h, float(dt)))
+        self.dt = float(dt)
         return self
 
     def save(self, path):

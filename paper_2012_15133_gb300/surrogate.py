@@ -1,0 +1,276 @@
+"""Learned surrogate of K SAV steps, with the plain SAV step as its fallback
+and judge.
+
+The network (a Fourier neural operator, declared in include/spfc.h) runs in
+this library's CUDA kernels (BF16 tensor-core GEMMs, FP32 accumulation):
+forward, backward and Adam. This module marshals arguments, drives training
+on trajectories of the batched solver, and runs the jump-and-check loop:
+
+* a jump maps (phi^{n-1}, phi^n, eps, beta) to a prediction of phi^{n+K};
+* after an accepted jump the two-level scheme restarts with the copy
+  convention phi^{n+K-1} := phi^{n+K}, r = sqrt(E_1) (the paper's restart
+  after a time-step change, Sec. 5);
+* the jump is rejected, and K plain SAV steps taken instead, if the modified
+  energy of the restarted state exceeds that of the current state. With
+  r = sqrt(E_1) the modified energy of a copy-restarted field is
+  E_N(phi) + C_beta |Omega|, so the test compares the original energies E_N
+  of phi^n and of the prediction;
+* every ``check_every`` jumps, K plain steps from the same state judge the
+  jump: rel-L2 above ``tol`` rejects it (and the plain result is kept).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import time
+
+import numpy as np
+
+from .spfc import SPFCError, Solver, Batch, load_library, _current_stream_ptr, field_energy_noalloc
+
+_FP = ct.POINTER(ct.c_float)
+
+# the network of the surrogate workload: 4 layers, width 32, 16 retained
+# modes per axis (kx < 16, |ky| <= 16 in the half spectrum), projection 64
+DEFAULT_NET = dict(width=32, modes1=16, modes2=16, layers=4, proj=64)
+
+
+class FNO:
+    """The surrogate network on the current CUDA device."""
+
+    def __init__(self, n=256, width=32, modes1=16, modes2=16, layers=4, proj=64, max_batch=16):
+        self._lib = load_library()
+        self.n, self.width, self.modes1, self.modes2 = n, width, modes1, modes2
+        self.layers, self.proj, self.max_batch = layers, proj, max_batch
+        h = ct.c_void_p()
+        rc = self._lib.spfc_fno_create(n, width, modes1, modes2, layers, proj, max_batch, _current_stream_ptr(),
+                                       ct.byref(h))
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_fno_last_error(None).decode())
+        self._h = h
+        self.nparams = int(self._lib.spfc_fno_num_params(h))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SPFCError(rc, self._lib.spfc_fno_last_error(self._h).decode())
+
+    def set_params(self, flat):
+        arr = np.ascontiguousarray(flat, dtype=np.float32)
+        if arr.size != self.nparams:
+            raise ValueError("wrong number of parameters")
+        self._check(self._lib.spfc_fno_set_params(self._h, arr.ctypes.data_as(_FP)))
+
+    def get_params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        self._check(self._lib.spfc_fno_get_params(self._h, out.ctypes.data_as(_FP)))
+        return out
+
+    @staticmethod
+    def _dev(t):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("fields must be contiguous float32 CUDA tensors [batch, n, n]")
+        return ct.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _params(eps, beta, B):
+        e = (ct.c_double * B)(*[float(x) for x in eps])
+        b = (ct.c_double * B)(*[float(x) for x in beta])
+        return e, b
+
+    def predict(self, phi_n, phi_nm1, eps, beta, out=None):
+        """phi^{n+K} for a batch of float32 CUDA fields [B, n, n]."""
+        import torch
+        B = phi_n.shape[0]
+        if out is None:
+            out = torch.empty_like(phi_n)
+        e, b = self._params(eps, beta, B)
+        self._check(self._lib.spfc_fno_predict(self._h, B, self._dev(phi_n), self._dev(phi_nm1), e, b,
+                                               self._dev(out)))
+        return out
+
+    def loss_grad(self, phi_n, phi_nm1, eps, beta, target, want_grad=False):
+        """Mean-square loss of the scaled increment; the gradient stays on the
+        device for adam_step (and is returned when want_grad)."""
+        B = phi_n.shape[0]
+        e, b = self._params(eps, beta, B)
+        loss = ct.c_double()
+        g = np.empty(self.nparams, dtype=np.float32) if want_grad else None
+        self._check(self._lib.spfc_fno_loss_grad(self._h, B, self._dev(phi_n), self._dev(phi_nm1), e, b,
+                                                 self._dev(target), ct.byref(loss),
+                                                 g.ctypes.data_as(_FP) if want_grad else None))
+        return (loss.value, g) if want_grad else loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        self._check(self._lib.spfc_fno_adam_step(self._h, lr, beta1, beta2, eps, weight_decay))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.spfc_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def init_params(fno: FNO, seed=0):
+    """Uniform fan-in initialisation in the library's parameter order (lift,
+    per layer Rr, Ri, W, b, then the projection); spectral weights are scaled
+    by 1/width^2, biases start at zero."""
+    rng = np.random.default_rng(seed)
+    W, M = fno.width, 2 * fno.modes2 * fno.modes1
+    parts = [rng.uniform(-0.5, 0.5, W * 4), np.zeros(W)]
+    for _ in range(fno.layers):
+        parts += [rng.uniform(0, 1, W * W * M) / (W * W), rng.uniform(0, 1, W * W * M) / (W * W),
+                  rng.uniform(-1, 1, W * W) / np.sqrt(W), np.zeros(W)]
+    parts += [rng.uniform(-1, 1, fno.proj * W) / np.sqrt(W), np.zeros(fno.proj),
+              rng.uniform(-1, 1, fno.proj) / np.sqrt(fno.proj), np.zeros(1)]
+    flat = np.concatenate(parts).astype(np.float32)
+    assert flat.size == fno.nparams
+    return flat
+
+
+def trajectory_pairs(runs, dt, K, snapshots, spacing, warm, precision="fp32"):
+    """Training triples from trajectories of the batched solver.
+
+    runs: dicts with n, L, eps, beta, phi0 (all of one grid size). After
+    `warm` steps, `snapshots` times: record (phi^{t-1}, phi^t), step K, record
+    phi^{t+K}, then step `spacing` - K more. Returns float32 CUDA tensors
+    (phi_n, phi_nm1, target) of shape [runs * snapshots, n, n] and numpy eps,
+    beta per sample."""
+    import torch
+    b = Batch(runs, dt, precision)
+    for i, r in enumerate(runs):
+        b.init(i, r["phi0"], "bdf1")
+    if warm:
+        b.step(warm)
+    X1, X0, Y = [], [], []
+    for s in range(snapshots):
+        cur = [b.get_field(i, 0) for i in range(len(runs))]
+        prev = [b.get_field(i, 1) for i in range(len(runs))]
+        b.step(K)
+        fut = [b.get_field(i, 0) for i in range(len(runs))]
+        X1 += cur
+        X0 += prev
+        Y += fut
+        if spacing > K and s + 1 < snapshots:
+            b.step(spacing - K)
+    b.close()
+    t = lambda xs: torch.tensor(np.stack(xs).astype(np.float32), device="cuda")
+    eps = np.array([r["eps"] for r in runs] * snapshots)
+    beta = np.array([r["beta"] for r in runs] * snapshots)
+    # sample i * len(runs) + j is run j at snapshot i
+    return {"phi_n": t(X1), "phi_nm1": t(X0), "target": t(Y), "eps": eps, "beta": beta}
+
+
+def train(fno: FNO, data, iters, batch, lr=1e-3, seed=0, weight_decay=0.0):
+    """Adam with a cosine learning-rate schedule on random mini-batches;
+    returns the per-iteration losses."""
+    import torch
+    rng = np.random.default_rng(seed)
+    nsamp = data["phi_n"].shape[0]
+    losses = []
+    for it in range(iters):
+        idx = np.sort(rng.choice(nsamp, size=min(batch, nsamp), replace=False))
+        ti = torch.as_tensor(idx, device="cuda")
+        loss = fno.loss_grad(data["phi_n"][ti].contiguous(), data["phi_nm1"][ti].contiguous(), data["eps"][idx],
+                             data["beta"][idx], data["target"][ti].contiguous())
+        fno.adam_step(lr=lr * 0.5 * (1.0 + np.cos(np.pi * it / max(1, iters))), weight_decay=weight_decay)
+        losses.append(loss)
+    return losses
+
+
+def identity_loss(data):
+    """Loss of a network that predicts no change (d = 0): the scale against
+    which a trained loss is read."""
+    inc = (data["target"] - data["phi_n"]).double() / 0.1
+    inc = inc - inc.mean(dim=(1, 2), keepdim=True)
+    return float((inc * inc).mean())
+
+
+def _rel(a, b):
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+class JumpLog:
+    def __init__(self):
+        self.jumps = self.accepted = self.rejected_energy = self.rejected_check = self.checks = 0
+        self.check_errors = []
+
+    def as_dict(self):
+        return {"jumps": self.jumps, "accepted": self.accepted, "rejected_energy": self.rejected_energy,
+                "rejected_check": self.rejected_check, "checks": self.checks,
+                "fallback_rate": 1.0 - self.accepted / max(1, self.jumps),
+                "max_check_rel_l2": max(self.check_errors) if self.check_errors else None}
+
+
+def _twin(s):
+    return Solver(2, s.n[0], s.L[0], s.eps, s.beta, s.dt, "fp64" if s.precision == 0 else "fp32")
+
+
+def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
+    """Advance 2D square runs (Solver objects of one grid size n <= 256) by
+    jumps x K steps with the surrogate, falling back to K plain SAV steps per
+    rejected jump. One network call predicts all runs of a jump round."""
+    import torch
+    if log is None:
+        log = JumpLog()
+    R = len(solvers)
+    n = solvers[0].n[0]
+    if any(s.d != 2 or s.n != [n, n] or s.L[0] != s.L[1] for s in solvers):
+        raise ValueError("the surrogate takes square 2D runs of one grid size")
+    if R > fno.max_batch or n != fno.n:
+        raise ValueError("runs do not fit the network (grid size or batch)")
+    eps = [s.eps for s in solvers]
+    beta = [s.beta for s in solvers]
+    cur = torch.empty((R, n, n), dtype=torch.float64, device="cuda")
+    prev = torch.empty_like(cur)
+    judge = {}
+    for j in range(jumps):
+        for i, s in enumerate(solvers):
+            s.get_field(0, out=cur[i])
+            s.get_field(1, out=prev[i])
+        pred = fno.predict(cur.float(), prev.float(), eps, beta).double()
+        check = check_every > 0 and j % check_every == 0
+        for i, s in enumerate(solvers):
+            log.jumps += 1
+            e_now = field_energy_noalloc(cur[i], s.L[0], s.eps, s.beta)[0]
+            e_new = field_energy_noalloc(pred[i], s.L[0], s.eps, s.beta)[0]
+            if e_new > e_now:
+                log.rejected_energy += 1
+                s.step(K)
+                continue
+            if check:
+                ref = judge.get(i)
+                if ref is None:
+                    ref = judge[i] = _twin(s)
+                sc = s.sav_scalars()
+                ref.set_state(cur[i], prev[i], sc["r"], sc["r_prev"])
+                ref.step(K)
+                plain = ref.get_field(0, out=torch.empty_like(cur[i]))
+                err = _rel(pred[i], plain)
+                log.checks += 1
+                log.check_errors.append(err)
+                if err > tol:
+                    log.rejected_check += 1
+                    rs = ref.sav_scalars()
+                    s.set_state(plain, ref.get_field(1, out=torch.empty_like(cur[i])), rs["r"], rs["r_prev"])
+                    continue
+            log.accepted += 1
+            s.init(pred[i].contiguous(), "copy")
+    for ref in judge.values():
+        ref.close()
+    return log
+
+
+def timed(fn, *args, **kw):
+    """(result, seconds) of fn with the device synchronised on both sides."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn(*args, **kw)
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0

@@ -99,3 +99,15 @@ def ensemble_run(i: int, sizes=ENSEMBLE_SIZES, first_seed: int = 100):
     phi0 = (mean + 0.05 * u).reshape(n, n)
     return dict(d=2, n=n, L=0.5 * n, eps=float(eps), beta=float(beta),
                 dt=0.02, mean=float(mean), seed=seed, phi0=phi0)
+
+
+SURROGATE_TRAIN_SEED = 1000
+SURROGATE_HELD_OUT_SEED = 9000
+
+
+def surrogate_run(i: int, n: int = 256, held_out: bool = False):
+    """Run ``i`` of the surrogate's training set (seeds 1000 + i) or of its
+    held-out evaluation set (seeds 9000 + i): the ensemble recipe on one grid
+    size (L = N/2, dt = 0.02)."""
+    first = SURROGATE_HELD_OUT_SEED if held_out else SURROGATE_TRAIN_SEED
+    return ensemble_run(i, sizes=(n,), first_seed=first)
