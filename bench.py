@@ -223,6 +223,66 @@ def measure_cube(steps, warmup, precision, peak, flush):
                          "note": "step level: 27 half-spectrum passes (6 kernels)"}}
 
 
+def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs=16, jumps=100, K=20,
+                      check_every=5, tol=1e-3):
+    """The learned surrogate at 256^2 (L = 128, the ensemble recipe on one grid
+    size, dt 0.02): trained with the library's own backward and Adam kernels
+    on trajectory pairs of the batched solver (training seeds), then run on
+    held-out seeds with the plain-step fallback. Reports point-steps/s of
+    surrogate + fallback against plain FP32 SAV steps of the same runs (one
+    solver per run, and the batched solver), and the rel-L2 of the final
+    fields against the plain trajectories."""
+    import numpy as np
+    import torch
+    from paper_2012_15133_gb300 import Solver, Batch
+    from paper_2012_15133_gb300 import surrogate as S
+    from seeded_inputs import surrogate_run
+    n = 256
+    t0 = time.perf_counter()
+    data = S.trajectory_pairs([surrogate_run(i, n) for i in range(train_runs)], 0.02, K, snapshots, 250, 100)
+    t_data = time.perf_counter() - t0
+    net = S.FNO(n=n, width=32, modes1=modes, modes2=modes, layers=4, proj=64, max_batch=eval_runs)
+    net.set_params(S.init_params(net, 0))
+    losses, t_train = S.timed(S.train, net, data, iters, 16, 2e-3)
+    idl = S.identity_loss(data)
+    del data
+    held = [surrogate_run(i, n, held_out=True) for i in range(eval_runs)]
+
+    def fresh():
+        out = []
+        for r in held:
+            s = Solver(2, n, r["L"], r["eps"], r["beta"], r["dt"], "fp32")
+            s.init(r["phi0"], "bdf1")
+            s.step(100)
+            out.append(s)
+        return out
+    sur, pl = fresh(), fresh()
+    log, t_sur = S.timed(S.advance, sur, net, K, jumps, check_every=check_every, tol=tol)
+    _, t_plain = S.timed(lambda: [s.step(K * jumps) for s in pl])
+    b = Batch(held, 0.02, "fp32")
+    for i, r in enumerate(held):
+        b.init(i, r["phi0"], "bdf1")
+    b.step(100)
+    _, t_batch = S.timed(b.step, K * jumps)
+    errs = [float(np.linalg.norm(x.get_field(0) - y.get_field(0)) / np.linalg.norm(y.get_field(0)))
+            for x, y in zip(sur, pl)]
+    pts = eval_runs * n * n * K * jumps
+    net.close()
+    return {"workload": f"surrogate jumps of K={K} steps, 256^2 (L=128), {eval_runs} held-out seeds x "
+                        f"{K * jumps} steps after 100 plain steps; network width 32, {modes} x {2 * modes} "
+                        f"retained modes, 4 layers",
+            "value": pts / t_sur / 1e6, "unit": UNIT,
+            "plain_value": pts / t_plain / 1e6, "plain_batched_value": pts / t_batch / 1e6,
+            "speedup_vs_plain": t_plain / t_sur, "speedup_vs_plain_batched": t_batch / t_sur,
+            "final_rel_l2_vs_plain": {"mean": float(np.mean(errs)), "max": float(np.max(errs))},
+            "jumps": log.as_dict(), "check_every": check_every, "tol": tol,
+            "training": {"pairs": train_runs * snapshots, "trajectories": train_runs, "iters": iters, "batch": 16,
+                         "loss_last": float(np.mean(losses[-20:])), "identity_loss": idl,
+                         "data_s": t_data, "train_s": t_train},
+            "note": "bounded sample of the surrogate workload (the full one trains on 2000 trajectories and "
+                    "evaluates 64 seeds x 10000 steps)"}
+
+
 def run_ours(args):
     rank, local, world, dist = _dist_init(args.gpus)
     import numpy as np
@@ -341,6 +401,10 @@ def run_ours(args):
     if not args.no_extras:
         extras["ensemble"] = measure_ensemble(min(args.steps, 200), args.warmup, args.precision, peak)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
+        if not args.no_surrogate:
+            del flush
+            extras["surrogate"] = measure_surrogate(modes=16)
+            extras["surrogate_32_modes"] = measure_surrogate(modes=32)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -362,7 +426,7 @@ def run_ours(args):
                         "h2d_bytes_per_step": P * 8 / args.steps,
                         "d2h_bytes_per_step": 48 + P * 8 / args.steps,
                         "note": "init from pinned host field, per step spfc_step(1) + scalar read-back, final field read-back"},
-                "gpu_launches": 3 * args.steps,
+                "gpu_launches": 2 * args.steps,
                 "l2_resident_value": resident,
                 "clocks": clk.summary(),
                 **extras}
@@ -422,7 +486,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble and 3D measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, 3D and surrogate measurements")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")

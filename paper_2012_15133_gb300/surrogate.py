@@ -199,6 +199,7 @@ class JumpLog:
     def __init__(self):
         self.jumps = self.accepted = self.rejected_energy = self.rejected_check = self.checks = 0
         self.check_errors = []
+        self.decisions = []   # (jump, run, "accept" | "energy" | "check")
 
     def as_dict(self):
         return {"jumps": self.jumps, "accepted": self.accepted, "rejected_energy": self.rejected_energy,
@@ -241,6 +242,7 @@ def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
             e_new = field_energy_noalloc(pred[i], s.L[0], s.eps, s.beta)[0]
             if e_new > e_now:
                 log.rejected_energy += 1
+                log.decisions.append((j, i, "energy"))
                 s.step(K)
                 continue
             if check:
@@ -256,10 +258,12 @@ def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
                 log.check_errors.append(err)
                 if err > tol:
                     log.rejected_check += 1
+                    log.decisions.append((j, i, "check"))
                     rs = ref.sav_scalars()
                     s.set_state(plain, ref.get_field(1, out=torch.empty_like(cur[i])), rs["r"], rs["r_prev"])
                     continue
             log.accepted += 1
+            log.decisions.append((j, i, "accept"))
             s.init(pred[i].contiguous(), "copy")
     for ref in judge.values():
         ref.close()

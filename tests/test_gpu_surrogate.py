@@ -1,0 +1,145 @@
+"""The learned surrogate trained on the solver's own trajectories, and its
+fallback to the plain SAV step.
+
+A network of the production shape (4 layers, width 32, 16 x 32 retained
+modes, projection 64) is trained on a 64^2 ensemble (L = 32; the square
+lattice's wave number then sits at mode index about 5, inside the retained
+band) with the library's backward and Adam kernels. The tests check that:
+training lowers the loss far below that of predicting no change, also on
+held-out seeds; an accepted jump never raises E_N and restarts the two-level
+scheme from the prediction; a rejected jump is exactly K plain steps; and
+the trained network predicts K steps much closer to the plain scheme than
+the untrained one. The throughput with and without the network is printed.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N, K = 64, 20
+
+
+def _runs(count, held_out=False):
+    from seeded_inputs import surrogate_run
+    return [surrogate_run(i, n=N, held_out=held_out) for i in range(count)]
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2012_15133_gb300 import surrogate as S
+    data = S.trajectory_pairs(_runs(32), 0.02, K, 8, 100, 50)
+    net = S.FNO(n=N, width=32, modes1=16, modes2=16, layers=4, proj=64, max_batch=16)
+    init = S.init_params(net, 0)
+    net.set_params(init)
+    losses = S.train(net, data, 400, 16, lr=2e-3)
+    return net, data, losses, init
+
+
+def _solvers(count, warm=50):
+    from paper_2012_15133_gb300 import Solver
+    out = []
+    for r in _runs(count, held_out=True):
+        s = Solver(2, N, r["L"], r["eps"], r["beta"], r["dt"], "fp32")
+        s.init(r["phi0"], "bdf1")
+        s.step(warm)
+        out.append(s)
+    return out
+
+
+def test_training_lowers_the_loss_on_training_and_held_out_trajectories(trained):
+    from paper_2012_15133_gb300 import surrogate as S
+    net, data, losses, _ = trained
+    assert all(np.isfinite(losses))
+    idl = S.identity_loss(data)
+    assert np.mean(losses[-20:]) < 0.1 * idl, (np.mean(losses[-20:]), idl)
+    # held-out seeds, sampled at the same times as the training pairs
+    held = S.trajectory_pairs(_runs(4, held_out=True), 0.02, K, 8, 100, 50)
+    hl = np.mean([net.loss_grad(held["phi_n"][i:i + 16].contiguous(), held["phi_nm1"][i:i + 16].contiguous(),
+                                held["eps"][i:i + 16], held["beta"][i:i + 16], held["target"][i:i + 16].contiguous())
+                  for i in (0, 16)])
+    assert hl < 0.2 * S.identity_loss(held), (hl, S.identity_loss(held))
+
+
+def test_accepted_jumps_keep_energy_and_restart_from_the_prediction(trained):
+    from paper_2012_15133_gb300 import surrogate as S, field_energy_noalloc
+    net = trained[0]
+    sol = _solvers(4)
+    accepted = 0
+    for j in range(4):
+        before = [s.get_field(0) for s in sol]
+        e_before = [field_energy_noalloc(torch.tensor(b, device="cuda"), s.L[0], s.eps, s.beta)[0]
+                    for b, s in zip(before, sol)]
+        cur = torch.tensor(np.stack(before), dtype=torch.float32, device="cuda")
+        prev = torch.tensor(np.stack([s.get_field(1) for s in sol]), dtype=torch.float32, device="cuda")
+        pred = net.predict(cur, prev, [s.eps for s in sol], [s.beta for s in sol]).double().cpu().numpy()
+        log = S.advance(sol, net, K, 1, check_every=0)
+        for (_, i, what) in log.decisions:
+            s = sol[i]
+            after = s.get_field(0)
+            if what == "accept":
+                accepted += 1
+                # the copy restart: both levels hold the prediction
+                assert np.max(np.abs(after - pred[i])) < 1e-6 * np.max(np.abs(pred[i]))
+                assert np.array_equal(s.get_field(1), after)
+                e_after = field_energy_noalloc(torch.tensor(after, device="cuda"), s.L[0], s.eps, s.beta)[0]
+                assert e_after <= e_before[i] + 1e-6 * abs(e_before[i])
+            else:
+                assert what == "energy"
+    assert accepted > 0
+
+
+def test_rejected_jumps_are_exactly_the_plain_steps():
+    from paper_2012_15133_gb300 import surrogate as S
+    # a network with inflated weights predicts rough fields whose energy rises
+    net = S.FNO(n=N, width=8, modes1=4, modes2=4, layers=1, proj=8, max_batch=4)
+    net.set_params(S.init_params(net, 3) * 40.0)
+    a, b = _solvers(3), _solvers(3)
+    log = S.advance(a, net, K, 3, check_every=0)
+    assert log.rejected_energy == log.jumps == 9
+    for s in b:
+        s.step(3 * K)
+    for sa, sb in zip(a, b):
+        assert np.array_equal(sa.get_field(0), sb.get_field(0))
+        assert sa.sav_scalars()["r"] == sb.sav_scalars()["r"]
+
+
+def test_what_the_trained_network_gains(trained):
+    """Rel-L2 of K-step predictions against the plain scheme on held-out
+    seeds (at the training pairs' times), for the trained network, the
+    untrained one and the no-change predictor; the rel-L2 of a field is
+    about the square root of the increment loss ratio times the no-change
+    error. Then the point-steps/s of surrogate + fallback and of plain
+    steps on the same runs."""
+    from paper_2012_15133_gb300 import surrogate as S
+    net, _, _, init = trained
+    held = S.trajectory_pairs(_runs(4, held_out=True), 0.02, K, 8, 100, 50)
+    fresh = S.FNO(n=N, width=32, modes1=16, modes2=16, layers=4, proj=64, max_batch=16)
+    fresh.set_params(init)
+
+    def rel_err(pred_fn):
+        errs = []
+        for i in (0, 16):
+            sl = slice(i, i + 16)
+            p = pred_fn(held["phi_n"][sl].contiguous(), held["phi_nm1"][sl].contiguous(), held["eps"][sl],
+                        held["beta"][sl])
+            t = held["target"][sl]
+            errs += [float(torch.linalg.vector_norm(p[j] - t[j]) / torch.linalg.vector_norm(t[j])) for j in range(16)]
+        return float(np.mean(errs))
+    err_trained = rel_err(net.predict)
+    err_untrained = rel_err(fresh.predict)
+    err_none = rel_err(lambda a, b, e, bt: a)
+    assert err_trained < 0.5 * err_none, (err_trained, err_none)
+    assert err_trained < 0.5 * err_untrained, (err_trained, err_untrained)
+    # throughput with and without the network (every 5th jump checked)
+    jumps = 10
+    sol = _solvers(8, warm=350)
+    log, t_sur = S.timed(S.advance, sol, net, K, jumps, check_every=5, tol=1e-3)
+    ref = _solvers(8, warm=350)
+    _, t_plain = S.timed(lambda: [s.step(K * jumps) for s in ref])
+    pts = 8 * N * N * K * jumps
+    print(f"\nsurrogate 64^2: rel-L2 per jump trained {err_trained:.2e}, untrained {err_untrained:.2e}, "
+          f"no change {err_none:.2e}; {log.as_dict()}; "
+          f"Mpt-steps/s surrogate+fallback {pts / t_sur / 1e6:.0f}, plain {pts / t_plain / 1e6:.0f}")
+    assert log.jumps == 8 * jumps
