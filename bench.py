@@ -456,6 +456,20 @@ def run_driver(args):
     import torch
     from paper_2012_15133_gb300 import Solver, Batch, build
     build.build()
+    if args.workload == "surrogate":
+        import torch
+        from paper_2012_15133_gb300 import surrogate as S
+        net = S.FNO(n=256, max_batch=16, **S.DEFAULT_NET)
+        net.set_params(S.init_params(net, 0))
+        x = torch.full((16, 256, 256), 0.2, device="cuda")
+        for _ in range(args.steps):
+            y = net.predict(x, x, [0.2] * 16, [1.0] * 16)
+        for _ in range(args.steps):
+            net.loss_grad(x, x, [0.2] * 16, [1.0] * 16, y)
+            net.adam_step(1e-4)
+        torch.cuda.synchronize()
+        print(json.dumps({"driver": True, "workload": "surrogate", "steps": args.steps}))
+        return 0
     if args.workload == "ensemble":
         from seeded_inputs import ensemble_run
         runs = [ensemble_run(i) for i in range(256)]
@@ -502,7 +516,7 @@ def main():
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
-    ap.add_argument("--workload", default="crystal", choices=["crystal", "cube", "ensemble"],
+    ap.add_argument("--workload", default="crystal", choices=["crystal", "cube", "ensemble", "surrogate"],
                     help="workload of --ncu-driver")
     args = ap.parse_args()
     if args.ncu_driver:
