@@ -107,29 +107,46 @@ template <int N, int E> __device__ __forceinline__ void fft_sync() {
   if constexpr (N / E <= 32) __syncwarp(); else __syncthreads();
 }
 
-// One Stockham stage of radix RAD (Govindaraju et al., SC'08 formulation):
+// Stockham stages of radix RAD (Govindaraju et al., SC'08 formulation):
 // butterfly j reads x[j + r N/RAD], twiddles by w^(r (j mod NS) N/(NS RAD)),
-// transforms, and writes x[(j/NS) NS RAD + (j mod NS) + r NS]. All lanes of a
-// sequence hold their inputs in registers across a barrier, so the stage
-// runs in place.
-template <typename C, int N, int E, bool INV, int NS, int RAD>
-__device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* __restrict__ tw) {
-  constexpr int T = fft_shape<N, E>::T;
-  constexpr int NB = E / RAD;
-  constexpr int STRIDE = N / RAD;
-  constexpr int TWS = TW_N / (NS * RAD);
-  C v[E];
-#pragma unroll
-  for (int m = 0; m < NB; ++m) {
-    const int j = lane + m * T;
-#pragma unroll
-    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sp(j + r * STRIDE) * es];
+// transforms, and writes x[(j/NS) NS RAD + (j mod NS) + r NS].
+//
+// Radix of the stage that starts with span NS (the same rule for every
+// caller: radix 8 while it divides the rest and E, then 4, then 2).
+template <int N, int E, int NS> struct stage_rad {
+  static constexpr int REM = N / NS;
+  static constexpr int value = (REM % 8 == 0 && E % 8 == 0) ? 8 : ((REM % 4 == 0 && E % 4 == 0) ? 4 : 2);
+};
+
+// Span NS of the last stage.
+template <int N, int E> __host__ __device__ constexpr int last_span() {
+  int ns = 1;
+  while (true) {
+    const int rem = N / ns;
+    const int rad = (rem % 8 == 0 && E % 8 == 0) ? 8 : ((rem % 4 == 0 && E % 4 == 0) ? 4 : 2);
+    if (ns * rad == N) return ns;
+    ns *= rad;
   }
-  fft_sync<N, E>();
+}
+
+// The three parts of a stage for the butterflies j = lane + m T of one lane:
+// load v[m RAD + r] = x[j + r N/RAD]; twiddle and transform in registers;
+// store to x[(j/NS) NS RAD + (j mod NS) + r NS].
+template <typename C, int N, int E, int RAD>
+__device__ __forceinline__ void stage_load(C* v, const C* s, int es, int lane) {
+  constexpr int T = fft_shape<N, E>::T, NB = E / RAD, STRIDE = N / RAD;
+#pragma unroll
+  for (int m = 0; m < NB; ++m)
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sp(lane + m * T + r * STRIDE) * es];
+}
+
+template <typename C, int N, int E, bool INV, int NS, int RAD>
+__device__ __forceinline__ void stage_compute(C* v, int lane, const C* __restrict__ tw) {
+  constexpr int T = fft_shape<N, E>::T, NB = E / RAD, TWS = TW_N / (NS * RAD);
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
-    const int j = lane + m * T;
-    const int k = j & (NS - 1);
+    const int k = (lane + m * T) & (NS - 1);
     if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
@@ -139,21 +156,82 @@ __device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* 
       }
     }
     dft_r<C, RAD, INV>(v + m * RAD);
+  }
+}
+
+template <typename C, int N, int E, int NS, int RAD>
+__device__ __forceinline__ void stage_store(const C* v, C* s, int es, int lane) {
+  constexpr int T = fft_shape<N, E>::T, NB = E / RAD;
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    const int j = lane + m * T, k = j & (NS - 1);
     const int base = (j - k) * RAD + k;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) s[sp(base + r * NS) * es] = v[m * RAD + r];
   }
+}
+
+// One Stockham stage of radix RAD in shared memory, in place: all lanes of a
+// sequence hold their inputs in registers across a barrier.
+template <typename C, int N, int E, bool INV, int NS, int RAD>
+__device__ __forceinline__ void stockham_stage(C* s, int es, int lane, const C* __restrict__ tw) {
+  C v[E];
+  stage_load<C, N, E, RAD>(v, s, es, lane);
+  fft_sync<N, E>();
+  stage_compute<C, N, E, INV, NS, RAD>(v, lane, tw);
+  stage_store<C, N, E, NS, RAD>(v, s, es, lane);
   fft_sync<N, E>();
 }
 
 template <typename C, int N, int E, bool INV, int NS>
 __device__ __forceinline__ void fft_stages(C* s, int es, int lane, const C* __restrict__ tw) {
   if constexpr (NS < N) {
-    constexpr int REM = N / NS;
-    constexpr int RAD = (REM % 8 == 0 && E % 8 == 0) ? 8 : ((REM % 4 == 0 && E % 4 == 0) ? 4 : 2);
+    constexpr int RAD = stage_rad<N, E, NS>::value;
     stockham_stage<C, N, E, INV, NS, RAD>(s, es, lane, tw);
     fft_stages<C, N, E, INV, NS * RAD>(s, es, lane, tw);
   }
+}
+
+// Stages NS .. NSL (exclusive) in shared memory.
+template <typename C, int N, int E, bool INV, int NS, int NSL>
+__device__ __forceinline__ void fft_mid_stages(C* s, int es, int lane, const C* __restrict__ tw) {
+  if constexpr (NS < NSL) {
+    constexpr int RAD = stage_rad<N, E, NS>::value;
+    stockham_stage<C, N, E, INV, NS, RAD>(s, es, lane, tw);
+    fft_mid_stages<C, N, E, INV, NS * RAD, NSL>(s, es, lane, tw);
+  }
+}
+
+// Unnormalised complex DFT of one length-N sequence held in registers: on
+// entry v[i] is element lane + i T of the input, on return v[i] is element
+// lane + i T of the output (T = N/E). The first stage reads its inputs from
+// registers and the last leaves its outputs there (both are strided by T in
+// this order), so only the middle stages and one exchange on each side go
+// through shared memory (`s`, es as for fft_smem). Starts with a barrier
+// (the buffer may still be read by the caller's previous use); on return
+// the lanes may still be reading `s`.
+template <typename C, int N, int E, bool INV>
+__device__ __forceinline__ void fft_regs(C* v, C* s, int es, int lane, const C* __restrict__ tw) {
+  constexpr int R1 = stage_rad<N, E, 1>::value, NB1 = E / R1;
+  constexpr int NSL = last_span<N, E>();
+  constexpr int RL = N / NSL, NBL = E / RL;
+  static_assert(NSL > 1, "at least two stages");
+  C w[E];
+#pragma unroll
+  for (int m = 0; m < NB1; ++m)
+#pragma unroll
+    for (int r = 0; r < R1; ++r) w[m * R1 + r] = v[m + r * NB1];  // element lane + T (m + r NB1)
+  stage_compute<C, N, E, INV, 1, R1>(w, lane, tw);
+  fft_sync<N, E>();
+  stage_store<C, N, E, 1, R1>(w, s, es, lane);
+  fft_sync<N, E>();
+  fft_mid_stages<C, N, E, INV, R1, NSL>(s, es, lane, tw);
+  stage_load<C, N, E, RL>(w, s, es, lane);
+  stage_compute<C, N, E, INV, NSL, RL>(w, lane, tw);
+#pragma unroll
+  for (int m = 0; m < NBL; ++m)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) v[m + r * NBL] = w[m * RL + r];  // output lane + T (m + r NBL)
 }
 
 // Unnormalised complex DFT of the length-N sequence whose element i is at

@@ -196,13 +196,30 @@ __global__ void k_gelu_back(long long n, const float* __restrict__ u, float* __r
     g[i] *= gelu_grad_f(u[i]);
 }
 
-// out[c] = sum_{b,p} X[b][c][p] (one block per channel, fixed order)
-__global__ void k_bias_grad(int B, int C, int P, const float* __restrict__ X, float* __restrict__ out) {
+// out[c] = sum_{b,p} X[b][c][p] in two fixed-order stages: block (c, j)
+// sums chunk j of the B*P values of channel c into part[c][j]; then one
+// block per channel sums its parts.
+constexpr int kBiasChunks = 64;
+
+__global__ void k_bias_grad_part(int B, int C, int P, const float* __restrict__ X, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int c = blockIdx.x, j = blockIdx.y;
+  const long long total = (long long)B * P;
+  const long long len = (total + kBiasChunks - 1) / kBiasChunks;
+  const long long i0 = j * len, i1 = min(total, i0 + len);
+  double s = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const long long b = i / P, p = i - b * P;
+    s += X[(b * C + c) * P + p];
+  }
+  s = spfc::block_sum(s, red);
+  if (threadIdx.x == 0) part[c * kBiasChunks + j] = s;
+}
+
+__global__ void k_bias_grad_final(const double* __restrict__ part, float* __restrict__ out) {
   __shared__ double red[32];
   const int c = blockIdx.x;
-  double s = 0.0;
-  for (int b = 0; b < B; ++b)
-    for (int p = threadIdx.x; p < P; p += blockDim.x) s += X[((long long)b * C + c) * P + p];
+  double s = threadIdx.x < kBiasChunks ? part[c * kBiasChunks + threadIdx.x] : 0.0;
   s = spfc::block_sum(s, red);
   if (threadIdx.x == 0) out[c] = (float)s;
 }
@@ -228,24 +245,7 @@ __global__ void k_to_bf16(long long n, const float* __restrict__ w, __nv_bfloat1
     wbf[i] = __float2bfloat16_rn(w[i]);
 }
 
-// x += bias[(row / bdiv) % bmod] (the pre-activation, kept in x); y = gelu(x) or x
-__global__ void k_bias_act(long long total, int N, int bdiv, int bmod, float* __restrict__ x,
-                           const float* __restrict__ bias, int act, float* __restrict__ y) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long row = i / N;
-    const float v = x[i] + (bias ? bias[(row / bdiv) % bmod] : 0.f);
-    x[i] = v;
-    y[i] = act ? gelu_f(v) : v;
-  }
-}
-
-Ix ix(long long a, int s = 0x7fffffff, long long b = 0) {
-  Ix r;
-  r.a = a;
-  r.s = s;
-  r.b = b;
-  return r;
-}
+Ix ix(long long a, int s = 0x7fffffff, long long b = 0) { return make_ix(a, s, b); }
 
 }  // namespace
 
@@ -266,7 +266,7 @@ struct spfc_fno_s {
   float *a = nullptr, *z = nullptr, *q = nullptr, *d = nullptr, *Xf = nullptr, *Oh = nullptr, *Zb = nullptr;
   std::vector<float*> v, u, Vh;
   float *eps_d = nullptr, *beta_d = nullptr, *ws = nullptr, *out = nullptr;
-  double *mean = nullptr, *dmean = nullptr, *lossb = nullptr;
+  double *mean = nullptr, *dmean = nullptr, *lossb = nullptr, *bpart = nullptr;
   // gradients of activations
   float *gd = nullptr, *gz = nullptr, *gv0 = nullptr, *gv1 = nullptr, *gu = nullptr, *gXf = nullptr, *gVh = nullptr,
         *gOh = nullptr, *gZ = nullptr;
@@ -290,10 +290,7 @@ struct spfc_fno_s {
   }
 
   int gemm(int M, int N, int K, int batch, const Mat& A, const Mat& B, const Out& O, int splits = 1) {
-    if (splits > 1) {
-      const long long need = (long long)batch * splits * M * N;
-      if (need > ws_elems) { err = "split-K workspace too small"; return SPFC_EINVAL; }
-    }
+    while (splits > 1 && (long long)batch * splits * M * N > ws_elems) splits /= 2;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splits);
     k_gemm<<<grid, GT, 0, st>>>(M, N, K, batch, splits, A, B, O, ws);
     if (splits > 1) k_gemm_reduce<<<1024, 256, 0, st>>>(M, N, batch, splits, ws, O);
@@ -409,8 +406,8 @@ struct spfc_fno_s {
         (rc = alloc(&gv1, BWP)) || (rc = alloc(&gu, BWP)) || (rc = alloc(&gXf, spec)) || (rc = alloc(&gVh, mix)) ||
         (rc = alloc(&gOh, mix)) || (rc = alloc(&gZ, spec)))
       return rc;
-    ws_elems = 64LL * 64 * 64 * 4;  // weight-gradient GEMMs: M, N <= 64, up to 64 splits
-    if ((rc = alloc(&ws, ws_elems))) return rc;
+    ws_elems = 4LL << 20;  // split-K partial tiles of the weight-gradient GEMMs (M, N <= 64)
+    if ((rc = alloc(&ws, ws_elems)) || (rc = alloc(&bpart, 64LL * kBiasChunks))) return rc;
     const size_t smix = (size_t)(2 * W * W + 4 * Bmax * W) * sizeof(float);
     if (smix > 48 * 1024) {
       if ((rc = ck(cudaFuncSetAttribute(k_mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smix), "attr")) ||
@@ -449,16 +446,23 @@ struct spfc_fno_s {
       // 1x1 conv: u[b] = W_l v[b]
       if ((rc = gemm(W, P, W, B, mb(o_W[l], ix(W), ix(1)), mf(v[l], ix(P), ix(1), WP), of(u[l], ix(P), ix(1), WP))))
         return rc;
-      // inverse along x accumulated onto u; then u += bias and v[l+1] = gelu(u) (none on the last layer)
+      // inverse along x accumulated onto the 1x1 conv in the epilogue, with the
+      // bias (row = (b W + o) n + y): u = pre-activation, v[l+1] = gelu(u)
+      // (no activation on the last layer)
       {
-        Out O = of(u[l], ix(n), ix(1));
+        Out O = of(v[l + 1], ix(n), ix(1));
+        O.cin = u[l];
         O.beta = 1.f;
+        O.bias = w + o_b[l];
+        O.bdiv = n;
+        O.bmod = W;
+        if (l < L - 1) {
+          O.act = 1;
+          O.pre = u[l];
+        }
         if ((rc = gemm(B * W * n, n, 2 * m1, 1, mf(Zb, ix(m1, n, sp), ix(1, m1, (long long)n * m1)),
                        mf(Gx, ix(n), ix(1)), O)))
           return rc;
-        const long long total = (long long)B * W * P;
-        k_bias_act<<<gs(total), 256, 0, st>>>(total, P, 1, W, u[l], w + o_b[l], l < L - 1 ? 1 : 0, v[l + 1]);
-        if ((rc = ck(cudaGetLastError(), "bias_act"))) return rc;
       }
     }
     // projection
@@ -480,22 +484,27 @@ struct spfc_fno_s {
     return ck(cudaGetLastError(), "forward");
   }
 
+  void bias_grad(int B, int C, const float* X, float* out) {
+    k_bias_grad_part<<<dim3(C, kBiasChunks), 256, 0, st>>>(B, C, P, X, bpart);
+    k_bias_grad_final<<<C, 64, 0, st>>>(bpart, out);
+  }
+
   // dL/d(parameters) for the B samples of the last forward pass, given gd = dL/dd
   int backward(int B) {
     int rc;
     const long long WP = (long long)W * P, QP = (long long)Q * P, sp = 2LL * n * m1, mx = 2LL * KY * m1;
     const int BP = B * P;
-    const int splits = std::min(64, std::max(1, BP / 8192));
+    const int splits = std::min(1024, std::max(1, BP / 1024));
     // projection: d = q2w q + q2b, q = gelu(z), z = q1w v_L + q1b
     {
       Out O = of(g + o_q2w, ix(1), ix(1));
       if ((rc = gemm(1, Q, BP, 1, mf(gd, ix(0), ix(1)), mf(q, ix(1, P, QP), ix(P)), O, splits))) return rc;
-      k_bias_grad<<<1, 256, 0, st>>>(B, 1, P, gd, g + o_q2b);
+      bias_grad(B, 1, gd, g + o_q2b);
       k_proj_back<<<gs((long long)B * QP), 256, 0, st>>>(B, Q, P, gd, wbf + o_q2w, z, gz);
       if ((rc = ck(cudaGetLastError(), "proj_back"))) return rc;
       Out O1 = of(g + o_q1w, ix(W), ix(1));
       if ((rc = gemm(Q, W, BP, 1, mf(gz, ix(P), ix(1, P, QP)), mf(v[L], ix(1, P, WP), ix(P)), O1, splits))) return rc;
-      k_bias_grad<<<Q, 256, 0, st>>>(B, Q, P, gz, g + o_q1b);
+      bias_grad(B, Q, gz, g + o_q1b);
       // gv = q1w^T gz
       if ((rc = gemm(W, P, Q, B, mb(o_q1w, ix(1), ix(W)), mf(gz, ix(P), ix(1), QP), of(gv0, ix(P), ix(1), WP))))
         return rc;
@@ -506,7 +515,7 @@ struct spfc_fno_s {
       // gu = gv * gelu'(u) (the last layer has no activation)
       if ((rc = ck(cudaMemcpyAsync(gu, gv, (size_t)B * WP * 4, cudaMemcpyDeviceToDevice, st), "copy"))) return rc;
       if (l < L - 1) k_gelu_back<<<gs((long long)B * WP), 256, 0, st>>>((long long)B * WP, u[l], gu);
-      k_bias_grad<<<W, 256, 0, st>>>(B, W, P, gu, g + o_b[l]);
+      bias_grad(B, W, gu, g + o_b[l]);
       if ((rc = ck(cudaGetLastError(), "gelu_back"))) return rc;
       // 1x1 conv: dW = sum_b gu[b] v[b]^T; gvn = W^T gu
       if ((rc = gemm(W, W, BP, 1, mf(gu, ix(P), ix(1, P, WP)), mf(v[l], ix(1, P, WP), ix(P)),
@@ -544,7 +553,7 @@ struct spfc_fno_s {
     if ((rc = gemm(W, 4, BP, 1, mf(gv, ix(P), ix(1, P, WP)), mf(a, ix(1, P, 4LL * P), ix(P)),
                    of(g + o_lw, ix(4), ix(1)), splits)))
       return rc;
-    k_bias_grad<<<W, 256, 0, st>>>(B, W, P, gv, g + o_lb);
+    bias_grad(B, W, gv, g + o_lb);
     return ck(cudaGetLastError(), "backward");
   }
 

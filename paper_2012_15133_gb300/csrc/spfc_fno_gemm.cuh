@@ -17,14 +17,37 @@
 namespace spfc {
 namespace fno {
 
-struct Ix {               // index map i -> (i % s) * a + (i / s) * b
+// Index map i -> (i % s) * a + (i / s) * b. The quotient uses a multiplier
+// fixed on the host (division by an invariant integer, Granlund & Montgomery
+// 1994): q = (umulhi(i, m) + i) >> l with l = ceil(log2 s) and
+// m = floor(2^32 (2^l - s) / s) + 1; exact for 0 <= i < 2^31 (the sum then
+// stays below 2^32). m = 0 marks a one-level map (s larger than any index).
+struct Ix {
   long long a = 1, b = 0;
   int s = 0x7fffffff;
-  __host__ __device__ long long operator()(int i) const {
-    const int q = i / s;
+  unsigned int m = 0;
+  int l = 0;
+  __device__ __forceinline__ long long operator()(int i) const {
+    if (m == 0) return (long long)i * a;
+    const int q = (int)((__umulhi((unsigned)i, m) + (unsigned)i) >> l);
     return (long long)(i - q * s) * a + (long long)q * b;
   }
 };
+
+inline Ix make_ix(long long a, int s = 0x7fffffff, long long b = 0) {
+  Ix r;
+  r.a = a;
+  r.b = b;
+  r.s = s;
+  if (s != 0x7fffffff) {
+    int l = 0;
+    while ((1ll << l) < (long long)s) ++l;
+    r.l = l;
+    r.m = (unsigned int)((((unsigned long long)1 << 32) * (((unsigned long long)1 << l) - (unsigned long long)s)) /
+                             (unsigned long long)s + 1ull);
+  }
+  return r;
+}
 
 struct Mat {
   const void* p = nullptr;
@@ -34,7 +57,8 @@ struct Mat {
 };
 
 struct Out {
-  float* p = nullptr;     // FP32 output (may be null if only bf16 is wanted)
+  float* p = nullptr;     // FP32 output
+  const float* cin = nullptr;  // C of beta * C (same addressing; p when null)
   Ix r, c;
   long long sb = 0;
   float alpha = 1.f, beta = 0.f;
@@ -69,7 +93,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 __device__ __forceinline__ void store_out(const Out& o, long long base, int row, int col, float acc) {
   const long long off = base + o.r(row) + o.c(col);
   float v = o.alpha * acc;
-  if (o.beta != 0.f) v += o.beta * o.p[off];
+  if (o.beta != 0.f) v += o.beta * (o.cin ? o.cin[off] : o.p[off]);
   if (o.bias) v += o.bias_col ? o.bias[col] : o.bias[(row / o.bdiv) % o.bmod];
   if (o.act == 1) {
     if (o.pre) o.pre[off] = v;

@@ -291,50 +291,47 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
   } else {
-    // pack Z = G_x + i G_y over the full x-spectrum (Hermitian extension)
-    C a[KH], b[KH];
+    // Z = G_x + i G_y over the full x-spectrum, element k = lane + i T loaded
+    // straight into registers: k <= N/2 from the half spectrum, k > N/2 as
+    // the Hermitian mirror of N - k.
+    C v[E];
 #pragma unroll
-    for (int i = 0; i < KH; ++i) {
-      a[i] = W0[roff + lane + i * T];
-      b[i] = W1[roff + lane + i * T];
-    }
-    C an = mk<C>(0, 0), bn = mk<C>(0, 0);
-    if (lane == 0) { an = W0[roff + N / 2]; bn = W1[roff + N / 2]; }
-#pragma unroll
-    for (int i = 0; i < KH; ++i) {
+    for (int i = 0; i < E; ++i) {
       const int k = lane + i * T;
-      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
-      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
+      const bool direct = k <= N / 2;
+      const size_t off = roff + (direct ? k : N - k);
+      const C a = W0[off], b = W1[off];
+      v[i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
     }
-    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
-    __syncthreads();
-    fft_smem<C, N, E, true>(z, 1, lane, tw);
-    // pointwise: s = g_x^2 + g_y^2, partial sums, w = (beta s - 2) g
+    fft_regs<C, N, E, true>(v, z, 1, lane, tw);
+    // pointwise on x = lane + i T: s = g_x^2 + g_y^2, partial sums, w = (beta s - 2) g
     typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
     const PC<R> pc(P);
     const R beta = pc.beta;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const int x = sp(lane + i * T);
-      const C g = z[x];
+      const C g = v[i];
       const R s = g.x * g.x + g.y * g.y;
       acc2 = RD::add(acc2, s * s);
       acc1 = RD::add(acc1, s);
       if (MODE == RW_NONLIN) {
         const R fac = beta * s - (R)2;
-        z[x] = mk<C>(fac * g.x, fac * g.y);
+        v[i] = mk<C>(fac * g.x, fac * g.y);
       }
     }
     if constexpr (MODE == RW_NONLIN) {
-      __syncthreads();
-      fft_smem<C, N, E, false>(z, 1, lane, tw);
+      fft_regs<C, N, E, false>(v, z, 1, lane, tw);
+      // the split into W_x, W_y pairs k with N - k: one exchange
+      fft_sync<N, E>();
+#pragma unroll
+      for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = v[i];
+      fft_sync<N, E>();
       const R half = (R)0.5 * pc.invP;
 #pragma unroll
       for (int i = 0; i < KH + 1; ++i) {
-        const int k = lane + i * T;
         if (i == KH && lane != 0) break;
-        const int kk = (i == KH) ? N / 2 : k;
-        const C zk = z[sp(kk)], zm = cconj(z[sp((N - kk) & (N - 1))]);
+        const int kk = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
+        const C zk = v[i], zm = cconj(z[sp((N - kk) & (N - 1))]);
         const C sx = cadd(zk, zm), dy = csub(zk, zm);
         W0[roff + kk] = cscale(sx, half);                      // W_x = (Z_k + conj Z_{N-k}) / 2
         W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);      // W_y = (Z_k - conj Z_{N-k}) / (2i)
@@ -655,6 +652,19 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
 // ---------------------------------------------------------------------------
 constexpr long long kSpinLimit = 1ll << 22;  // x ~100 ns sleep: about half a second
 
+// Bounded wait until *ctr >= target (a counter other blocks advance): polls
+// with a short sleep at most `limit` times. Returns false if the limit ran
+// out; the caller then latches DEV_TIMEOUT and returns instead of hanging.
+__device__ __forceinline__ bool wait_counter(const unsigned long long* ctr, unsigned long long target,
+                                             long long limit) {
+  long long it = 0;
+  while (*((const volatile unsigned long long*)ctr) < target) {
+    if (++it > limit) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
+
 template <typename R, int N, int E, int CT, bool BDF1>
 __global__ void __launch_bounds__(2 * CT * (N / E))
 k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
@@ -760,18 +770,10 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
     __threadfence();
     const unsigned long long prev = atomicAdd(sync64, 1ull);
     const unsigned long long target = (prev / gridDim.x + 1ull) * gridDim.x;
-    int ok = 1;
-    long long it = 0;
-    while (*((volatile unsigned long long*)sync64) < target) {
-      if (++it > kSpinLimit) {
-        atomicExch(&sc->status, (int)DEV_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
+    const bool ok = wait_counter(sync64, target, kSpinLimit);
+    if (!ok) atomicExch(&sc->status, (int)DEV_TIMEOUT);
     __threadfence();
-    bar_ok = ok;
+    bar_ok = ok ? 1 : 0;
   }
   __syncthreads();
   if (!bar_ok) return;

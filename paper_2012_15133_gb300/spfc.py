@@ -47,6 +47,7 @@ _SIGS = {
     "spfc_set_timing": (_I, [_P, _I]),
     "spfc_kernel_times": (_I, [_P, _I, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_int64), _DP]),
     "spfc_device_bytes": (ct.c_int64, [_P]),
+    "spfc_wait_selftest": (_I, [ct.c_ulonglong, ct.c_longlong, _P]),
     "spfc_destroy": (None, [_P]),
     "spfc_last_error": (ct.c_char_p, [_P]),
     "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
