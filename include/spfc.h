@@ -75,8 +75,11 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
                 int precision, void* cuda_stream, spfc_t* out);
 
 /* Kernel launch schedules (tile shapes) compiled for a grid: spfc_create uses
- * schedule 0; spfc_create_scheduled picks one explicitly (0 <= schedule <
- * spfc_num_schedules(d, n)), which is how the autotuner times the choices.
+ * the grid's default (the fastest measured on GB300: 2D float32 N = 128, 256
+ * -> 2; 2D float64 N = 128, 256 -> 5, N = 512 -> 1; otherwise 0), as does
+ * spfc_create_scheduled with schedule = -1; a schedule in
+ * [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
+ * autotuner times the choices.
  * All schedules compute the same step; results agree to rounding.
  * spfc_schedule returns the handle's schedule. */
 int spfc_num_schedules(int d, int n);

@@ -21,6 +21,15 @@ static int fail(spfc_t h, int code, const std::string& msg) {
   return code;
 }
 
+// Default launch schedule per grid: the fastest measured on GB300 (flushed
+// plus L2-resident step time); the float64 path is bound by its arithmetic
+// and prefers the shapes with the most threads (schedule 5: 4 values per lane).
+static int default_schedule(int d, int n, int precision) {
+  if (d != 2) return 0;
+  if (precision == SPFC_FP64) return n == 512 ? 1 : ((n == 128 || n == 256) ? 5 : 0);
+  return (n == 128 || n == 256) ? 2 : 0;
+}
+
 static int wrap(spfc_t h, int rc) {
   if (rc) h->err = h->s->err;
   return rc;
@@ -72,7 +81,7 @@ int spfc_create_scheduled(int d, const int* n, const double* L, double eps, doub
   spfc::fill_float_params(&P);
   int status = 0;
   std::string err;
-  if (schedule < 0) schedule = 0;
+  if (schedule < 0) schedule = default_schedule(d, n[0], precision);
   SolverBase* s = (precision == SPFC_FP64)
                       ? spfc::make_solver_f64(P, (cudaStream_t)cuda_stream, schedule, &status, &err)
                       : spfc::make_solver_f32(P, (cudaStream_t)cuda_stream, schedule, &status, &err);

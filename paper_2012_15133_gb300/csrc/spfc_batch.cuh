@@ -39,7 +39,7 @@ k2b_row(BatchView<R> B, const C_t<R>* __restrict__ tw) {
 }
 
 template <typename R, int N, int E, int CT>
-__global__ void __launch_bounds__(2 * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k2b_col_fwd(BatchView<R> B, const C_t<R>* __restrict__ tw) {
   const int r = blockIdx.y;
   Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};
@@ -48,7 +48,7 @@ k2b_col_fwd(BatchView<R> B, const C_t<R>* __restrict__ tw) {
 }
 
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__(2 * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k2b_col_inv(BatchView<R> B, const C_t<R>* __restrict__ tw) {
   const int r = blockIdx.y;
   Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};
@@ -95,15 +95,18 @@ class BatchClassBase {
   std::string err;
 };
 
-// The batch uses 4-column tiles for N >= 256 (schedule 4): with many runs the
-// column passes stream from HBM, and 4 float32 complex values fill a 32-byte
-// sector per row.
-template <int N> constexpr int batch_sched() { return N >= 256 ? 4 : 0; }
+// The float32 batch uses 4-column tiles for N >= 256 (schedule 4): with many
+// runs the column passes stream from HBM, and 4 float32 complex values fill a
+// 32-byte sector per row. The float64 batch, bound by its arithmetic, uses the
+// shapes with the most threads (schedule 5) from N = 128.
+template <typename R, int N> constexpr int batch_sched() {
+  return sizeof(R) == 8 ? (N >= 128 ? 5 : 0) : (N >= 256 ? 4 : 0);
+}
 
 template <typename R, int N_>
 class BatchClass final : public BatchClassBase {
   using C = C_t<R>;
-  using SH = Shape2D<N_, batch_sched<N_>()>;
+  using SH = Shape2D<N_, batch_sched<R, N_>()>;
   static constexpr int NH = N_ / 2 + 1;
   static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RPC = SH::RPC, CTP = (CT == 1) ? 1 : CT + 1;
   static constexpr int GCOL = (NH + CT - 1) / CT, GROW = N_ / RPC;
@@ -170,16 +173,16 @@ class BatchClass final : public BatchClassBase {
     const size_t smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);
     const size_t smr = (size_t)RPC * (sp_len(N_) + 1) * sizeof(C);
     k2b_row<R, N_, E, RPC><<<dim3(GROW, nruns), RPC * T, smr, st>>>(v_, tw_);
-    k2b_col_fwd<R, N_, E, CT><<<dim3(GCOL, nruns), 2 * CT * T, smc, st>>>(v_, tw_);
+    k2b_col_fwd<R, N_, E, CT><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
     k2b_scalar<R><<<nruns, 256, 0, st>>>(v_);
-    k2b_col_inv<R, N_, E, CT, CI_STEP_COMMITTED><<<dim3(GCOL, nruns), 2 * CT * T, smc, st>>>(v_, tw_);
+    k2b_col_inv<R, N_, E, CT, CI_STEP_COMMITTED><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
     SPFC_CK(cudaGetLastError());
     return 0;
   }
 
   int prepare(cudaStream_t st) override {
     const size_t smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);
-    k2b_col_inv<R, N_, E, CT, CI_STEP><<<dim3(GCOL, nruns), 2 * CT * T, smc, st>>>(v_, tw_);
+    k2b_col_inv<R, N_, E, CT, CI_STEP><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
     SPFC_CK(cudaGetLastError());
     return 0;
   }

@@ -103,8 +103,8 @@ template <int N, int E> struct fft_shape {
   static_assert(T >= 1 && (T <= 32 ? 32 % T == 0 : T % 32 == 0), "a sequence must not straddle warps unevenly");
 };
 
-template <int N, int E> __device__ __forceinline__ void fft_sync() {
-  if constexpr (N / E <= 32) __syncwarp(); else __syncthreads();
+template <int N, int E, bool BS = false> __device__ __forceinline__ void fft_sync() {
+  if constexpr (N / E <= 32 && !BS) __syncwarp(); else __syncthreads();
 }
 
 // Stockham stages of radix RAD (Govindaraju et al., SC'08 formulation):
@@ -232,6 +232,59 @@ __device__ __forceinline__ void fft_regs(C* v, C* s, int es, int lane, const C* 
   for (int m = 0; m < NBL; ++m)
 #pragma unroll
     for (int r = 0; r < RL; ++r) v[m + r * NBL] = w[m * RL + r];  // output lane + T (m + r NBL)
+}
+
+// fft_regs for NSEQ sequences of one lane at once (sequence q in shared
+// memory at s + q * qs), sharing the barriers; BS forces block-wide barriers
+// (for lanes of one sequence spread over several warps).
+template <typename C, int N, int E, bool INV, int NSEQ, bool BS, int NS, int NSL>
+__device__ __forceinline__ void fft_mid_multi(C* s, int qs, int es, int lane, const C* __restrict__ tw) {
+  if constexpr (NS < NSL) {
+    constexpr int RAD = stage_rad<N, E, NS>::value;
+    C v[NSEQ][E];
+#pragma unroll
+    for (int q = 0; q < NSEQ; ++q) stage_load<C, N, E, RAD>(v[q], s + q * qs, es, lane);
+    fft_sync<N, E, BS>();
+#pragma unroll
+    for (int q = 0; q < NSEQ; ++q) {
+      stage_compute<C, N, E, INV, NS, RAD>(v[q], lane, tw);
+      stage_store<C, N, E, NS, RAD>(v[q], s + q * qs, es, lane);
+    }
+    fft_sync<N, E, BS>();
+    fft_mid_multi<C, N, E, INV, NSEQ, BS, NS * RAD, NSL>(s, qs, es, lane, tw);
+  }
+}
+
+template <typename C, int N, int E, bool INV, int NSEQ, bool BS>
+__device__ __forceinline__ void fft_regs_multi(C (*v)[E], C* s, int qs, int es, int lane,
+                                               const C* __restrict__ tw) {
+  constexpr int R1 = stage_rad<N, E, 1>::value, NB1 = E / R1;
+  constexpr int NSL = last_span<N, E>();
+  constexpr int RL = N / NSL, NBL = E / RL;
+  static_assert(NSL > 1, "at least two stages");
+  fft_sync<N, E, BS>();
+#pragma unroll
+  for (int q = 0; q < NSEQ; ++q) {
+    C w[E];
+#pragma unroll
+    for (int m = 0; m < NB1; ++m)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) w[m * R1 + r] = v[q][m + r * NB1];
+    stage_compute<C, N, E, INV, 1, R1>(w, lane, tw);
+    stage_store<C, N, E, 1, R1>(w, s + q * qs, es, lane);
+  }
+  fft_sync<N, E, BS>();
+  fft_mid_multi<C, N, E, INV, NSEQ, BS, R1, NSL>(s, qs, es, lane, tw);
+#pragma unroll
+  for (int q = 0; q < NSEQ; ++q) {
+    C w[E];
+    stage_load<C, N, E, RL>(w, s + q * qs, es, lane);
+    stage_compute<C, N, E, INV, NSL, RL>(w, lane, tw);
+#pragma unroll
+    for (int m = 0; m < NBL; ++m)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) v[q][m + r * NBL] = w[m * RL + r];
+  }
 }
 
 // Unnormalised complex DFT of the length-N sequence whose element i is at

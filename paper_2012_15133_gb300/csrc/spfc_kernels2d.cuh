@@ -111,8 +111,11 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha) {
 }
 
 // ---------------------------------------------------------------------------
-// Column inverse pass. Grid: ceil(NH/CT) blocks, each a tile of CT kx columns;
-// NF * CT sequences of length N, T = N/E lanes each.
+// Column passes. Grid: ceil(NH/CT) blocks, each a tile of CT kx columns;
+// CT * T threads, thread (lane, c) = threadIdx.x = lane * CT + c owning the
+// rows y = lane + i T (i < E) of column kx0 + c, for every field of the pass
+// (one warp then reads 32/CT rows of CT adjacent columns). The column FFTs
+// keep their first and last stages in registers (fft_regs_multi).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE>
 __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
@@ -121,13 +124,12 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
-  constexpr int NTH = NF * CT * T;
+  constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = N * CT / NTH;  // elements per thread in the tile phases
   constexpr bool COMMITTED = (MODE == CI_STEP_COMMITTED);
   constexpr int SEQ = sp_len(N);
-  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  static_assert(NTH % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
 
@@ -141,7 +143,9 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
   // applied into slot p (holding phi^{n-1}) from phi^n in slot 1-p.
   const int pending = (MODE == CI_STEP) ? sc->pending : (COMMITTED ? 1 : 0);
   const R alpha = read_alpha<R>(sc);
-  const int kx0 = blockIdx.x * CT;
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c;
+  const bool col = kx < NH;
   C* src_new;
   C* src_old;
   if (MODE == CI_STEP) {
@@ -155,32 +159,31 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
     src_old = src_new;
   }
 
-  // gather the tile (all loads first), then the pointwise spectral work
-  C vcur[IT], vold[IT], vnh[IT];
+  // all loads first, then the pointwise spectral work in registers
+  C vcur[E], vold[E], vnh[E];
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int ky = idx / CT, kx = kx0 + idx % CT;
-    if (kx < NH) {
-      const size_t off = (size_t)ky * NH + kx;
-      vcur[it] = src_new[off];
+  for (int i = 0; i < E; ++i) {
+    vcur[i] = vold[i] = vnh[i] = mk<C>(0, 0);
+    if (col) {
+      const size_t off = (size_t)(lane + i * T) * NH + kx;
+      vcur[i] = src_new[off];
       if (MODE == CI_STEP || COMMITTED) {
-        vold[it] = src_old[off];
-        if (pending) vnh[it] = Nhat[off];
+        vold[i] = src_old[off];
+        if (pending) vnh[i] = Nhat[off];
       }
     }
   }
+  C g[NF][E];
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
+  for (int i = 0; i < E; ++i) {
+    const int ky = lane + i * T;
     C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
-    if (kx < NH) {
+    if (col) {
       const size_t off = (size_t)ky * NH + kx;
-      C ph = vcur[it];
+      C ph = vcur[i];
       if (MODE == CI_STEP || COMMITTED) {
-        const C cur = vcur[it];
-        C old = vold[it];
+        const C cur = vcur[i];
+        C old = vold[i];
         C nw = cur;
         if (pending) {
           if (off == 0) {
@@ -191,7 +194,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
             nw = mk<C>((R)z, (R)0);
           } else {
             const R K2 = sym_K2<R>(kx, ky, N, pc);
-            nw = bdf2_update<C, R>(cur, old, vnh[it], K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
+            nw = bdf2_update<C, R>(cur, old, vnh[i], K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
           }
           src_old[off] = nw;  // phi^{n+1} overwrites phi^{n-1}
           old = cur;
@@ -206,29 +209,22 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
         g1 = mk<C>(-kty * ph.y, kty * ph.x);  // i k~_y phi
       }
     }
-    sm[sp(ky) * CTP + c] = g0;
-    if (NF == 2) sm[SEQ * CTP + sp(ky) * CTP + c] = g1;
+    g[0][i] = g0;
+    if (NF == 2) g[NF - 1][i] = g1;
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
+  fft_regs_multi<C, N, E, true, NF, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
+  if (col) {
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int y = idx / CT, c = idx % CT, kx = kx0 + c;
-    if (kx < NH) {
-      W0[(size_t)y * NH + kx] = sm[sp(y) * CTP + c];
-      if (NF == 2) W1[(size_t)y * NH + kx] = sm[SEQ * CTP + sp(y) * CTP + c];
+    for (int i = 0; i < E; ++i) {
+      const size_t off = (size_t)(lane + i * T) * NH + kx;
+      W0[off] = g[0][i];
+      if (NF == 2) W1[off] = g[NF - 1][i];
     }
   }
 }
 
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CI_FIELD ? 1 : 2) * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
             C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
   k2d_col_inv_body<R, N, E, CT, MODE>(P, S, Nhat, W0, W1, sc, tw, which);
@@ -476,7 +472,7 @@ __device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const type
 }
 
 // ---------------------------------------------------------------------------
-// Column forward pass. Grid: ceil(NH/CT) blocks.
+// Column forward pass (thread layout as the inverse pass).
 // partG: 3 x gridDim.x doubles (gamma, eta, theta partial sums, without |Omega|).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE>
@@ -488,12 +484,11 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
-  constexpr int NTH = NF * CT * T;
+  constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = N * CT / NTH;
   constexpr int SEQ = sp_len(N);
-  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  static_assert(NTH % 32 == 0, "tile must fill whole warps");
   using RD = Red<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -505,43 +500,23 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   pdl_wait();
   pdl_trigger();
   if (sc->status != DEV_OK) return;
-  const int kx0 = blockIdx.x * CT;
-  {
-    C va[IT], vb[IT];
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c;
+  const bool col = kx < NH;
+  C v[NF][E];
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int y = idx / CT, kx = kx0 + idx % CT;
-      va[it] = mk<C>(0, 0);
-      vb[it] = mk<C>(0, 0);
-      if (kx < NH) {
-        va[it] = W0[(size_t)y * NH + kx];
-        if (NF == 2) vb[it] = W1[(size_t)y * NH + kx];
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int y = idx / CT, c = idx % CT;
-      sm[sp(y) * CTP + c] = va[it];
-      if (NF == 2) sm[SEQ * CTP + sp(y) * CTP + c] = vb[it];
-    }
+  for (int i = 0; i < E; ++i) {
+    const size_t off = (size_t)(lane + i * T) * NH + kx;
+    v[0][i] = col ? W0[off] : mk<C>(0, 0);
+    if (NF == 2) v[NF - 1][i] = col ? W1[off] : mk<C>(0, 0);
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
 
   if constexpr (MODE == CF_TO_STATE) {
+    fft_regs_multi<C, N, E, false, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
     C* dst = S.at(target);
+    if (col) {
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
-      if (kx < NH) dst[(size_t)ky * NH + kx] = sm[sp(ky) * CTP + c];
+      for (int i = 0; i < E; ++i) dst[(size_t)(lane + i * T) * NH + kx] = v[0][i];
     }
   } else {
     const PC<R> pc(P);
@@ -550,27 +525,24 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
     const C* snew = S.at(newest);
     const C* sold = S.at(1 - newest);
     const R c0 = (MODE == CF_BDF1) ? (R)1 : (R)1.5;
-    C vn[IT], vo[IT];
-    if (MODE != CF_NHAT) {
+    C vn[E], vo[E];
 #pragma unroll
-      for (int it = 0; it < IT; ++it) {
-        const int idx = threadIdx.x + it * NTH;
-        const int ky = idx / CT, kx = kx0 + idx % CT;
-        if (kx < NH) {
-          const size_t off = (size_t)ky * NH + kx;
-          vn[it] = snew[off];
-          if (MODE == CF_BDF2 || MODE == CF_PART) vo[it] = sold[off];
-        }
+    for (int i = 0; i < E; ++i) {
+      vn[i] = vo[i] = mk<C>(0, 0);
+      if (MODE != CF_NHAT && col) {   // issued before the FFT: their latency overlaps it
+        const size_t off = (size_t)(lane + i * T) * NH + kx;
+        vn[i] = snew[off];
+        if (MODE == CF_BDF2 || MODE == CF_PART) vo[i] = sold[off];
       }
     }
+    fft_regs_multi<C, N, E, false, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
     typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
-      if (kx >= NH) continue;
+    for (int i = 0; i < E; ++i) {
+      const int ky = lane + i * T;
+      if (!col) continue;
       const size_t off = (size_t)ky * NH + kx;
-      const C wx = sm[sp(ky) * CTP + c], wy = sm[SEQ * CTP + sp(ky) * CTP + c];
+      const C wx = v[0][i], wy = v[NF - 1][i];
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
       // N_hat = -i (k~_x W_x + k~_y W_y)
       const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
@@ -579,15 +551,15 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       if (MODE == CF_NHAT) continue;
       const R K2 = sym_K2<R>(kx, ky, N, pc);
       const R invA = sym_invA<R>(K2, c0, pc);
-      C v;
+      C vv;
       if (MODE == CF_BDF1) {
-        v = vn[it];
+        vv = vn[i];
       } else {
-        v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+        vv = mk<C>((R)2 * vn[i].x - (R)0.5 * vo[i].x, (R)2 * vn[i].y - (R)0.5 * vo[i].y);
       }
       const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
       const R n2 = nh.x * nh.x + nh.y * nh.y;
-      const R nv = nh.x * v.x + nh.y * v.y;
+      const R nv = nh.x * vv.x + nh.y * vv.y;
       ag = RD::add(ag, w * (-K2 * invA) * n2);   // <N, A^{-1} Delta N>
       ae = RD::add(ae, w * nv * invA);           // <N, A^{-1} v>
       at = RD::add(at, w * nv);                  // <N, v>
@@ -628,7 +600,7 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
 }
 
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == CF_TO_STATE ? 1 : 2) * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
             C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const double* __restrict__ partE, int nE,
             SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
@@ -666,19 +638,18 @@ __device__ __forceinline__ bool wait_counter(const unsigned long long* ctr, unsi
 }
 
 template <typename R, int N, int E, int CT, bool BDF1>
-__global__ void __launch_bounds__(2 * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
               double* __restrict__ partG, const double* __restrict__ partE, int nE, SavScal* __restrict__ sc,
               unsigned long long* __restrict__ sync64, const C_t<R>* __restrict__ tw) {
   using C = C_t<R>;
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NTH = 2 * CT * T;
+  constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = N * CT / NTH;
   constexpr int SEQ = sp_len(N);
-  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  static_assert(NTH % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   __shared__ typename RD::acc red[32];
@@ -692,63 +663,43 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   const RIn<R> rin(sc);  // read before arriving at the barrier (block 0 rewrites them after it)
   C* scur = S.at(p);
   C* sold = S.at(1 - p);
-  const int kx0 = blockIdx.x * CT;
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c;
+  const bool col = kx < NH;
 
-  // ---- A: gather W tile and the state tile
-  C vn[IT], vo[IT], nh[IT];
-  {
-    C va[IT], vb[IT];
+  // ---- A: the W columns and the state of this thread's rows ky = lane + i T
+  C g[2][E], vn[E], vo[E], nh[E];
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int y = idx / CT, kx = kx0 + idx % CT;
-      va[it] = mk<C>(0, 0);
-      vb[it] = mk<C>(0, 0);
-      vn[it] = mk<C>(0, 0);
-      vo[it] = mk<C>(0, 0);
-      if (kx < NH) {
-        const size_t off = (size_t)y * NH + kx;  // y doubles as ky: same tile mapping
-        va[it] = W0[off];
-        vb[it] = W1[off];
-        vn[it] = scur[off];
-        vo[it] = sold[off];
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int y = idx / CT, c = idx % CT;
-      sm[sp(y) * CTP + c] = va[it];
-      sm[SEQ * CTP + sp(y) * CTP + c] = vb[it];
+  for (int i = 0; i < E; ++i) {
+    g[0][i] = g[1][i] = vn[i] = vo[i] = mk<C>(0, 0);
+    if (col) {
+      const size_t off = (size_t)(lane + i * T) * NH + kx;
+      g[0][i] = W0[off];
+      g[1][i] = W1[off];
+      vn[i] = scur[off];
+      vo[i] = sold[off];
     }
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
+  fft_regs_multi<C, N, E, false, 2, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
   const R c0 = BDF1 ? (R)1 : (R)1.5;
   typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
-    nh[it] = mk<C>(0, 0);
-    if (kx >= NH) continue;
-    const C wx = sm[sp(ky) * CTP + c], wy = sm[SEQ * CTP + sp(ky) * CTP + c];
+  for (int i = 0; i < E; ++i) {
+    const int ky = lane + i * T;
+    nh[i] = mk<C>(0, 0);
+    if (!col) continue;
+    const C wx = g[0][i], wy = g[1][i];
     const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
     const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
-    nh[it] = mk<C>(uy, -ux);  // N_hat = -i (k~_x W_x + k~_y W_y)
+    nh[i] = mk<C>(uy, -ux);  // N_hat = -i (k~_x W_x + k~_y W_y)
     const R K2 = sym_K2<R>(kx, ky, N, pc);
     const R invA = sym_invA<R>(K2, c0, pc);
     C v;
-    if (BDF1) v = vn[it];
-    else v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+    if (BDF1) v = vn[i];
+    else v = mk<C>((R)2 * vn[i].x - (R)0.5 * vo[i].x, (R)2 * vn[i].y - (R)0.5 * vo[i].y);
     const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
-    const R n2 = nh[it].x * nh[it].x + nh[it].y * nh[it].y;
-    const R nv = nh[it].x * v.x + nh[it].y * v.y;
+    const R n2 = nh[i].x * nh[i].x + nh[i].y * nh[i].y;
+    const R nv = nh[i].x * v.x + nh[i].y * v.y;
     ag = RD::add(ag, w * (-K2 * invA) * n2);
     ae = RD::add(ae, w * nv * invA);
     at = RD::add(at, w * nv);
@@ -799,13 +750,12 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
 
   // ---- B: update, next extrapolation and its gradients, inverse DFT in y
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int ky = idx / CT, c = idx % CT, kx = kx0 + c;
+  for (int i = 0; i < E; ++i) {
+    const int ky = lane + i * T;
     C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
-    if (kx < NH) {
+    if (col) {
       const size_t off = (size_t)ky * NH + kx;
-      const C cur = vn[it];
+      const C cur = vn[i];
       C nw;
       if (off == 0) {
         // zero mode: A_0 = c0 and Delta kills N; BDF1 keeps phi_0, BDF2 gives a + (a - b)/3
@@ -814,8 +764,8 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
         nw = mk<C>((R)z, (R)0);
       } else {
         const R K2 = sym_K2<R>(kx, ky, N, pc);
-        if (BDF1) nw = bdf1_update<C, R>(cur, nh[it], K2, sym_invA<R>(K2, (R)1, pc), al);
-        else nw = bdf2_update<C, R>(cur, vo[it], nh[it], K2, sym_invA<R>(K2, (R)1.5, pc), al);
+        if (BDF1) nw = bdf1_update<C, R>(cur, nh[i], K2, sym_invA<R>(K2, (R)1, pc), al);
+        else nw = bdf2_update<C, R>(cur, vo[i], nh[i], K2, sym_invA<R>(K2, (R)1.5, pc), al);
       }
       sold[off] = nw;  // phi^{n+1} over phi^{n-1}
       const C ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
@@ -823,23 +773,16 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
       g0 = mk<C>(-ktx * ph.y, ktx * ph.x);
       g1 = mk<C>(-kty * ph.y, kty * ph.x);
     }
-    sm[sp(ky) * CTP + c] = g0;
-    sm[SEQ * CTP + sp(ky) * CTP + c] = g1;
+    g[0][i] = g0;
+    g[1][i] = g1;
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
+  fft_regs_multi<C, N, E, true, 2, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
+  if (col) {
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int y = idx / CT, c = idx % CT, kx = kx0 + c;
-    if (kx < NH) {
-      W0[(size_t)y * NH + kx] = sm[sp(y) * CTP + c];
-      W1[(size_t)y * NH + kx] = sm[SEQ * CTP + sp(y) * CTP + c];
+    for (int i = 0; i < E; ++i) {
+      const size_t off = (size_t)(lane + i * T) * NH + kx;
+      W0[off] = g[0][i];
+      W1[off] = g[1][i];
     }
   }
 }

@@ -95,7 +95,7 @@ int run(const Params& P, const double* phi, double* out, cudaStream_t st, unsign
   k2d_col_fwd<double, N, E, CT, CF_TO_STATE><<<GCOL, CT * T, scol, st>>>(P, S, w0, w1, nullptr, nullptr, nullptr, 0,
                                                                           sc, nullptr, tw, 0);
   k_put_zero_modes<double><<<1, 1, 0, st>>>(S, sc);
-  k2d_col_inv<double, N, E, CT, CI_GRAD><<<GCOL, 2 * CT * T, 2 * scol, st>>>(P, S, nullptr, w0, w1, sc, tw, 0);
+  k2d_col_inv<double, N, E, CT, CI_GRAD><<<GCOL, CT * T, 2 * scol, st>>>(P, S, nullptr, w0, w1, sc, tw, 0);
   k2d_row<double, N, E, RPC, RW_ENERGY><<<GROW, RPC * T, srow, st>>>(P, w0, w1, partE, sc, tw, nullptr);
   k2d_norms<double><<<gpw, PW, 0, st>>>(P, S, sc, partN);
   k_scalar_op<double><<<1, 32, 0, st>>>(P, sc, SO_ENERGY, partE, GROW, partN, gpw, 0, 0.0, 0.0);

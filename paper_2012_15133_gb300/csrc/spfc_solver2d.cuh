@@ -29,13 +29,15 @@ namespace spfc {
 // the others are alternatives for N >= 128 that the autotuner times:
 //   1: one column per block (twice the blocks), 2: 4 values per lane
 //   (twice the threads per sequence), 3: 16 values per lane, 4 columns,
-//   4: 8 values per lane, 4 columns (full 32-byte sectors per row in float32).
+//   4: 8 values per lane, 4 columns (full 32-byte sectors per row in float32),
+//   5: 4 values per lane and the fewest columns that fill a warp (the most
+//   blocks and threads: for the float64 path, bound by its arithmetic).
 template <int N, int SCHED = 0> struct Shape2D {
-  static constexpr int E = (SCHED == 2) ? 4 : ((SCHED == 3) ? 16 : 8);  // 0, 1 and 4 use 8
+  static constexpr int E = (SCHED == 2 || SCHED == 5) ? 4 : ((SCHED == 3) ? 16 : 8);  // 0, 1 and 4 use 8
   static constexpr int T = N / E;
   static constexpr int CT0 = (N >= 256) ? 2 : ((32 / T > 4) ? 32 / T : 4);
   static constexpr int CT1 = (32 / T > 1) ? 32 / T : 1;  // fewest columns that fill a warp
-  static constexpr int CT = (SCHED == 1) ? CT1 : ((SCHED == 3 || SCHED == 4) ? 4 : CT0);
+  static constexpr int CT = (SCHED == 1 || SCHED == 5) ? CT1 : ((SCHED == 3 || SCHED == 4) ? 4 : CT0);
   static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
   static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
   static_assert(sizeof(Red<float>::store) == sizeof(double) && sizeof(Red<double>::store) == sizeof(double),
@@ -162,7 +164,7 @@ class Solver2D final : public SolverBase {
       int dev = 0, nsm = 0, per = 0;
       SPFC_CK(cudaGetDevice(&dev));
       SPFC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-      SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_col_fused<R, N, E, CT, false>, 2 * CT * T,
+      SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_col_fused<R, N, E, CT, false>, CT * T,
                                                              smem_col(2)));
       if (per * nsm < GCOL) {
         err = "the fused column pass does not fit co-resident on this GPU";
@@ -391,11 +393,11 @@ class Solver2D final : public SolverBase {
   int launch_col_inv(int mode, int which) {
     switch (mode) {
       case CI_STEP:
-        SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, false, P, S_, Nhat_,
+        SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, CT * T, smem_col(2), st_, pdl_, false, P, S_, Nhat_,
                          W_[0], W_[1], sc_, tw_, which));
         break;
       case CI_GRAD:
-        k2d_col_inv<R, N, E, CT, CI_GRAD><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
+        k2d_col_inv<R, N, E, CT, CI_GRAD><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
         break;
       default:
         k2d_col_inv<R, N, E, CT, CI_FIELD><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
@@ -424,14 +426,14 @@ class Solver2D final : public SolverBase {
   int launch_col_fwd(int mode, int target) {
     switch (mode) {
       case CF_BDF2:
-        SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, 2 * CT * T, smem_col(2), st_, pdl_, false, P, S_, W_[0],
+        SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, CT * T, smem_col(2), st_, pdl_, false, P, S_, W_[0],
                          W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target));
         break;
       case CF_BDF1:
-        k2d_col_fwd<R, N, E, CT, CF_BDF1><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        k2d_col_fwd<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
         break;
       case CF_NHAT:
-        k2d_col_fwd<R, N, E, CT, CF_NHAT><<<GCOL, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
+        k2d_col_fwd<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
         break;
       default:
         k2d_col_fwd<R, N, E, CT, CF_TO_STATE><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_, target);
@@ -505,10 +507,10 @@ class Solver2D final : public SolverBase {
 
   int launch_fused(bool bdf1) {
     if (bdf1)
-      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, true>, GCOL, 2 * CT * T, smem_col(2), st_, false, true, P, S_,
+      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, true>, GCOL, CT * T, smem_col(2), st_, false, true, P, S_,
                        W_[0], W_[1], partG_, partE_, nE_, sc_, sync64_, tw_));
     else
-      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, false>, GCOL, 2 * CT * T, smem_col(2), st_, false, true, P, S_,
+      SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, false>, GCOL, CT * T, smem_col(2), st_, false, true, P, S_,
                        W_[0], W_[1], partG_, partE_, nE_, sc_, sync64_, tw_));
     return 0;
   }
@@ -593,7 +595,7 @@ class Solver2D final : public SolverBase {
 };
 
 // Number of launch schedules compiled for a 2D grid size.
-inline int num_schedules_2d(int N) { return (N >= 256) ? 5 : ((N == 128) ? 2 : 1); }
+inline int num_schedules_2d(int N) { return (N >= 128) ? 6 : 1; }
 
 template <typename R, int N, int SCHED>
 SolverBase* new_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
@@ -618,6 +620,7 @@ SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int
     case 2: return new_solver_2d<R, N, 2>(P, st, status, err);
     case 3: return new_solver_2d<R, N, 3>(P, st, status, err);
     case 4: return new_solver_2d<R, N, 4>(P, st, status, err);
+    case 5: return new_solver_2d<R, N, 5>(P, st, status, err);
     default: return new_solver_2d<R, N, 0>(P, st, status, err);
   }
 }
@@ -646,7 +649,7 @@ SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int schedule, int* 
     case 32: return new_solver_2d<R, 32, 0>(P, st, status, err);
     case 64: return new_solver_2d<R, 64, 0>(P, st, status, err);
     case 128:
-      return schedule == 1 ? new_solver_2d<R, 128, 1>(P, st, status, err) : new_solver_2d<R, 128, 0>(P, st, status, err);
+      return make_solver_2d_n<R, 128>(P, st, schedule, status, err);
     case 256:
       return F64 ? make_solver_2d_f64_256(P, st, schedule, status, err) : make_solver_2d_f32_256(P, st, schedule, status, err);
     default:
