@@ -415,6 +415,25 @@ __device__ __forceinline__ typename Red<R>::acc block_red(typename Red<R>::acc v
   return t;
 }
 
+// K block sums at once (the same tree as K calls of block_red, sharing the
+// barriers); results in thread 0 (v overwritten).
+template <typename R, int K>
+__device__ __forceinline__ void block_red_multi(typename Red<R>::acc* v, typename Red<R>::acc (*scratch)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_red<R>(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[k][wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_red<R>((lane < nw) ? scratch[k][lane] : Red<R>::zero());
+  }
+}
+
 // Sum of n stored accumulators by one warp, fixed order; returned as double
 // to every lane. L1 is bypassed (values written by other blocks).
 template <typename R>

@@ -248,7 +248,7 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
   using RD = Red<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ typename RD::acc red[32];
+  __shared__ typename RD::acc red2[2][32];
 
   pdl_wait();
   pdl_trigger();
@@ -333,12 +333,12 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
         W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);      // W_y = (Z_k - conj Z_{N-k}) / (2i)
       }
     }
-    const typename RD::acc t2 = block_red<R>(acc2, red);
-    const typename RD::acc t1 = block_red<R>(acc1, red);
+    typename RD::acc t21[2] = {acc2, acc1};
+    block_red_multi<R, 2>(t21, red2);
     if (threadIdx.x == 0) {
       typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
-      ps[blockIdx.x] = t2;
-      ps[gridDim.x + blockIdx.x] = t1;
+      ps[blockIdx.x] = t21[0];
+      ps[gridDim.x + blockIdx.x] = t21[1];
     }
   }
 }
@@ -383,13 +383,28 @@ template <> struct RIn<float> {
   __device__ RIn() : r1{0.f, 0.f}, r0{0.f, 0.f} {}
 };
 
+// The solve in two parts: E_1, S = sqrt(E_1) and 1/S need only the row
+// pass's sums (q[0], q[1]); the rest needs gamma, eta, theta (qg[0..2]).
+template <typename R> struct SolvePre;
+template <> struct SolvePre<double> { double E1, S, iS; };
+template <> struct SolvePre<float> { ff E1, S, iS; };
+
 // float64 path: float64 scalar algebra, one square root and two divisions.
-__device__ inline SolveOut<double> sav_solve(const Params& P, const double* q, bool bdf1, const RIn<double>& rin) {
-  SolveOut<double> o;
-  const double s2 = q[0], s1 = q[1], gs = q[2], es = q[3], ts = q[4];
-  o.E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
+__device__ inline SolvePre<double> sav_solve_pre(const Params& P, const double* q) {
+  SolvePre<double> o;
+  o.E1 = P.hd * (0.25 * P.beta * q[0] - q[1]) + P.C * P.vol;
   o.S = sqrt(o.E1);
-  const double iS = 1.0 / o.S;
+  o.iS = 1.0 / o.S;
+  return o;
+}
+
+__device__ inline SolveOut<double> sav_solve_post(const Params& P, const SolvePre<double>& pre, const double* qg,
+                                                  bool bdf1, const RIn<double>& rin) {
+  SolveOut<double> o;
+  const double gs = qg[0], es = qg[1], ts = qg[2];
+  o.E1 = pre.E1;
+  o.S = pre.S;
+  const double iS = pre.iS;
   o.gamma = P.vol * gs; o.eta = P.vol * es; o.theta = P.vol * ts;
   const double dt = P.dt;
   o.denom = 1.0 - 0.5 * dt * o.gamma * (iS * iS);
@@ -410,15 +425,29 @@ __device__ inline SolveOut<double> sav_solve(const Params& P, const double* q, b
   return o;
 }
 
+__device__ inline SolveOut<double> sav_solve(const Params& P, const double* q, bool bdf1, const RIn<double>& rin) {
+  return sav_solve_post(P, sav_solve_pre(P, q), q + 2, bdf1, rin);
+}
+
 // float32-bulk path: the same algebra in float-float (float32 pipes; about
 // 48 significant bits, float64-class for these well-conditioned formulas).
-__device__ inline SolveOut<float> sav_solve(const Params& P, const float2* q, bool bdf1, const RIn<float>& rin) {
-  SolveOut<float> o;
-  const ff s2{q[0].x, q[0].y}, s1{q[1].x, q[1].y}, gs{q[2].x, q[2].y}, es{q[3].x, q[3].y}, ts{q[4].x, q[4].y};
-  const ff vol = ffp(P.vol_ff), dt = ffp(P.dt_ff);
+__device__ inline SolvePre<float> sav_solve_pre(const Params& P, const float2* q) {
+  SolvePre<float> o;
+  const ff s2{q[0].x, q[0].y}, s1{q[1].x, q[1].y};
   o.E1 = ff_add(ff_mul(ffp(P.hd_ff), ff_sub(ff_mul(ffp(P.qbeta_ff), s2), s1)), ffp(P.Cvol_ff));
   o.S = ff_sqrt(o.E1);
-  const ff iS = ff_div(ff_make(1.f), o.S);
+  o.iS = ff_div(ff_make(1.f), o.S);
+  return o;
+}
+
+__device__ inline SolveOut<float> sav_solve_post(const Params& P, const SolvePre<float>& pre, const float2* qg,
+                                                 bool bdf1, const RIn<float>& rin) {
+  SolveOut<float> o;
+  const ff gs{qg[0].x, qg[0].y}, es{qg[1].x, qg[1].y}, ts{qg[2].x, qg[2].y};
+  const ff vol = ffp(P.vol_ff), dt = ffp(P.dt_ff);
+  o.E1 = pre.E1;
+  o.S = pre.S;
+  const ff iS = pre.iS;
   o.gamma = ff_mul(vol, gs); o.eta = ff_mul(vol, es); o.theta = ff_mul(vol, ts);
   o.denom = ff_sub(ff_make(1.f), ff_mulf(ff_mul(ff_mul(dt, o.gamma), ff_mul(iS, iS)), 0.5f));
   ff rho;
@@ -436,6 +465,10 @@ __device__ inline SolveOut<float> sav_solve(const Params& P, const float2* q, bo
   o.ok = ff_isfinite(o.E1) && o.E1.hi > 0.f && ff_isfinite(o.gamma) && ff_isfinite(o.eta) &&
          ff_isfinite(o.theta) && o.denom.hi > 0.f && ff_isfinite(o.r_new);
   return o;
+}
+
+__device__ inline SolveOut<float> sav_solve(const Params& P, const float2* q, bool bdf1, const RIn<float>& rin) {
+  return sav_solve_post(P, sav_solve_pre(P, q), q + 2, bdf1, rin);
 }
 
 // Write a solve into the record: r shifts, p and pending as given.
@@ -652,7 +685,6 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   static_assert(NTH % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ typename RD::acc red[32];
   __shared__ typename RD::acc red5[5][32];
   __shared__ typename RD::acc qres[5];
   __shared__ int bar_ok;
@@ -680,6 +712,20 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
       vo[i] = sold[off];
     }
   }
+  // the row pass's E_1 sums (complete before this launch), reduced while the
+  // loads above are in flight; the float64 zero modes for the update
+  {
+    using ST = typename RD::store;
+    const ST* pe = reinterpret_cast<const ST*>(partE);
+    const ST* arr[2] = {pe, pe + nE};
+    const int cnt[2] = {nE, nE};
+    block_red_arrays<R, 2>(arr, cnt, qres, red5);
+  }
+  double zm_n = 0.0, zm_o = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    zm_n = sc->zm[p];
+    zm_o = sc->zm[1 - p];
+  }
   fft_regs_multi<C, N, E, false, 2, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
   const R c0 = BDF1 ? (R)1 : (R)1.5;
   typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
@@ -704,23 +750,25 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
     ae = RD::add(ae, w * nv * invA);
     at = RD::add(at, w * nv);
   }
-  const typename RD::acc tg = block_red<R>(ag, red);
-  const typename RD::acc te = block_red<R>(ae, red);
-  const typename RD::acc tt = block_red<R>(at, red);
+  typename RD::acc t3[3] = {ag, ae, at};
+  block_red_multi<R, 3>(t3, red5);
 
   // ---- grid barrier: publish the partial sums, arrive, wait for all blocks
-  // (bounded); then every block reduces all partial sums in the same fixed
-  // order and solves the scalar system itself (identical results), and block
-  // 0 alone writes the record. sync64[0] counts arrivals monotonically, so it
-  // never needs a reset: this launch's target is the next multiple of the grid.
+  // (bounded; thread 0 takes E_1 and S meanwhile); then every block reduces
+  // the gamma, eta, theta partial sums in the same fixed order and finishes
+  // the scalar solve itself (identical results), and block 0 alone writes the
+  // record. sync64[0] counts arrivals monotonically, so it never needs a
+  // reset: this launch's target is the next multiple of the grid.
+  SolvePre<R> pre;
   if (threadIdx.x == 0) {
     typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
-    ps[blockIdx.x] = tg;
-    ps[gridDim.x + blockIdx.x] = te;
-    ps[2 * gridDim.x + blockIdx.x] = tt;
+    ps[blockIdx.x] = t3[0];
+    ps[gridDim.x + blockIdx.x] = t3[1];
+    ps[2 * gridDim.x + blockIdx.x] = t3[2];
     __threadfence();
     const unsigned long long prev = atomicAdd(sync64, 1ull);
     const unsigned long long target = (prev / gridDim.x + 1ull) * gridDim.x;
+    pre = sav_solve_pre(P, qres);  // E_1, S, 1/S: overlaps the wait
     const bool ok = wait_counter(sync64, target, kSpinLimit);
     if (!ok) atomicExch(&sc->status, (int)DEV_TIMEOUT);
     __threadfence();
@@ -730,16 +778,15 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   if (!bar_ok) return;
   {
     using ST = typename RD::store;
-    const ST* pe = reinterpret_cast<const ST*>(partE);
     const ST* pg = reinterpret_cast<const ST*>(partG);
-    const ST* arr[5] = {pe, pe + nE, pg, pg + gridDim.x, pg + 2 * gridDim.x};
-    const int cnt[5] = {nE, nE, (int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
-    block_red_arrays<R, 5>(arr, cnt, qres, red5);
+    const ST* arr[3] = {pg, pg + gridDim.x, pg + 2 * gridDim.x};
+    const int cnt[3] = {(int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
+    block_red_arrays<R, 3>(arr, cnt, qres + 2, red5);
   }
   __shared__ R alpha_s;
   __shared__ int solve_ok;
   if (threadIdx.x == 0) {
-    const SolveOut<R> o = sav_solve(P, qres, BDF1, rin);
+    const SolveOut<R> o = sav_solve_post(P, pre, qres + 2, BDF1, rin);
     alpha_s = (R)o.alpha;
     solve_ok = o.ok;
     if (blockIdx.x == 0) sav_commit(sc, o, 1 - p, PEND_NONE);
@@ -759,7 +806,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
       C nw;
       if (off == 0) {
         // zero mode: A_0 = c0 and Delta kills N; BDF1 keeps phi_0, BDF2 gives a + (a - b)/3
-        const double z = BDF1 ? sc->zm[p] : zero_mode_update(sc->zm[p], sc->zm[1 - p]);
+        const double z = BDF1 ? zm_n : zero_mode_update(zm_n, zm_o);
         sc->zm[1 - p] = z;
         nw = mk<C>((R)z, (R)0);
       } else {
