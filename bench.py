@@ -233,6 +233,43 @@ def measure_cube(steps, warmup, precision, peak, flush):
                          "note": "step level: 27 half-spectrum passes (6 kernels)"}}
 
 
+def measure_patterns(precision="fp32", n=256):
+    """The paper's square-pattern run (Sec. 5.2): a = 0.5 on [0, 100]^2,
+    phi0 = 0.05 (2 r - 1) (seed 21), dt = 0.01 up to t = 1000, then the copy
+    restart and dt = 0.02 up to t = 21000; N = 256. Point-steps/s over the
+    1.1 M steps (CUDA events around the step chunks), the energies at the
+    paper's snapshot times and the final pattern measures."""
+    import torch
+    from paper_2012_15133_gb300 import Solver
+    from paper_2012_15133_gb300.analysis import bond_order, peak_wavenumber
+    from seeded_inputs import noisy_field
+    s = Solver(2, n, 100.0, 0.5, 1.0, 0.01, precision)
+    s.init(noisy_field((n, n), 0.0, 0.05, 21), "copy")
+    st = torch.cuda.current_stream()
+    t, ms, steps, energies = 0.0, 0.0, 0, {}
+    for t_end in (10, 100, 1000, 3000, 9000, 15000, 21000):
+        if t_end > 1000 and s.dt < 0.015:
+            s.dt_change(0.02)
+        k = int(round((t_end - t) / s.dt))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(k)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        steps += k
+        t = t_end
+        e = s.energy()
+        energies[str(t_end)] = {"E_N": e[0], "E_breve": e[2]}
+    phi = s.get_field(0)
+    order, npk = bond_order(phi, 100.0)
+    return {"workload": "square-pattern run of Sec. 5.2: a=0.5, L=100, N=256, phi0=0.05(2r-1) seed 21, dt 0.01 "
+                        "to t=1000, copy restart, dt 0.02 to t=21000",
+            "value": n * n * steps / (ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps, "precision": precision,
+            "energies": energies, "peak_wavenumber": peak_wavenumber(phi, 100.0), "maxima": npk,
+            "psi4": order[4], "psi6": order[6]}
+
+
 def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs=16, jumps=100, K=20,
                       check_every=5, tol=1e-3):
     """The learned surrogate at 256^2 (L = 128, the ensemble recipe on one grid
@@ -412,6 +449,8 @@ def run_ours(args):
         extras["ensemble"] = measure_ensemble(min(args.steps, 200), args.warmup, args.precision, peak, rank, world,
                                               dist)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
+        if rank == 0:
+            extras["patterns"] = measure_patterns()
         if not args.no_surrogate and rank == 0:
             del flush
             extras["surrogate"] = measure_surrogate(modes=16)
