@@ -164,6 +164,7 @@ class Model:
         self.beta = float(beta)
         self.C = 1.0 + 1.0 / self.beta       # C_beta; 2 at beta = 1
         self.nonlinear = nonlinear            # test switch: False sets N_N := 0
+        self.stab = 0.0                       # A of the stabilised scheme (Sec. 5.2); 0: Sec. 2
 
     def L_op(self, f):
         """L_N f = a f + Delta_N^2 f (Sec. 2.1, before eq. spectral-coll-6)."""
@@ -226,14 +227,24 @@ class Model:
 # ---------------------------------------------------------------------------
 
 def A_inv(model: Model, f, dt: float, c0: float):
-    """Solve (c0 I - dt Delta_N L_N) u = f by division in Fourier space.
+    """Solve (c0 I - dt Delta_N L_N - A dt Delta_N) u = f by division in
+    Fourier space (A = model.stab, 0 for the scheme of Sec. 2).
 
     c0 = 3/2 gives A_N of eq. solver-1; c0 = 1 the first-order operator.
-    The symbol is c0 + dt |k|^2 (a + |k|^4) > 0.
+    The symbol is c0 + dt |k|^2 (a + |k|^4) + A dt |k|^2 > 0.
     """
     g = model.g
-    sym = c0 + dt * g.K2 * (model.a + g.K2 ** 2)
+    sym = c0 + dt * g.K2 * (model.a + g.K2 ** 2) + model.stab * dt * g.K2
     return g.idft(g.dft(f) / sym)
+
+
+def stab_rhs(model: Model, dt: float, phi_n):
+    """Right-hand-side part of the stabiliser of Sec. 5.2: the left side of (a)
+    times dt gains - A dt Delta_N (phi^{n+1} - phi^n), whose phi^n part moves to
+    the right as - A dt Delta_N phi^n (zero for the scheme of Sec. 2)."""
+    if not model.stab:
+        return 0.0
+    return -model.stab * dt * model.g.lap(phi_n)
 
 
 def bdf2_sav_step(model: Model, dt: float, phi_n, phi_nm1, r_n: float, r_nm1: float,
@@ -251,7 +262,7 @@ def bdf2_sav_step(model: Model, dt: float, phi_n, phi_nm1, r_n: float, r_nm1: fl
     Nh = model.N_op(phi_hat)
     lapN = g.lap(Nh)
     # right-hand side g_N^n after substituting eq. solver-2 into eq. solver-1
-    base = 2.0 * phi_n - 0.5 * phi_nm1
+    base = 2.0 * phi_n - 0.5 * phi_nm1 + stab_rhs(model, dt, phi_n)
     if forcing is not None:
         base = base + dt * forcing
     coef = (4.0 / 3.0) * r_n - (1.0 / 3.0) * r_nm1 \
@@ -281,7 +292,7 @@ def bdf1_sav_step(model: Model, dt: float, phi0, forcing=None):
     r0 = sqE1
     Nh = model.N_op(phi0)
     lapN = g.lap(Nh)
-    base = phi0 if forcing is None else phi0 + dt * forcing
+    base = (phi0 if forcing is None else phi0 + dt * forcing) + stab_rhs(model, dt, phi0)
     coef = r0 - g.inner(Nh, phi0) / (2.0 * sqE1)
     gN = (dt / sqE1) * coef * lapN + base
     Ainv_g = A_inv(model, gN, dt, 1.0)
@@ -316,9 +327,10 @@ def copy_start(model: Model, phi0):
 class Oracle:
     """State (phi^n, phi^{n-1}, r^n, r^{n-1}) advanced by bdf2_sav_step."""
 
-    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive"):
+    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive", stab=0.0):
         self.grid = Grid(d, n, L, dft=dft)
         self.model = Model(self.grid, eps, beta, nonlinear=nonlinear)
+        self.model.stab = float(stab)
         self.dt = float(dt)
         self.phi = self.phi_prev = None
         self.r = self.r_prev = None

@@ -393,3 +393,104 @@ def self_convergence_ratio() -> float:
     a = np.linalg.norm(sols[0] - sols[1])
     b = np.linalg.norm(sols[1] - sols[2])
     return float(a / b)
+
+
+# --- the stabilised scheme (Sec. 5.2: - A dt Delta_N (phi^{n+1} - phi^n)) ---------
+
+STAB_A = 3.0
+
+
+def pin_stab_residual() -> float:
+    """Plug (phi^{n+1}, r^{n+1}) of the stabilised scheme into
+    (3 phi^{n+1} - 4 phi^n + phi^{n-1})/(2 dt) - A Delta_N (phi^{n+1} - phi^n)
+    = Delta_N mu^{n+1} and the unchanged r-equation (b), for the BDF1 start
+    (first-order form) and three BDF2 steps."""
+    o, phi0 = _case()
+    o.model.stab = STAB_A
+    m, g, dt = o.model, o.grid, o.dt
+    o.start(phi0, "bdf1")
+    sq = math.sqrt(m.E1(phi0))
+    Nh = m.N_op(phi0)
+    D = o.phi - phi0
+    terms = (D / dt, STAB_A * g.lap(o.phi - phi0), g.lap(o.r / sq * Nh), g.lap(m.L_op(o.phi)))
+    res = terms[0] - terms[1] - terms[2] - terms[3]
+    worst = float(np.max(np.abs(res))) / max(float(np.max(np.abs(t))) for t in terms)
+    for _ in range(3):
+        pn, pnm1, rn, rnm1 = o.phi, o.phi_prev, o.r, o.r_prev
+        o.step()
+        pnp1, rnp1 = o.phi, o.r
+        ph = 2 * pn - pnm1
+        sq = math.sqrt(m.E1(ph))
+        Nh = m.N_op(ph)
+        D = 1.5 * pnp1 - 2 * pn + 0.5 * pnm1
+        terms = (D / dt, STAB_A * g.lap(pnp1 - pn), g.lap(rnp1 / sq * Nh), g.lap(m.L_op(pnp1)))
+        res = terms[0] - terms[1] - terms[2] - terms[3]
+        worst = max(worst, float(np.max(np.abs(res))) / max(float(np.max(np.abs(t))) for t in terms))
+        resb = (1.5 * rnp1 - 2 * rn + 0.5 * rnm1) / dt - g.inner(Nh, D / dt) / (2 * sq)
+        worst = max(worst, abs(resb) / ((1.5 * abs(rnp1) + 2 * abs(rn) + 0.5 * abs(rnm1)) / dt))
+    return worst
+
+
+def pin_stab_dissipation() -> float:
+    """The stabilised equation is (a) with mu~ = mu + A (phi^{n+1} - phi^n):
+    testing it with mu~ gives the identity eq. eng stab-5 with -dt ||grad mu~||^2
+    and the extra term - A <D, phi^{n+1} - phi^n>, D = 3/2 phi^{n+1} - 2 phi^n
+    + 1/2 phi^{n-1}. Returns the worst |residual| / |E^{n+1} - E^n|."""
+    o, phi0 = _case(dt=0.1)
+    o.model.stab = STAB_A
+    o.start(phi0, "bdf1")
+    m, g, dt = o.model, o.grid, o.dt
+    worst = 0.0
+    for _ in range(4):
+        pn, pnm1, rn, rnm1 = o.phi, o.phi_prev, o.r, o.r_prev
+        Eold = m.E_mod(pn, pnm1, rn, rnm1)
+        ph = 2 * pn - pnm1
+        sq = math.sqrt(m.E1(ph))
+        Nh = m.N_op(ph)
+        o.step()
+        pnp1, rnp1 = o.phi, o.r
+        Enew = m.E_mod(pnp1, pn, rnp1, rn)
+        mut = m.L_op(pnp1) + rnp1 / sq * Nh + STAB_A * (pnp1 - pn)
+        dd = pnp1 - 2 * pn + pnm1
+        D = 1.5 * pnp1 - 2 * pn + 0.5 * pnm1
+        rhs = -0.25 * m.L_norm_sq(dd) - 0.5 * (rnp1 - 2 * rn + rnm1) ** 2 \
+            - dt * g.inner(-g.lap(mut), mut) - STAB_A * g.inner(D, pnp1 - pn)
+        worst = max(worst, abs((Enew - Eold) - rhs) / abs(Enew - Eold))
+    return worst
+
+
+def pin_stab_linear_closed_form() -> float:
+    """N_N off, stabiliser on: each mode follows (3/2 + lam + s) x_{n+1} =
+    (2 + s) x_n - x_{n-1}/2 with s = A dt |k|^2, solved by its two roots."""
+    o = so.Oracle(2, 12, 6.0, 0.3, 1.0, 0.02, nonlinear=False, stab=STAB_A)
+    g = o.grid
+    phi0 = noisy_field(g.shape, 0.1, 0.5, 9)
+    phim1 = noisy_field(g.shape, 0.1, 0.5, 10)
+    o.set_state(phi0, phim1, 2.0, 2.0)
+    nsteps = 25
+    o.step(nsteps)
+    x0, xm1 = g.dft(phi0), g.dft(phim1)
+    lam = o.dt * g.K2 * (o.model.a + g.K2 ** 2)
+    sk = STAB_A * o.dt * g.K2
+    out = g.dft(o.phi)
+    worst = 0.0
+    for idx in np.ndindex(*g.shape):
+        A2, B1 = 1.5 + float(lam[idx]) + float(sk[idx]), 2.0 + float(sk[idx])
+        disc = cmath.sqrt(B1 * B1 - 2.0 * A2)
+        z1, z2 = (B1 + disc) / (2 * A2), (B1 - disc) / (2 * A2)
+        det = 1 / z2 - 1 / z1
+        c1 = (x0[idx] / z2 - xm1[idx]) / det
+        c2 = (xm1[idx] - x0[idx] / z1) / det
+        ref = c1 * z1 ** nsteps + c2 * z2 ** nsteps
+        worst = max(worst, abs(out[idx] - ref) / max(abs(x0[idx]), 1e-12))
+    return worst
+
+
+def stab_zero_is_the_plain_scheme() -> float:
+    """stab = 0 reproduces the scheme of Sec. 2 bit for bit."""
+    o1, phi0 = _case()
+    o2, _ = _case()
+    o2.model.stab = 0.0
+    o1.start(phi0, "bdf1").step(3)
+    o2.start(phi0, "bdf1").step(3)
+    return float(np.max(np.abs(o1.phi - o2.phi)))

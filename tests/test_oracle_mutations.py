@@ -21,6 +21,9 @@ PINS = [
     (P.constant_state_error, lambda v: v < 1e-13),
     (P.min_E1_margin, lambda v: v >= -1e-14),
     (lambda: P.manufactured_slope((50, 100)), lambda v: -2.2 < v < -1.8),
+    (P.pin_stab_residual, lambda v: v < 1e-10),
+    (P.pin_stab_dissipation, lambda v: v < 1e-9),
+    (P.pin_stab_linear_closed_form, lambda v: v < 1e-12),
 ]
 
 
@@ -134,10 +137,34 @@ def _m_laplacian_drops_nyquist(mp):
     mp.setattr(so.Grid, "lap", lap)
 
 
+def _m_stab_rhs_sign(mp):
+    orig = so.stab_rhs
+    mp.setattr(so, "stab_rhs", lambda model, dt, phi: -orig(model, dt, phi) if model.stab else 0.0)
+
+
+def _m_stab_rhs_dropped(mp):
+    mp.setattr(so, "stab_rhs", lambda model, dt, phi: 0.0)
+
+
+def _m_stab_symbol_dropped(mp):
+    def A_inv(model, f, dt, c0):
+        g = model.g
+        return g.idft(g.dft(f) / (c0 + dt * g.K2 * (model.a + g.K2 ** 2)))
+    mp.setattr(so, "A_inv", A_inv)
+
+
+def _m_stab_symbol_without_dt(mp):
+    def A_inv(model, f, dt, c0):
+        g = model.g
+        return g.idft(g.dft(f) / (c0 + dt * g.K2 * (model.a + g.K2 ** 2) + model.stab * g.K2))
+    mp.setattr(so, "A_inv", A_inv)
+
+
 MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_axis,
              _m_wrong_bdf2_operator, _m_wrong_r_coefficient, _m_E1_constant_ignores_beta,
              _m_energy_quarter_dropped, _m_first_order_extrapolation,
-             _m_dft_missing_normalisation, _m_linear_operator_sign, _m_laplacian_drops_nyquist]
+             _m_dft_missing_normalisation, _m_linear_operator_sign, _m_laplacian_drops_nyquist,
+             _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt]
 
 
 def test_pins_pass_unmutated():

@@ -82,3 +82,19 @@ def test_second_order_manufactured_solution():
 def test_self_convergence_ratio():
     ratio = P.self_convergence_ratio()
     assert 3.6 < ratio < 4.4, ratio
+
+
+def test_stabilised_scheme_residual():
+    assert P.pin_stab_residual() < 1e-10
+
+
+def test_stabilised_dissipation_identity():
+    assert P.pin_stab_dissipation() < 1e-9
+
+
+def test_stabilised_linear_part_closed_form():
+    assert P.pin_stab_linear_closed_form() < 1e-12
+
+
+def test_zero_stabiliser_is_the_plain_scheme():
+    assert P.stab_zero_is_the_plain_scheme() == 0.0
