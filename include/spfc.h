@@ -125,6 +125,17 @@ int spfc_get_field(spfc_t h, double* out, int out_on_device, int which);
 /* Change dt and restart the two-level scheme with phi^{n-1} = phi^n (Sec. 5.2). */
 int spfc_dt_change(spfc_t h, double dt_new);
 
+/* Stabilised scheme (Sec. 5.2, the remedy for rough initial data): the
+ * dt-multiplied equation (a) gains - A dt Delta_N (phi^{n+1} - phi^n) on its
+ * left side, i.e. the symbol A_N becomes 3/2 + dt |k|^2 (a + |k|^4) + A dt |k|^2
+ * and the right-hand side gains - A dt Delta_N phi^n; the r-equation is
+ * unchanged. A >= 0 (0, the default, is the scheme of Sec. 2). Set before
+ * spfc_init it also applies to the start-up step; set later it applies to the
+ * steps that follow (a pending update is completed first). Checkpoints record
+ * A and spfc_load requires the same A. SPFC_EINVAL for a negative or
+ * non-finite A. */
+int spfc_set_stabilization(spfc_t h, double A);
+
 /* Write / read a checkpoint: the exact device state (both spectral levels in the
  * handle's precision, r^n, r^{n-1}, the step count) plus the grid and parameters.
  * A resumed run continues bit-identically. spfc_load rejects a file whose grid,

@@ -142,6 +142,17 @@ int spfc_get_field(spfc_t h, double* out, int on_device, int which) {
   return wrap(h, h->s->get_field(out, on_device != 0, which));
 }
 
+int spfc_set_stabilization(spfc_t h, double A) {
+  if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
+  if (!(A >= 0.0) || !std::isfinite(A)) return fail(h, SPFC_EINVAL, "the stabiliser A must be finite and >= 0");
+  if (!h->s->inited) {  // before spfc_init: the start-up step uses it too
+    h->s->P.stab = A;
+    spfc::fill_float_params(&h->s->P);
+    return SPFC_OK;
+  }
+  return wrap(h, h->s->set_stab(A));
+}
+
 int spfc_dt_change(spfc_t h, double dt_new) {
   if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
   if (!(dt_new > 0.0) || !std::isfinite(dt_new)) return fail(h, SPFC_EINVAL, "dt must be positive");
@@ -152,7 +163,7 @@ int spfc_dt_change(spfc_t h, double dt_new) {
 // Checkpoint file: magic, then int32 {d, N, precision, blob bytes}, then
 // float64 {kf0, kf1, kf2, dt, a, beta}, then the raw state blob (scalar
 // record and both spectral levels), so that a resumed run is bit-identical.
-static const char kMagic[8] = {'S', 'P', 'F', 'C', 'C', 'K', 'P', '2'};
+static const char kMagic[8] = {'S', 'P', 'F', 'C', 'C', 'K', 'P', '3'};
 
 int spfc_save(spfc_t h, const char* path) {
   if (!h || !path) return fail(h, SPFC_EINVAL, "NULL argument");
@@ -164,7 +175,7 @@ int spfc_save(spfc_t h, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(h, SPFC_EINVAL, std::string("cannot open ") + path);
   const int32_t hdr[4] = {P.d, P.N, h->s->precision, (int32_t)blob.size()};
-  const double sv[6] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta};
+  const double sv[7] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab};
   bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
             std::fwrite(sv, sizeof(sv), 1, fp) == 1 && std::fwrite(blob.data(), 1, blob.size(), fp) == blob.size();
   ok = (std::fclose(fp) == 0) && ok;
@@ -179,18 +190,18 @@ int spfc_load(spfc_t h, const char* path) {
   if (!fp) return fail(h, SPFC_EINVAL, std::string("cannot open ") + path);
   char magic[8];
   int32_t hdr[4];
-  double sv[6];
+  double sv[7];
   bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
             std::fread(hdr, sizeof(hdr), 1, fp) == 1 && std::fread(sv, sizeof(sv), 1, fp) == 1;
   if (!ok || hdr[0] != P.d || hdr[1] != P.N || hdr[2] != h->s->precision || hdr[3] <= 0) {
     std::fclose(fp);
     return fail(h, SPFC_EINVAL, "checkpoint does not match this handle (grid or precision)");
   }
-  const double want[6] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta};
-  for (int i = 0; i < 6; ++i)
+  const double want[7] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab};
+  for (int i = 0; i < 7; ++i)
     if (std::fabs(sv[i] - want[i]) > 1e-12 * std::fabs(want[i])) {
       std::fclose(fp);
-      return fail(h, SPFC_EINVAL, "checkpoint parameters (L, dt, eps or beta) differ from this handle's");
+      return fail(h, SPFC_EINVAL, "checkpoint parameters (L, dt, eps, beta or stabiliser) differ from this handle's");
     }
   std::string blob((size_t)hdr[3], '\0');
   ok = std::fread(&blob[0], 1, blob.size(), fp) == blob.size();

@@ -28,6 +28,7 @@ class SolverBase {
   virtual int scalars(SavScal* out) = 0;
   virtual int get_field(double* out, bool on_device, int which) = 0;
   virtual int dt_change(double dt) = 0;
+  virtual int set_stab(double A) = 0;  // stabiliser of Sec. 5.2 for the following steps
   virtual int sync() = 0;
   virtual int set_timing(bool on) = 0;
   virtual int kernel_times(KernelTimes* kt) = 0;
@@ -51,6 +52,8 @@ inline void fill_float_params(Params* P) {
   P->a_f = (float)P->a;
   P->beta_f = (float)P->beta;
   P->invP_f = (float)P->invP;
+  P->sdt = P->stab * P->dt;
+  P->sdt_f = (float)P->sdt;
   auto split = [](double x, float* o) {
     o[0] = (float)x;
     o[1] = (float)(x - (double)o[0]);

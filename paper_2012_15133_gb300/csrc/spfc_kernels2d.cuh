@@ -38,14 +38,15 @@ template <typename R> __device__ __forceinline__ R kderiv(int i, int N, R kf) {
 // Per-run constants in the working precision (read, never converted, per thread).
 template <typename R> struct PC;
 template <> struct PC<double> {
-  double kfx, kfy, kfz, dt, a, beta, invP;
+  double kfx, kfy, kfz, dt, a, beta, invP, sdt;
   __device__ __forceinline__ explicit PC(const Params& P)
-      : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP) {}
+      : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP), sdt(P.sdt) {}
 };
 template <> struct PC<float> {
-  float kfx, kfy, kfz, dt, a, beta, invP;
+  float kfx, kfy, kfz, dt, a, beta, invP, sdt;
   __device__ __forceinline__ explicit PC(const Params& P)
-      : kfx(P.kf_f[0]), kfy(P.kf_f[1]), kfz(P.kf_f[2]), dt(P.dt_f), a(P.a_f), beta(P.beta_f), invP(P.invP_f) {}
+      : kfx(P.kf_f[0]), kfy(P.kf_f[1]), kfz(P.kf_f[2]), dt(P.dt_f), a(P.a_f), beta(P.beta_f), invP(P.invP_f),
+        sdt(P.sdt_f) {}
 };
 template <typename R> __device__ __forceinline__ R read_alpha(const SavScal* sc);
 template <> __device__ __forceinline__ double read_alpha<double>(const SavScal* sc) { return sc->alpha; }
@@ -78,11 +79,12 @@ __device__ __forceinline__ R sym_K2(int kx, int ky, int N, const PC<R>& c) {
   return rn_fma(kxx, kxx, rn_mul(kyy, kyy));
 }
 
-// 1 / (c0 + dt |k|^2 (a + |k|^4)): inverse symbol of A_N (c0 = 3/2, eq. solver-1)
-// or of the first-order operator (c0 = 1).
+// 1 / (c0 + dt |k|^2 (a + |k|^4) + A dt |k|^2): inverse symbol of A_N (c0 = 3/2,
+// eq. solver-1) or of the first-order operator (c0 = 1); the last term is the
+// stabiliser of Sec. 5.2 (exactly zero when A = 0).
 template <typename R>
 __device__ __forceinline__ R sym_invA(R K2, R c0, const PC<R>& c) {
-  const R A = rn_fma(c.dt, rn_mul(K2, rn_fma(K2, K2, c.a)), c0);
+  const R A = rn_fma(c.sdt, K2, rn_fma(c.dt, rn_mul(K2, rn_fma(K2, K2, c.a)), c0));
   return (R)1 / A;
 }
 
@@ -94,20 +96,22 @@ __device__ __forceinline__ double zero_mode_update(double a, double b) {
 }
 
 // BDF2 update of one spectral coefficient (eq. solver-6 in the form
-// phi^{n+1} = (dt r^{n+1}/sqrt(E1)) A^{-1} Delta N + A^{-1}(2 phi^n - phi^{n-1}/2)).
+// phi^{n+1} = (dt r^{n+1}/sqrt(E1)) A^{-1} Delta N + A^{-1}(2 phi^n - phi^{n-1}/2 + s phi^n)),
+// s = A dt |k|^2 the stabiliser's right-hand side (Sec. 5.2; zero when A = 0).
 template <typename C, typename R>
-__device__ __forceinline__ C bdf2_update(C cur, C old, C nh, R K2, R invA, R alpha) {
+__device__ __forceinline__ C bdf2_update(C cur, C old, C nh, R K2, R invA, R alpha, R s) {
   const R bfac = rn_mul(rn_mul(-alpha, K2), invA);
-  const R vx = rn_fma((R)2, cur.x, rn_mul((R)-0.5, old.x));
-  const R vy = rn_fma((R)2, cur.y, rn_mul((R)-0.5, old.y));
+  const R vx = rn_fma(s, cur.x, rn_fma((R)2, cur.x, rn_mul((R)-0.5, old.x)));
+  const R vy = rn_fma(s, cur.y, rn_fma((R)2, cur.y, rn_mul((R)-0.5, old.y)));
   return mk<C>(rn_fma(bfac, nh.x, rn_mul(vx, invA)), rn_fma(bfac, nh.y, rn_mul(vy, invA)));
 }
 
-// First-order (BDF1 start) update: phi^1 = alpha A1^{-1} Delta N + A1^{-1} phi^0.
+// First-order (BDF1 start) update: phi^1 = alpha A1^{-1} Delta N + A1^{-1} (1 + s) phi^0.
 template <typename C, typename R>
-__device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha) {
+__device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha, R s) {
   const R bfac = rn_mul(rn_mul(-alpha, K2), invA);
-  return mk<C>(rn_fma(bfac, nh.x, rn_mul(cur.x, invA)), rn_fma(bfac, nh.y, rn_mul(cur.y, invA)));
+  const R vx = rn_fma(s, cur.x, cur.x), vy = rn_fma(s, cur.y, cur.y);
+  return mk<C>(rn_fma(bfac, nh.x, rn_mul(vx, invA)), rn_fma(bfac, nh.y, rn_mul(vy, invA)));
 }
 
 // ---------------------------------------------------------------------------
@@ -194,7 +198,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
             nw = mk<C>((R)z, (R)0);
           } else {
             const R K2 = sym_K2<R>(kx, ky, N, pc);
-            nw = bdf2_update<C, R>(cur, old, vnh[i], K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
+            nw = bdf2_update<C, R>(cur, old, vnh[i], K2, sym_invA<R>(K2, (R)1.5, pc), alpha, rn_mul(pc.sdt, K2));
           }
           src_old[off] = nw;  // phi^{n+1} overwrites phi^{n-1}
           old = cur;
@@ -593,8 +597,11 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
       const R n2 = nh.x * nh.x + nh.y * nh.y;
       const R nv = nh.x * vv.x + nh.y * vv.y;
+      // eta takes the stabiliser's right-hand side s phi^n (Sec. 5.2), theta does not
+      const R sK = rn_mul(pc.sdt, K2);
+      const R nvs = nh.x * rn_fma(sK, vn[i].x, vv.x) + nh.y * rn_fma(sK, vn[i].y, vv.y);
       ag = RD::add(ag, w * (-K2 * invA) * n2);   // <N, A^{-1} Delta N>
-      ae = RD::add(ae, w * nv * invA);           // <N, A^{-1} v>
+      ae = RD::add(ae, w * nvs * invA);          // <N, A^{-1} v>
       at = RD::add(at, w * nv);                  // <N, v>
     }
     if constexpr (MODE != CF_NHAT) {
@@ -746,8 +753,10 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
     const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;  // half-spectrum Parseval weight
     const R n2 = nh[i].x * nh[i].x + nh[i].y * nh[i].y;
     const R nv = nh[i].x * v.x + nh[i].y * v.y;
+    const R sK = rn_mul(pc.sdt, K2);  // stabiliser (Sec. 5.2): in eta, not in theta
+    const R nvs = nh[i].x * rn_fma(sK, vn[i].x, v.x) + nh[i].y * rn_fma(sK, vn[i].y, v.y);
     ag = RD::add(ag, w * (-K2 * invA) * n2);
-    ae = RD::add(ae, w * nv * invA);
+    ae = RD::add(ae, w * nvs * invA);
     at = RD::add(at, w * nv);
   }
   typename RD::acc t3[3] = {ag, ae, at};
@@ -811,8 +820,8 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
         nw = mk<C>((R)z, (R)0);
       } else {
         const R K2 = sym_K2<R>(kx, ky, N, pc);
-        if (BDF1) nw = bdf1_update<C, R>(cur, nh[i], K2, sym_invA<R>(K2, (R)1, pc), al);
-        else nw = bdf2_update<C, R>(cur, vo[i], nh[i], K2, sym_invA<R>(K2, (R)1.5, pc), al);
+        if (BDF1) nw = bdf1_update<C, R>(cur, nh[i], K2, sym_invA<R>(K2, (R)1, pc), al, rn_mul(pc.sdt, K2));
+        else nw = bdf2_update<C, R>(cur, vo[i], nh[i], K2, sym_invA<R>(K2, (R)1.5, pc), al, rn_mul(pc.sdt, K2));
       }
       sold[off] = nw;  // phi^{n+1} over phi^{n-1}
       const C ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
@@ -864,9 +873,9 @@ __global__ void k2d_finalize(const Params P, Slots<R> S, const C_t<R>* __restric
     const C cu = cur[off], nh = Nhat[off];
     C nw;
     if (bdf1) {
-      nw = bdf1_update<C, R>(cu, nh, K2, sym_invA<R>(K2, (R)1, pc), alpha);
+      nw = bdf1_update<C, R>(cu, nh, K2, sym_invA<R>(K2, (R)1, pc), alpha, rn_mul(pc.sdt, K2));
     } else {
-      nw = bdf2_update<C, R>(cu, old[off], nh, K2, sym_invA<R>(K2, (R)1.5, pc), alpha);
+      nw = bdf2_update<C, R>(cu, old[off], nh, K2, sym_invA<R>(K2, (R)1.5, pc), alpha, rn_mul(pc.sdt, K2));
     }
     old[off] = nw;
   }

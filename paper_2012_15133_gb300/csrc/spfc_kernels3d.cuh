@@ -225,8 +225,10 @@ k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>
       const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;
       const R n2 = nh.x * nh.x + nh.y * nh.y;
       const R nv = nh.x * v.x + nh.y * v.y;
+      const R sK = rn_mul(pc.sdt, K2);  // stabiliser (Sec. 5.2): in eta, not in theta
+      const R nvs = nh.x * rn_fma(sK, vn[it].x, v.x) + nh.y * rn_fma(sK, vn[it].y, v.y);
       ag = RD::add(ag, w * (-K2 * invA) * n2);
-      ae = RD::add(ae, w * nv * invA);
+      ae = RD::add(ae, w * nvs * invA);
       at = RD::add(at, w * nv);
     }
     if constexpr (MODE != Z3F_NHAT) {
@@ -332,8 +334,8 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
           nw = mk<C>((R)z, (R)0);
         } else {
           const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
-          if (MODE == Z3I_STEP_BDF1) nw = bdf1_update<C, R>(cur, vn[it], K2, sym_invA<R>(K2, (R)1, pc), al);
-          else nw = bdf2_update<C, R>(cur, vb[it], vn[it], K2, sym_invA<R>(K2, (R)1.5, pc), al);
+          if (MODE == Z3I_STEP_BDF1) nw = bdf1_update<C, R>(cur, vn[it], K2, sym_invA<R>(K2, (R)1, pc), al, rn_mul(pc.sdt, K2));
+          else nw = bdf2_update<C, R>(cur, vb[it], vn[it], K2, sym_invA<R>(K2, (R)1.5, pc), al, rn_mul(pc.sdt, K2));
         }
         B[off] = nw;
         ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);

@@ -236,6 +236,15 @@ class Solver2D final : public SolverBase {
     return 0;
   }
 
+  int set_stab(double A) override {
+    int rc = finalize(); if (rc) return rc;
+    P.stab = A;
+    fill_float_params(&P);
+    drop_graphs();
+    w_ready_ = false;
+    return 0;
+  }
+
   int dt_change(double dt) override {
     int rc = finalize(); if (rc) return rc;
     P.dt = dt;

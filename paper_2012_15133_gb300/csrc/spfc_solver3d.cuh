@@ -137,6 +137,14 @@ class Solver3D final : public SolverBase {
     return 0;
   }
 
+  int set_stab(double A) override {
+    P.stab = A;
+    fill_float_params(&P);
+    drop_graphs();
+    w_ready_ = false;
+    return 0;
+  }
+
   int dt_change(double dt) override {
     P.dt = dt;
     fill_float_params(&P);

@@ -25,6 +25,10 @@ struct Params {
   float dt_f, a_f, beta_f, invP_f;
   // float-float (hi, lo) copies for the float32-bulk scalar algebra
   float hd_ff[2], vol_ff[2], Cvol_ff[2], qbeta_ff[2], dt_ff[2];
+  // stabiliser of Sec. 5.2 (- A dt Delta_N (phi^{n+1} - phi^n)); A = 0: the scheme of Sec. 2
+  double stab;    // A
+  double sdt;     // A dt
+  float sdt_f;
 };
 
 enum PendingKind : int { PEND_NONE = 0, PEND_BDF2 = 1, PEND_BDF1 = 2 };

@@ -41,6 +41,7 @@ _SIGS = {
     "spfc_sav_scalars": (_I, [_P, _DP, _I]),
     "spfc_get_field": (_I, [_P, _P, _I, _I]),
     "spfc_dt_change": (_I, [_P, _D]),
+    "spfc_set_stabilization": (_I, [_P, _D]),
     "spfc_save": (_I, [_P, ct.c_char_p]),
     "spfc_load": (_I, [_P, ct.c_char_p]),
     "spfc_sync": (_I, [_P]),
@@ -236,6 +237,12 @@ class Solver:
     def dt_change(self, dt):
         self._check(self._lib.spfc_dt_change(self._h, float(dt)))
         self.dt = float(dt)
+        return self
+
+    def set_stabilization(self, A):
+        """The stabilised scheme of Sec. 5.2 with constant A >= 0 (0: plain)."""
+        self._check(self._lib.spfc_set_stabilization(self._h, float(A)))
+        self.stab = float(A)
         return self
 
     def save(self, path):
