@@ -399,10 +399,9 @@ def run_ours(args):
     achieved = passes[dom] * SB / avg_s / 1e9
     peak, peak_kind = _peaks()
     # DRAM bytes (read + write) per launch of each kernel from the committed ncu
-    # capture (profiles/step2d_512_kernels_ncu_full.md); set to None whenever the
+    # capture of the 512^2 step kernels (ncu --set full, cold caches); set to None whenever the
     # kernel changes after the capture
-    traffic_ncu = {("fp32", "col_fused"): 3232000, ("fp32", "row"): 2136064,
-                   ("fp64", "col_fused"): 6408704, ("fp64", "row"): 4272640}
+    traffic_ncu = {("fp32", "col_fused"): 4294400, ("fp32", "row"): 2131968}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,
