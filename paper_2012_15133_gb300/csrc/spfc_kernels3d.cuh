@@ -38,98 +38,83 @@ template <int MODE> struct y3_nf { static constexpr int in = (MODE == Y3_FWD) ? 
                                    static constexpr int fft = (MODE == Y3_FWD || MODE == Y3_INV) ? 3 : 1; };
 
 // ---------------------------------------------------------------------------
-// y pass. Grid (ceil(NH/CT), N): tile of CT kx columns in plane z = blockIdx.y.
+// Column passes (y and z). Grid (ceil(NH/CT), N); CT * T threads, thread
+// (lane, c) = threadIdx.x = lane * CT + c owning the lines lane + i T (i < E)
+// of column kx0 + c for every field of the pass; the transforms keep their
+// first and last stages in registers (fft_regs_multi).
 // ---------------------------------------------------------------------------
+
+// y pass: tile of CT kx columns in plane z = blockIdx.y.
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__(y3_nf<MODE>::fft * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
           const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = y3_nf<MODE>::fft;
-  constexpr int NTH = NF * CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = (N * CT + NTH - 1) / NTH;  // three sequences per column: N*CT need not divide NTH
   constexpr int SEQ = sp_len(N);
-  static_assert(NTH % 32 == 0, "tile must fill whole warps");
+  constexpr bool INV = (MODE == Y3_INV || MODE == Y3_INV_FIELD);
+  static_assert((CT * T) % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
-  const int kx0 = blockIdx.x * CT;
-  const size_t base = (size_t)blockIdx.y * N * NH;
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c;
+  const bool col = kx < NH;
+  const size_t base = (size_t)blockIdx.y * N * NH + kx;
 
-  // load: FWD reads U_x, U_y, U_z; INV reads F, G_z and forms (i k~_y F, F, G_z);
-  // the field modes read one array
-  C va[IT], vb[IT], vc[IT];
+  // FWD reads U_x, U_y, U_z; INV reads F, G_z and forms (i k~_y F, F, G_z); the field modes one array
+  C v[NF][E];
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int i = idx / CT, kx = kx0 + idx % CT;
-    va[it] = vb[it] = vc[it] = mk<C>(0, 0);
-    if (idx < N * CT && kx < NH) {
-      const size_t off = base + (size_t)i * NH + kx;
-      va[it] = W0[off];
-      if (MODE == Y3_FWD || MODE == Y3_INV) vb[it] = W1[off];
-      if (MODE == Y3_FWD) vc[it] = W2[off];
-    }
-  }
+  for (int i = 0; i < E; ++i) {
+    const int y = lane + i * T;
+    const size_t off = base + (size_t)y * NH;
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int i = idx / CT, c = idx % CT;
-    if (idx >= N * CT) continue;
-    if (MODE == Y3_INV) {
-      const R kty = kderiv<R>(i, N, pc.kfy);
-      const C F = va[it];
-      sm[sp(i) * CTP + c] = mk<C>(-kty * F.y, kty * F.x);     // i k~_y F
-      sm[SEQ * CTP + sp(i) * CTP + c] = F;                     // F
-      sm[2 * SEQ * CTP + sp(i) * CTP + c] = vb[it];            // G_z
+    for (int f = 0; f < NF; ++f) v[f][i] = mk<C>(0, 0);
+    if (!col) continue;
+    if constexpr (MODE == Y3_FWD) {
+      v[0][i] = W0[off];
+      v[NF - 2][i] = W1[off];
+      v[NF - 1][i] = W2[off];
+    } else if constexpr (MODE == Y3_INV) {
+      const C F = W0[off];
+      const R kty = kderiv<R>(y, N, pc.kfy);
+      v[0][i] = mk<C>(-kty * F.y, kty * F.x);  // i k~_y F
+      v[NF - 2][i] = F;
+      v[NF - 1][i] = W1[off];                  // G_z
     } else {
-      sm[sp(i) * CTP + c] = va[it];
-      if (NF == 3) {
-        sm[SEQ * CTP + sp(i) * CTP + c] = vb[it];
-        sm[2 * SEQ * CTP + sp(i) * CTP + c] = vc[it];
-      }
+      v[0][i] = W0[off];
     }
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    constexpr bool INV = (MODE == Y3_INV || MODE == Y3_INV_FIELD);
-    fft_smem<C, N, E, INV>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
+  fft_regs_multi<C, N, E, INV, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
+  if (!col) return;
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int i = idx / CT, c = idx % CT, kx = kx0 + c;
-    if (idx >= N * CT || kx >= NH) continue;
-    const size_t off = base + (size_t)i * NH + kx;
-    if (MODE == Y3_FWD) {
-      const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(i, N, pc.kfy);
-      const C a = sm[sp(i) * CTP + c], b = sm[SEQ * CTP + sp(i) * CTP + c];
+  for (int i = 0; i < E; ++i) {
+    const int y = lane + i * T;
+    const size_t off = base + (size_t)y * NH;
+    if constexpr (MODE == Y3_FWD) {
+      const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(y, N, pc.kfy);
+      const C a = v[0][i], b = v[NF - 2][i];
       W0[off] = mk<C>(ktx * a.x + kty * b.x, ktx * a.y + kty * b.y);  // Q1
-      W1[off] = sm[2 * SEQ * CTP + sp(i) * CTP + c];                  // Q2
-    } else if (MODE == Y3_INV) {
+      W1[off] = v[NF - 1][i];                                         // Q2
+    } else if constexpr (MODE == Y3_INV) {
       const R ktx = kderiv<R>(kx, N, pc.kfx);
-      const C Fy = sm[SEQ * CTP + sp(i) * CTP + c];
-      W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);        // W_x = i k~_x Y^-1 F
-      W1[off] = sm[sp(i) * CTP + c];                    // W_y
-      W2[off] = sm[2 * SEQ * CTP + sp(i) * CTP + c];    // W_z
+      const C Fy = v[NF - 2][i];
+      W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);  // W_x = i k~_x Y^-1 F
+      W1[off] = v[0][i];                          // W_y
+      W2[off] = v[NF - 1][i];                     // W_z
     } else {
-      W0[off] = sm[sp(i) * CTP + c];
+      W0[off] = v[0][i];
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// z forward pass. Grid (ceil(NH/CT), N): tile of CT kx columns at ky = blockIdx.y.
-// ---------------------------------------------------------------------------
+// z forward pass: tile of CT kx columns at ky = blockIdx.y.
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == Z3F_TO_STATE ? 1 : 2) * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
          C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const SavScal* __restrict__ sc,
          const C_t<R>* __restrict__ tw, int target) {
@@ -137,81 +122,57 @@ k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == Z3F_TO_STATE) ? 1 : 2;
-  constexpr int NTH = NF * CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = N * CT / NTH;
   constexpr int SEQ = sp_len(N);
   constexpr size_t PS = (size_t)N * NH;
-  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  static_assert((CT * T) % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ typename RD::acc red[32];
+  __shared__ typename RD::acc red3[3][32];
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
-  const int kx0 = blockIdx.x * CT, ky = blockIdx.y;
-  const size_t base = (size_t)ky * NH;
-  {
-    C va[IT], vb[IT];
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c, ky = blockIdx.y;
+  const bool col = kx < NH;
+  const size_t base = (size_t)ky * NH + kx;
+  C v[NF][E];
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int i = idx / CT, kx = kx0 + idx % CT;
-      va[it] = vb[it] = mk<C>(0, 0);
-      if (kx < NH) {
-        va[it] = W0[base + i * PS + kx];
-        if (NF == 2) vb[it] = W1[base + i * PS + kx];
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int i = idx / CT, c = idx % CT;
-      sm[sp(i) * CTP + c] = va[it];
-      if (NF == 2) sm[SEQ * CTP + sp(i) * CTP + c] = vb[it];
-    }
+  for (int i = 0; i < E; ++i) {
+    const size_t off = base + (size_t)(lane + i * T) * PS;
+    v[0][i] = col ? W0[off] : mk<C>(0, 0);
+    if (NF == 2) v[NF - 1][i] = col ? W1[off] : mk<C>(0, 0);
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, false>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
   if constexpr (MODE == Z3F_TO_STATE) {
+    fft_regs_multi<C, N, E, false, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
     C* dst = S.at(target);
+    if (col) {
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int i = idx / CT, c = idx % CT, kx = kx0 + c;
-      if (kx < NH) dst[base + i * PS + kx] = sm[sp(i) * CTP + c];
+      for (int i = 0; i < E; ++i) dst[base + (size_t)(lane + i * T) * PS] = v[0][i];
     }
   } else {
     const int p = sc->p;
     const C* scur = S.at(p);
     const C* sold = S.at(1 - p);
     const R c0 = (MODE == Z3F_BDF1) ? (R)1 : (R)1.5;
-    C vn[IT], vo[IT];
-    if (MODE != Z3F_NHAT) {
+    C vn[E], vo[E];
 #pragma unroll
-      for (int it = 0; it < IT; ++it) {
-        const int idx = threadIdx.x + it * NTH;
-        const int i = idx / CT, kx = kx0 + idx % CT;
-        vn[it] = vo[it] = mk<C>(0, 0);
-        if (kx < NH) {
-          vn[it] = scur[base + i * PS + kx];
-          if (MODE == Z3F_BDF2) vo[it] = sold[base + i * PS + kx];
-        }
+    for (int i = 0; i < E; ++i) {   // issued before the FFT: their latency overlaps it
+      vn[i] = vo[i] = mk<C>(0, 0);
+      if (MODE != Z3F_NHAT && col) {
+        const size_t off = base + (size_t)(lane + i * T) * PS;
+        vn[i] = scur[off];
+        if (MODE == Z3F_BDF2) vo[i] = sold[off];
       }
     }
-    typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
+    fft_regs_multi<C, N, E, false, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
+    typename RD::acc acc[3] = {RD::zero(), RD::zero(), RD::zero()};
 #pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int idx = threadIdx.x + it * NTH;
-      const int kz = idx / CT, c = idx % CT, kx = kx0 + c;
-      if (kx >= NH) continue;
-      const size_t off = base + kz * PS + kx;
-      const C q1 = sm[sp(kz) * CTP + c], q2 = sm[SEQ * CTP + sp(kz) * CTP + c];
+    for (int i = 0; i < E; ++i) {
+      if (!col) continue;
+      const int kz = lane + i * T;
+      const size_t off = base + (size_t)kz * PS;
+      const C q1 = v[0][i], q2 = v[NF - 1][i];
       const R ktz = kderiv<R>(kz, N, pc.kfz);
       const R ux = q1.x + ktz * q2.x, uy = q1.y + ktz * q2.y;
       const C nh = mk<C>(uy, -ux);  // -i (k~_x W_x + k~_y W_y + k~_z W_z)
@@ -219,28 +180,26 @@ k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>
       if (MODE == Z3F_NHAT) continue;
       const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
       const R invA = sym_invA<R>(K2, c0, pc);
-      C v;
-      if (MODE == Z3F_BDF1) v = vn[it];
-      else v = mk<C>((R)2 * vn[it].x - (R)0.5 * vo[it].x, (R)2 * vn[it].y - (R)0.5 * vo[it].y);
+      C vv;
+      if (MODE == Z3F_BDF1) vv = vn[i];
+      else vv = mk<C>((R)2 * vn[i].x - (R)0.5 * vo[i].x, (R)2 * vn[i].y - (R)0.5 * vo[i].y);
       const R w = (kx == 0 || kx == N / 2) ? (R)1 : (R)2;
       const R n2 = nh.x * nh.x + nh.y * nh.y;
-      const R nv = nh.x * v.x + nh.y * v.y;
+      const R nv = nh.x * vv.x + nh.y * vv.y;
       const R sK = rn_mul(pc.sdt, K2);  // stabiliser (Sec. 5.2): in eta, not in theta
-      const R nvs = nh.x * rn_fma(sK, vn[it].x, v.x) + nh.y * rn_fma(sK, vn[it].y, v.y);
-      ag = RD::add(ag, w * (-K2 * invA) * n2);
-      ae = RD::add(ae, w * nvs * invA);
-      at = RD::add(at, w * nv);
+      const R nvs = nh.x * rn_fma(sK, vn[i].x, vv.x) + nh.y * rn_fma(sK, vn[i].y, vv.y);
+      acc[0] = RD::add(acc[0], w * (-K2 * invA) * n2);
+      acc[1] = RD::add(acc[1], w * nvs * invA);
+      acc[2] = RD::add(acc[2], w * nv);
     }
     if constexpr (MODE != Z3F_NHAT) {
-      const typename RD::acc tg = block_red<R>(ag, red);
-      const typename RD::acc te = block_red<R>(ae, red);
-      const typename RD::acc tt = block_red<R>(at, red);
+      block_red_multi<R, 3>(acc, red3);
       if (threadIdx.x == 0) {
         const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
         typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
-        ps[b] = tg;
-        ps[nb + b] = te;
-        ps[2 * nb + b] = tt;
+        ps[b] = acc[0];
+        ps[nb + b] = acc[1];
+        ps[2 * nb + b] = acc[2];
       }
     }
   }
@@ -270,33 +229,33 @@ k3d_scalar(const Params P, SavScal* __restrict__ sc, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// z inverse pass. Grid (ceil(NH/CT), N): tile of CT kx columns at ky = blockIdx.y.
+// z inverse pass: tile of CT kx columns at ky = blockIdx.y (thread layout as above).
 // STEP: after k3d_scalar (p already points at the slot being written):
 //   phi^{n+1} -> slot p, phi* = 2 phi^{n+1} - phi^n; PREP: phi* = 2 S[p] - S[1-p];
 //   GRAD: phi* = S[p] (which 0) or S[1-p]; FIELD: one output, the field itself.
 // Outputs: W0 = Z^-1 phi*, W1 = Z^-1 (i k~_z phi*).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__((MODE == Z3I_FIELD ? 1 : 2) * CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E))
 k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
          C_t<R>* __restrict__ W1, SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == Z3I_FIELD) ? 1 : 2;
-  constexpr int NTH = NF * CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;
   constexpr int NH = N / 2 + 1;
-  constexpr int IT = N * CT / NTH;
   constexpr int SEQ = sp_len(N);
   constexpr size_t PS = (size_t)N * NH;
   constexpr bool STEP = (MODE == Z3I_STEP || MODE == Z3I_STEP_BDF1);
-  static_assert(NTH % 32 == 0 && (N * CT) % NTH == 0, "tile must fill whole warps");
+  static_assert((CT * T) % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
-  const int kx0 = blockIdx.x * CT, ky = blockIdx.y;
-  const size_t base = (size_t)ky * NH;
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c, ky = blockIdx.y;
+  const bool col = kx < NH;
+  const size_t base = (size_t)ky * NH + kx;
   const int p = sc->p;
   C* A;  // STEP: phi^n; PREP: S[p]; GRAD/FIELD: the chosen slot
   C* B;  // STEP: the slot receiving phi^{n+1} (holds phi^{n-1}); PREP: S[1-p]
@@ -304,29 +263,27 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
   else if (MODE == Z3I_PREP) { A = S.at(p); B = S.at(1 - p); }
   else { A = S.at(which == 0 ? p : 1 - p); B = A; }
   const R al = read_alpha<R>(sc);
-  C va[IT], vb[IT], vn[IT];
+  C va[E], vb[E], vn[E];
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int i = idx / CT, kx = kx0 + idx % CT;
-    va[it] = vb[it] = vn[it] = mk<C>(0, 0);
-    if (kx < NH) {
-      const size_t off = base + i * PS + kx;
-      va[it] = A[off];
-      if (STEP || MODE == Z3I_PREP) vb[it] = B[off];
-      if (STEP) vn[it] = Nhat[off];
+  for (int i = 0; i < E; ++i) {
+    va[i] = vb[i] = vn[i] = mk<C>(0, 0);
+    if (col) {
+      const size_t off = base + (size_t)(lane + i * T) * PS;
+      va[i] = A[off];
+      if (STEP || MODE == Z3I_PREP) vb[i] = B[off];
+      if (STEP) vn[i] = Nhat[off];
     }
   }
+  C g[NF][E];
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int kz = idx / CT, c = idx % CT, kx = kx0 + c;
+  for (int i = 0; i < E; ++i) {
+    const int kz = lane + i * T;
     C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
-    if (kx < NH) {
-      const size_t off = base + kz * PS + kx;
+    if (col) {
+      const size_t off = base + (size_t)kz * PS;
       C ph;
       if (STEP) {
-        const C cur = va[it];
+        const C cur = va[i];
         C nw;
         if (off == 0) {
           const double z = (MODE == Z3I_STEP_BDF1) ? sc->zm[1 - p] : zero_mode_update(sc->zm[1 - p], sc->zm[p]);
@@ -334,37 +291,32 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
           nw = mk<C>((R)z, (R)0);
         } else {
           const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
-          if (MODE == Z3I_STEP_BDF1) nw = bdf1_update<C, R>(cur, vn[it], K2, sym_invA<R>(K2, (R)1, pc), al, rn_mul(pc.sdt, K2));
-          else nw = bdf2_update<C, R>(cur, vb[it], vn[it], K2, sym_invA<R>(K2, (R)1.5, pc), al, rn_mul(pc.sdt, K2));
+          if (MODE == Z3I_STEP_BDF1)
+            nw = bdf1_update<C, R>(cur, vn[i], K2, sym_invA<R>(K2, (R)1, pc), al, rn_mul(pc.sdt, K2));
+          else
+            nw = bdf2_update<C, R>(cur, vb[i], vn[i], K2, sym_invA<R>(K2, (R)1.5, pc), al, rn_mul(pc.sdt, K2));
         }
         B[off] = nw;
         ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
       } else if (MODE == Z3I_PREP) {
-        ph = mk<C>((R)2 * va[it].x - vb[it].x, (R)2 * va[it].y - vb[it].y);
+        ph = mk<C>((R)2 * va[i].x - vb[i].x, (R)2 * va[i].y - vb[i].y);
       } else {
-        ph = va[it];
+        ph = va[i];
       }
       g0 = ph;
       const R ktz = kderiv<R>(kz, N, pc.kfz);
       g1 = mk<C>(-ktz * ph.y, ktz * ph.x);
     }
-    sm[sp(kz) * CTP + c] = g0;
-    if (NF == 2) sm[SEQ * CTP + sp(kz) * CTP + c] = g1;
+    g[0][i] = g0;
+    if (NF == 2) g[NF - 1][i] = g1;
   }
-  __syncthreads();
-  {
-    const int q = threadIdx.x / T, lane = threadIdx.x % T;
-    const int f = q / CT, c = q % CT;
-    fft_smem<C, N, E, true>(sm + f * SEQ * CTP + c, CTP, lane, tw);
-  }
-  __syncthreads();
+  fft_regs_multi<C, N, E, true, NF, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
+  if (col) {
 #pragma unroll
-  for (int it = 0; it < IT; ++it) {
-    const int idx = threadIdx.x + it * NTH;
-    const int z = idx / CT, c = idx % CT, kx = kx0 + c;
-    if (kx < NH) {
-      W0[base + z * PS + kx] = sm[sp(z) * CTP + c];
-      if (NF == 2) W1[base + z * PS + kx] = sm[SEQ * CTP + sp(z) * CTP + c];
+    for (int i = 0; i < E; ++i) {
+      const size_t off = base + (size_t)(lane + i * T) * PS;
+      W0[off] = g[0][i];
+      if (NF == 2) W1[off] = g[NF - 1][i];
     }
   }
 }
@@ -372,13 +324,14 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
 // ---------------------------------------------------------------------------
 // x row pass over pairs of rows (flat row index z*N + y; N even, so a pair
 // shares z). Grid: N*N/(2*RP) blocks of RP row pairs.
-// NONLIN / ENERGY: three sequences per pair: G_x + i G_y of each row and
-// G_z(row 0) + i G_z(row 1). IN_REAL / OUT_REAL: one sequence per pair,
-// f(row 0) + i f(row 1).
+// NONLIN / ENERGY: three sequences per pair, all held by the pair's lanes:
+// G_x + i G_y of each row and G_z(row 0) + i G_z(row 1), with the first and
+// last FFT stages in registers. IN_REAL / OUT_REAL: one sequence per pair,
+// f(row 0) + i f(row 1). T lanes per pair.
 // part: 2 x gridDim.x accumulators (sum s^2, sum s).
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int RP, int MODE>
-__global__ void __launch_bounds__(((MODE == RW_NONLIN || MODE == RW_ENERGY) ? 3 : 1) * RP * (N / E))
+__global__ void __launch_bounds__(RP * (N / E))
 k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
         double* __restrict__ part, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw,
         double* __restrict__ real_io) {
@@ -386,19 +339,18 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NS = (MODE == RW_NONLIN || MODE == RW_ENERGY) ? 3 : 1;
-  constexpr int NTH = NS * RP * T;
+  constexpr int NTH = RP * T;
   constexpr int NH = N / 2 + 1;
   constexpr int KH = (N / 2) / T;
   constexpr int SEQ = sp_len(N);
   static_assert(NTH % 32 == 0 && KH * T == N / 2, "rows must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ typename RD::acc red[32];
+  __shared__ typename RD::acc red2[2][32];
   if (sc->status != DEV_OK) return;
-  const int q = threadIdx.x / T, lane = threadIdx.x % T;
-  const int pl = q / NS, kind = q % NS;            // local pair, sequence kind
+  const int pl = threadIdx.x / T, lane = threadIdx.x % T;   // local pair, lane
   const size_t row0 = 2 * ((size_t)blockIdx.x * RP + pl);
-  C* z = sm + q * (SEQ + 1);
+  C* z = sm + pl * NS * (SEQ + 1);                         // the pair's NS sequences
 
   if constexpr (MODE == RW_IN_REAL) {
 #pragma unroll
@@ -442,72 +394,77 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
       real_io[(row0 + 1) * N + x] = (double)z[sp(x)].y;
     }
   } else {
-    // pack: kind 0/1 = G_x + i G_y of row 0/1, kind 2 = G_z(row 0) + i G_z(row 1)
-    const C* Aa = (kind == 2) ? W2 : W0;
-    const C* Bb = (kind == 2) ? W2 : W1;
-    const size_t ra = row0 + (kind == 1 ? 1 : 0);
-    const size_t rb = (kind == 2) ? row0 + 1 : ra;
-    C a[KH], b[KH];
+    // Z_q = A_q + i B_q over the full x-spectrum, element k = lane + i T
+    // straight into registers (k > N/2 from the Hermitian mirror N - k):
+    // q = 0/1: G_x + i G_y of row 0/1, q = 2: G_z(row 0) + i G_z(row 1)
+    C v[NS][E];
 #pragma unroll
-    for (int i = 0; i < KH; ++i) {
-      a[i] = Aa[ra * NH + lane + i * T];
-      b[i] = Bb[rb * NH + lane + i * T];
-    }
-    const C an = Aa[ra * NH + N / 2], bn = Bb[rb * NH + N / 2];
-#pragma unroll
-    for (int i = 0; i < KH; ++i) {
-      const int k = lane + i * T;
-      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
-      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
-    }
-    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
-    __syncthreads();
-    fft_smem<C, N, E, true>(z, 1, lane, tw);
-    __syncthreads();
-    // pointwise (kinds 0 and 1 own row 0 and row 1; kind 2 lanes only wait)
-    typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
-    const PC<R> pc(P);
-    C* zxy = sm + (pl * NS + kind) * (SEQ + 1);
-    C* zz = sm + (pl * NS + 2) * (SEQ + 1);
-    if (kind < 2) {
+    for (int q = 0; q < NS; ++q) {
+      const C* Aa = (q == 2) ? W2 : W0;
+      const C* Bb = (q == 2) ? W2 : W1;
+      const size_t ra = row0 + (q == 1 ? 1 : 0);
+      const size_t rb = (q == 2) ? row0 + 1 : ra;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
-        const int x = sp(lane + i * T);
-        const C g = zxy[x];
-        const C gzc = zz[x];
-        const R gz = (kind == 0) ? gzc.x : gzc.y;
-        const R s = g.x * g.x + g.y * g.y + gz * gz;
-        acc2 = RD::add(acc2, s * s);
-        acc1 = RD::add(acc1, s);
-        if (MODE == RW_NONLIN) {
-          const R fac = pc.beta * s - (R)2;
-          zxy[x] = mk<C>(fac * g.x, fac * g.y);
-          if (kind == 0) zz[x].x = fac * gz; else zz[x].y = fac * gz;
-        }
+        const int k = lane + i * T;
+        const bool direct = k <= N / 2;
+        const int m = direct ? k : N - k;
+        const C a = Aa[ra * NH + m], b = Bb[rb * NH + m];
+        v[q][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
+      }
+    }
+    fft_regs_multi<C, N, E, true, NS, false>(v, z, SEQ + 1, 1, lane, tw);
+    // pointwise on x = lane + i T for both rows of the pair
+    typename RD::acc acc[2] = {RD::zero(), RD::zero()};
+    const PC<R> pc(P);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const C g0 = v[0][i], g1 = v[1][i], gz = v[2][i];
+      const R s0 = g0.x * g0.x + g0.y * g0.y + gz.x * gz.x;
+      const R s1 = g1.x * g1.x + g1.y * g1.y + gz.y * gz.y;
+      acc[0] = RD::add(acc[0], s0 * s0);
+      acc[1] = RD::add(acc[1], s0);
+      acc[0] = RD::add(acc[0], s1 * s1);
+      acc[1] = RD::add(acc[1], s1);
+      if (MODE == RW_NONLIN) {
+        const R f0 = pc.beta * s0 - (R)2, f1 = pc.beta * s1 - (R)2;
+        v[0][i] = mk<C>(f0 * g0.x, f0 * g0.y);
+        v[1][i] = mk<C>(f1 * g1.x, f1 * g1.y);
+        v[2][i] = mk<C>(f0 * gz.x, f1 * gz.y);
       }
     }
     if constexpr (MODE == RW_NONLIN) {
-      __syncthreads();
-      fft_smem<C, N, E, false>(z, 1, lane, tw);
-      const R h = (R)0.5 * pc.invP;
-      C* Oa = (kind == 2) ? W2 : W0;
-      C* Ob = (kind == 2) ? W2 : W1;
+      fft_regs_multi<C, N, E, false, NS, false>(v, z, SEQ + 1, 1, lane, tw);
+      // the split into the two signals of each sequence pairs k with N - k: one exchange
+      fft_sync<N, E>();
 #pragma unroll
-      for (int i = 0; i < KH + 1; ++i) {
-        if (i == KH && lane != 0) break;
-        const int k = (i == KH) ? N / 2 : lane + i * T;
-        const C zk = z[sp(k)], zm = cconj(z[sp((N - k) & (N - 1))]);
-        const C sx = cadd(zk, zm), dy = csub(zk, zm);
-        Oa[ra * NH + k] = cscale(sx, h);
-        Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);
+      for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int i = 0; i < E; ++i) z[q * (SEQ + 1) + sp(lane + i * T)] = v[q][i];
+      fft_sync<N, E>();
+      const R h = (R)0.5 * pc.invP;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        C* Oa = (q == 2) ? W2 : W0;
+        C* Ob = (q == 2) ? W2 : W1;
+        const size_t ra = row0 + (q == 1 ? 1 : 0);
+        const size_t rb = (q == 2) ? row0 + 1 : ra;
+#pragma unroll
+        for (int i = 0; i < KH + 1; ++i) {
+          if (i == KH && lane != 0) break;
+          const int k = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
+          const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + sp((N - k) & (N - 1))]);
+          const C sx = cadd(zk, zm), dy = csub(zk, zm);
+          Oa[ra * NH + k] = cscale(sx, h);
+          Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);
+        }
       }
     }
-    const typename RD::acc t2 = block_red<R>(acc2, red);
-    const typename RD::acc t1 = block_red<R>(acc1, red);
+    block_red_multi<R, 2>(acc, red2);
     if (threadIdx.x == 0) {
       typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
-      ps[blockIdx.x] = t2;
-      ps[gridDim.x + blockIdx.x] = t1;
+      ps[blockIdx.x] = acc[0];
+      ps[gridDim.x + blockIdx.x] = acc[1];
     }
   }
 }

@@ -7,8 +7,11 @@
 
 namespace spfc {
 
-template <int N> struct Shape3D {
-  static constexpr int E = 8;
+// Launch shape per grid size: E values per FFT lane (8 on the float32-bulk
+// path; 4 on the float64 path, whose arithmetic needs the extra threads once
+// one thread carries every field of its column or row pair).
+template <int N, int E_ = 8> struct Shape3D {
+  static constexpr int E = E_;
   static constexpr int T = N / E;
   static constexpr int CT = (32 / T > 4) ? 32 / T : 4;  // kx columns per column-pass block (>= 32 B per row)
   static constexpr int RP = 32 / T > 1 ? 32 / T : 1;    // row pairs per row-pass block
@@ -18,7 +21,7 @@ template <int N> struct Shape3D {
 template <typename R, int N>
 class Solver3D final : public SolverBase {
   using C = C_t<R>;
-  using SH = Shape3D<N>;
+  using SH = Shape3D<N, sizeof(R) == 8 ? 4 : 8>;
   static constexpr int NH = N / 2 + 1;
   static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RP = SH::RP;
   static constexpr int CTP = (CT == 1) ? 1 : CT + 1;
@@ -290,8 +293,8 @@ class Solver3D final : public SolverBase {
   int ypass(int mode) {
     const dim3 g(GX, N);
     switch (mode) {
-      case Y3_FWD: k3d_ypass<R, N, E, CT, Y3_FWD><<<g, 3 * CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
-      case Y3_INV: k3d_ypass<R, N, E, CT, Y3_INV><<<g, 3 * CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
+      case Y3_FWD: k3d_ypass<R, N, E, CT, Y3_FWD><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
+      case Y3_INV: k3d_ypass<R, N, E, CT, Y3_INV><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
       case Y3_INV_FIELD:
         k3d_ypass<R, N, E, CT, Y3_INV_FIELD><<<g, CT * T, smem_col(1), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
       default:
@@ -304,11 +307,11 @@ class Solver3D final : public SolverBase {
     const dim3 g(GX, N);
     switch (mode) {
       case Z3F_BDF2:
-        k3d_zfwd<R, N, E, CT, Z3F_BDF2><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
+        k3d_zfwd<R, N, E, CT, Z3F_BDF2><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
       case Z3F_BDF1:
-        k3d_zfwd<R, N, E, CT, Z3F_BDF1><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
+        k3d_zfwd<R, N, E, CT, Z3F_BDF1><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
       case Z3F_NHAT:
-        k3d_zfwd<R, N, E, CT, Z3F_NHAT><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
+        k3d_zfwd<R, N, E, CT, Z3F_NHAT><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
       default:
         k3d_zfwd<R, N, E, CT, Z3F_TO_STATE><<<g, CT * T, smem_col(1), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target);
     }
@@ -319,13 +322,13 @@ class Solver3D final : public SolverBase {
     const dim3 g(GX, N);
     switch (mode) {
       case Z3I_STEP:
-        k3d_zinv<R, N, E, CT, Z3I_STEP><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
+        k3d_zinv<R, N, E, CT, Z3I_STEP><<<g, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
       case Z3I_STEP_BDF1:
-        k3d_zinv<R, N, E, CT, Z3I_STEP_BDF1><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
+        k3d_zinv<R, N, E, CT, Z3I_STEP_BDF1><<<g, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
       case Z3I_PREP:
-        k3d_zinv<R, N, E, CT, Z3I_PREP><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
+        k3d_zinv<R, N, E, CT, Z3I_PREP><<<g, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
       case Z3I_GRAD:
-        k3d_zinv<R, N, E, CT, Z3I_GRAD><<<g, 2 * CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
+        k3d_zinv<R, N, E, CT, Z3I_GRAD><<<g, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which); break;
       default:
         k3d_zinv<R, N, E, CT, Z3I_FIELD><<<g, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], W_[1], sc_, tw_, which);
     }
@@ -335,9 +338,9 @@ class Solver3D final : public SolverBase {
   int row(int mode) {
     switch (mode) {
       case RW_NONLIN:
-        k3d_row<R, N, E, RP, RW_NONLIN><<<GROW, 3 * RP * T, smem_row(3), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
+        k3d_row<R, N, E, RP, RW_NONLIN><<<GROW, RP * T, smem_row(3), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
       case RW_ENERGY:
-        k3d_row<R, N, E, RP, RW_ENERGY><<<GROW, 3 * RP * T, smem_row(3), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
+        k3d_row<R, N, E, RP, RW_ENERGY><<<GROW, RP * T, smem_row(3), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
       case RW_IN_REAL:
         k3d_row<R, N, E, RP, RW_IN_REAL><<<GROW, RP * T, smem_row(1), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
       default:
