@@ -278,21 +278,23 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
     held-out seeds with the plain-step fallback. Reports point-steps/s of
     surrogate + fallback against plain FP32 SAV steps of the same runs (one
     solver per run, and the batched solver), and the rel-L2 of the final
-    fields against the plain trajectories."""
+    fields against the plain trajectories. Set-up (the twin solvers of the
+    periodic check, first calls) stays outside the timed regions."""
     import numpy as np
     import torch
-    from paper_2012_15133_gb300 import Solver, Batch
+    from paper_2012_15133_gb300 import Solver, Batch, field_energy_noalloc
     from paper_2012_15133_gb300 import surrogate as S
     from seeded_inputs import surrogate_run
     n = 256
     t0 = time.perf_counter()
     data = S.trajectory_pairs([surrogate_run(i, n) for i in range(train_runs)], 0.02, K, snapshots, 250, 100)
     t_data = time.perf_counter() - t0
-    net = S.FNO(n=n, width=32, modes1=modes, modes2=modes, layers=4, proj=64, max_batch=eval_runs)
+    net = S.FNO(n=n, width=32, modes1=modes, modes2=modes, layers=4, proj=64, max_batch=max(16, eval_runs))
     net.set_params(S.init_params(net, 0))
     losses, t_train = S.timed(S.train, net, data, iters, 16, 2e-3)
     idl = S.identity_loss(data)
     del data
+    torch.cuda.empty_cache()
     held = [surrogate_run(i, n, held_out=True) for i in range(eval_runs)]
 
     def fresh():
@@ -304,7 +306,12 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
             out.append(s)
         return out
     sur, pl = fresh(), fresh()
-    log, t_sur = S.timed(S.advance, sur, net, K, jumps, check_every=check_every, tol=tol)
+    judges = S.judges_for(sur)
+    # first calls outside the timing: the network, the allocation-free energy
+    x = sur[0].get_field(0, out=torch.empty((n, n), dtype=torch.float64, device="cuda"))
+    field_energy_noalloc(x, held[0]["L"], held[0]["eps"], held[0]["beta"])
+    net.predict(x.float()[None].contiguous(), x.float()[None].contiguous(), [0.2], [1.0])
+    log, t_sur = S.timed(S.advance, sur, net, K, jumps, check_every=check_every, tol=tol, judges=judges)
     _, t_plain = S.timed(lambda: [s.step(K * jumps) for s in pl])
     b = Batch(held, 0.02, "fp32")
     for i, r in enumerate(held):
@@ -315,6 +322,8 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
             for x, y in zip(sur, pl)]
     pts = eval_runs * n * n * K * jumps
     net.close()
+    for j in judges.values():
+        j.close()
     return {"workload": f"surrogate jumps of K={K} steps, 256^2 (L=128), {eval_runs} held-out seeds x "
                         f"{K * jumps} steps after 100 plain steps; network width 32, {modes} x {2 * modes} "
                         f"retained modes, 4 layers",
@@ -326,8 +335,8 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
             "training": {"pairs": train_runs * snapshots, "trajectories": train_runs, "iters": iters, "batch": 16,
                          "loss_last": float(np.mean(losses[-20:])), "identity_loss": idl,
                          "data_s": t_data, "train_s": t_train},
-            "note": "bounded sample of the surrogate workload (the full one trains on 2000 trajectories and "
-                    "evaluates 64 seeds x 10000 steps)"}
+            "note": "bounded sample of the surrogate workload" if train_runs < 2000 else
+                    "the surrogate workload at full scale"}
 
 
 def run_ours(args):
@@ -551,6 +560,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the ensemble, 3D and surrogate measurements")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--surrogate-full", action="store_true",
+                    help="only the surrogate workload at full scale (2000 training trajectories, 64 held-out "
+                         "seeds x 10000 steps), one JSON line")
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
@@ -559,6 +571,13 @@ def main():
     args = ap.parse_args()
     if args.ncu_driver:
         return run_driver(args)
+    if args.surrogate_full:
+        from paper_2012_15133_gb300 import build
+        build.build()
+        out = {m: measure_surrogate(modes=m, train_runs=2000, snapshots=8, iters=2000, eval_runs=64, jumps=500)
+               for m in (16, 32)}
+        print(json.dumps({"surrogate_full": out}))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -146,23 +146,25 @@ def trajectory_pairs(runs, dt, K, snapshots, spacing, warm, precision="fp32"):
         b.init(i, r["phi0"], "bdf1")
     if warm:
         b.step(warm)
-    X1, X0, Y = [], [], []
+    n = int(runs[0]["n"])
+    total = len(runs) * snapshots
+    X1, X0, Y = (torch.empty((total, n, n), dtype=torch.float32, device="cuda") for _ in range(3))
+    dev = lambda a: torch.from_numpy(a.astype(np.float32))
     for s in range(snapshots):
-        cur = [b.get_field(i, 0) for i in range(len(runs))]
-        prev = [b.get_field(i, 1) for i in range(len(runs))]
+        o = s * len(runs)
+        for i in range(len(runs)):
+            X1[o + i].copy_(dev(b.get_field(i, 0)))
+            X0[o + i].copy_(dev(b.get_field(i, 1)))
         b.step(K)
-        fut = [b.get_field(i, 0) for i in range(len(runs))]
-        X1 += cur
-        X0 += prev
-        Y += fut
+        for i in range(len(runs)):
+            Y[o + i].copy_(dev(b.get_field(i, 0)))
         if spacing > K and s + 1 < snapshots:
             b.step(spacing - K)
     b.close()
-    t = lambda xs: torch.tensor(np.stack(xs).astype(np.float32), device="cuda")
     eps = np.array([r["eps"] for r in runs] * snapshots)
     beta = np.array([r["beta"] for r in runs] * snapshots)
     # sample i * len(runs) + j is run j at snapshot i
-    return {"phi_n": t(X1), "phi_nm1": t(X0), "target": t(Y), "eps": eps, "beta": beta}
+    return {"phi_n": X1, "phi_nm1": X0, "target": Y, "eps": eps, "beta": beta}
 
 
 def train(fno: FNO, data, iters, batch, lr=1e-3, seed=0, weight_decay=0.0):
@@ -212,10 +214,18 @@ def _twin(s):
     return Solver(2, s.n[0], s.L[0], s.eps, s.beta, s.dt, "fp64" if s.precision == 0 else "fp32")
 
 
-def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
+def judges_for(solvers):
+    """One twin solver per run, for the periodic plain-step check of advance();
+    creating them up front keeps their set-up out of a timed advance."""
+    return {i: _twin(s) for i, s in enumerate(solvers)}
+
+
+def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None, judges=None):
     """Advance 2D square runs (Solver objects of one grid size n <= 256) by
     jumps x K steps with the surrogate, falling back to K plain SAV steps per
-    rejected jump. One network call predicts all runs of a jump round."""
+    rejected jump. One network call predicts all runs of a jump round.
+    judges: twins from judges_for(solvers), kept by the caller (else made on
+    first use and closed on return)."""
     import torch
     if log is None:
         log = JumpLog()
@@ -229,7 +239,8 @@ def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
     beta = [s.beta for s in solvers]
     cur = torch.empty((R, n, n), dtype=torch.float64, device="cuda")
     prev = torch.empty_like(cur)
-    judge = {}
+    own = judges is None
+    judge = {} if own else judges
     for j in range(jumps):
         for i, s in enumerate(solvers):
             s.get_field(0, out=cur[i])
@@ -265,8 +276,9 @@ def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None):
             log.accepted += 1
             log.decisions.append((j, i, "accept"))
             s.init(pred[i].contiguous(), "copy")
-    for ref in judge.values():
-        ref.close()
+    if own:
+        for ref in judge.values():
+            ref.close()
     return log
 
 
