@@ -93,6 +93,15 @@ int spfc_schedule(spfc_t h);
  * after eq. scheme-SAV-initial-2. */
 int spfc_init(spfc_t h, const double* phi0, int phi0_on_device, int mode);
 
+/* Start from a seeded noise field, generated on the device: phi0[j] = mean +
+ * amp (2 u_j - 1) at flat grid index j (x fastest), u_j = (x_j >> 11) 2^-53
+ * with x_j output j of SplitMix64 (Steele, Lea & Flood 2014) seeded with
+ * `seed`, i.e. the finaliser applied to seed + (j + 1) 0x9E3779B97F4A7C15.
+ * The paper's initial data (Sec. 5.2) is mean = 0, amp = 0.05. Then as
+ * spfc_init with `mode`. Allocates and frees one temporary device field;
+ * synchronises. SPFC_EINVAL for a non-finite mean or amp or a bad mode. */
+int spfc_init_random(spfc_t h, double mean, double amp, uint64_t seed, int mode);
+
 /* Set the two time levels and auxiliary scalars directly: phi = phi^n,
  * phi_prev = phi^{n-1}, r = r^n, r_prev = r^{n-1} (used for restarts and
  * for per-step comparisons from a given state). */

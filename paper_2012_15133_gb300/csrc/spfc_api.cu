@@ -1,4 +1,5 @@
 // C ABI of the SPFC solver (declared in include/spfc.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,24 @@ struct spfc_s {
 };
 
 static thread_local std::string g_create_err;
+
+// phi[j] = mean + amp (2 u_j - 1), u_j = (x_j >> 11) 2^-53 with x_j output j of
+// SplitMix64 (Steele, Lea & Flood 2014) seeded with `seed`, used as a
+// counter-based generator: x_j is the finaliser applied to
+// seed + (j + 1) * 0x9E3779B97F4A7C15 (mod 2^64). The arithmetic is rounded
+// explicitly (no contraction), so the field is the same on every platform.
+__global__ void k_noise_field(double* __restrict__ phi, size_t count, unsigned long long seed, double mean,
+                              double amp) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < count; j += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = __dmul_rn((double)(z >> 11), 0x1.0p-53);
+    const double c = __dadd_rn(__dmul_rn(2.0, u), -1.0);
+    phi[j] = __dadd_rn(mean, __dmul_rn(amp, c));
+  }
+}
 
 static int fail(spfc_t h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_create_err = msg;
@@ -97,6 +116,25 @@ int spfc_init(spfc_t h, const double* phi0, int on_device, int mode) {
   if (!h || !phi0) return fail(h, SPFC_EINVAL, "NULL argument");
   if (mode < 0 || mode > 2) return fail(h, SPFC_EINVAL, "unknown start mode");
   return wrap(h, h->s->init(phi0, on_device != 0, mode));
+}
+
+int spfc_init_random(spfc_t h, double mean, double amp, uint64_t seed, int mode) {
+  if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
+  if (mode < 0 || mode > 2) return fail(h, SPFC_EINVAL, "unknown start mode");
+  if (!std::isfinite(mean) || !std::isfinite(amp)) return fail(h, SPFC_EINVAL, "mean and amp must be finite");
+  const spfc::Params& P = h->s->P;
+  const size_t count = (size_t)std::llround(P.P);
+  double* phi = nullptr;
+  cudaError_t e = cudaMalloc(&phi, count * sizeof(double));
+  if (e != cudaSuccess) return fail(h, SPFC_ENOMEM, std::string("allocation: ") + cudaGetErrorString(e));
+  const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+  k_noise_field<<<blocks, 256>>>(phi, count, (unsigned long long)seed, mean, amp);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  int rc = (e == cudaSuccess) ? wrap(h, h->s->init(phi, true, mode))
+                              : fail(h, SPFC_ECUDA, std::string("noise field: ") + cudaGetErrorString(e));
+  cudaFree(phi);  // synchronises with the device: the start-up has consumed the field
+  return rc;
 }
 
 int spfc_set_state(spfc_t h, const double* phi, const double* phi_prev, double r, double r_prev, int on_device) {

@@ -34,6 +34,7 @@ _SIGS = {
     "spfc_create_scheduled": (_I, [_I, ct.POINTER(_I), _DP, _D, _D, _D, _I, _P, _I, ct.POINTER(_P)]),
     "spfc_schedule": (_I, [_P]),
     "spfc_init": (_I, [_P, _P, _I, _I]),
+    "spfc_init_random": (_I, [_P, _D, _D, ct.c_uint64, _I]),
     "spfc_set_state": (_I, [_P, _P, _P, _D, _D, _I]),
     "spfc_step": (_I, [_P, ct.c_int64]),
     "spfc_energy": (_I, [_P, _DP, _DP, _DP]),
@@ -195,6 +196,12 @@ class Solver:
     def init(self, phi0, mode="bdf1"):
         ptr, dev, keep = self._field_arg(phi0)
         self._check(self._lib.spfc_init(self._h, ptr, dev, _START[mode]))
+        return self
+
+    def init_random(self, mean, amp, seed, mode="bdf1"):
+        """Start from mean + amp U(-1, 1), the noise drawn on the device from
+        SplitMix64 (the same stream as seeded_inputs.noisy_field)."""
+        self._check(self._lib.spfc_init_random(self._h, float(mean), float(amp), int(seed), _START[mode]))
         return self
 
     def set_state(self, phi, phi_prev, r, r_prev):

@@ -256,3 +256,19 @@ def test_every_launch_schedule_matches_the_oracle(precision, n):
         s.step(2)
         assert rel_l2(s.get_field(0), o.phi) < TOL[precision], sch
         assert abs(s.sav_scalars()["r"] - o.r) / o.r < TOL[precision], sch
+
+
+def test_device_noise_start_equals_the_host_noise_field():
+    """spfc_init_random draws the same SplitMix64 stream as the host inputs:
+    starting from it or from the host field gives bit-identical runs."""
+    from paper_2012_15133_gb300 import Solver
+    from seeded_inputs import cube_3d_case
+    for c, mean, amp, seed in ((crystal_2d_case(64), 0.2, 0.02, 1), (cube_3d_case(16), 0.15, 0.05, 2)):
+        args = (c["d"], c["n"], c["L"], c["eps"], c["beta"], c["dt"], "fp64")
+        a, b = Solver(*args), Solver(*args)
+        a.init(c["phi0"], "bdf1")
+        b.init_random(mean, amp, seed, "bdf1")
+        assert np.array_equal(a.get_field(1), b.get_field(1))
+        a.step(5)
+        b.step(5)
+        assert np.array_equal(a.get_field(0), b.get_field(0))
