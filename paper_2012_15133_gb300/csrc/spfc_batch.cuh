@@ -30,8 +30,16 @@ template <typename R> struct BatchView {
   int nE, nG;   // partial-sum blocks per run (row pass, column pass)
 };
 
+// Resident blocks per SM asked of the compiler for the batched passes (their
+// many blocks hide load and shared-memory latency): 24 warps per SM on the
+// float32 path (at most 85 registers per thread; 32 warps spill the row pass
+// and measured slower), none on the float64 path.
+template <typename R> constexpr int batch_min_blocks(int threads) {
+  return sizeof(R) == 8 ? 1 : (24 * 32 + threads - 1) / threads;
+}
+
 template <typename R, int N, int E, int RPC>
-__global__ void __launch_bounds__(RPC * (N / E))
+__global__ void __launch_bounds__(RPC * (N / E), batch_min_blocks<R>(RPC * (N / E)))
 k2b_row(BatchView<R> B, const C_t<R>* __restrict__ tw) {
   const int r = blockIdx.y;
   k2d_row_body<R, N, E, RPC, RW_NONLIN>(B.P[r], B.W0 + r * B.spec, B.W1 + r * B.spec, B.partE + (size_t)r * 2 * B.nE,
@@ -39,7 +47,7 @@ k2b_row(BatchView<R> B, const C_t<R>* __restrict__ tw) {
 }
 
 template <typename R, int N, int E, int CT>
-__global__ void __launch_bounds__(CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E), batch_min_blocks<R>(CT * (N / E)))
 k2b_col_fwd(BatchView<R> B, const C_t<R>* __restrict__ tw) {
   const int r = blockIdx.y;
   Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};
@@ -48,7 +56,7 @@ k2b_col_fwd(BatchView<R> B, const C_t<R>* __restrict__ tw) {
 }
 
 template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__(CT * (N / E))
+__global__ void __launch_bounds__(CT * (N / E), batch_min_blocks<R>(CT * (N / E)))
 k2b_col_inv(BatchView<R> B, const C_t<R>* __restrict__ tw) {
   const int r = blockIdx.y;
   Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};

@@ -562,17 +562,25 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
     const C* snew = S.at(newest);
     const C* sold = S.at(1 - newest);
     const R c0 = (MODE == CF_BDF1) ? (R)1 : (R)1.5;
+    // the state is loaded before the FFT where registers allow (its latency
+    // overlaps the transform), after it in the batched pass, which keeps
+    // its registers low for three resident blocks per SM
+    constexpr bool EARLY = (MODE != CF_PART);
     C vn[E], vo[E];
+    auto load_state = [&]() {
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      vn[i] = vo[i] = mk<C>(0, 0);
-      if (MODE != CF_NHAT && col) {   // issued before the FFT: their latency overlaps it
-        const size_t off = (size_t)(lane + i * T) * NH + kx;
-        vn[i] = snew[off];
-        if (MODE == CF_BDF2 || MODE == CF_PART) vo[i] = sold[off];
+      for (int i = 0; i < E; ++i) {
+        vn[i] = vo[i] = mk<C>(0, 0);
+        if (MODE != CF_NHAT && col) {
+          const size_t off = (size_t)(lane + i * T) * NH + kx;
+          vn[i] = snew[off];
+          if (MODE == CF_BDF2 || MODE == CF_PART) vo[i] = sold[off];
+        }
       }
-    }
+    };
+    if (EARLY) load_state();
     fft_regs_multi<C, N, E, false, NF, true>(v, sm + c, SEQ * CTP, CTP, lane, tw);
+    if (!EARLY) load_state();
     typename RD::acc ag = RD::zero(), ae = RD::zero(), at = RD::zero();
 #pragma unroll
     for (int i = 0; i < E; ++i) {
