@@ -165,6 +165,7 @@ class Model:
         self.C = 1.0 + 1.0 / self.beta       # C_beta; 2 at beta = 1
         self.nonlinear = nonlinear            # test switch: False sets N_N := 0
         self.stab = 0.0                       # A of the stabilised scheme (Sec. 5.2); 0: Sec. 2
+        self.gamma3 = 0.0                     # optional gamma3/4 phi^4 in E_1 (the PFC term); 0: SPFC
 
     def L_op(self, f):
         """L_N f = a f + Delta_N^2 f (Sec. 2.1, before eq. spectral-coll-6)."""
@@ -176,11 +177,14 @@ class Model:
         return sum(gc * gc for gc in self.g.grad(phi))
 
     def E1(self, phi) -> float:
-        """E_{1,N}(phi) = beta/4 ||grad_N phi||_4^4 - ||grad_N phi||_2^2 + C |Omega| (Sec. 2.2)."""
+        """E_{1,N}(phi) = beta/4 ||grad_N phi||_4^4 - ||grad_N phi||_2^2 + C |Omega| (Sec. 2.2),
+        plus gamma3/4 ||phi||_4^4 when the optional phi^4 term is on (E_1 >= |Omega| still)."""
         g = self.g
         s = self.grad_sq(phi)
-        return (self.beta / 4.0) * g.hd * float(np.sum(s * s)) - g.hd * float(np.sum(s)) \
-            + self.C * g.volume
+        e = (self.beta / 4.0) * g.hd * float(np.sum(s * s)) - g.hd * float(np.sum(s)) + self.C * g.volume
+        if self.gamma3:
+            e += (self.gamma3 / 4.0) * g.hd * float(np.sum(phi ** 4))
+        return e
 
     def N_op(self, phi):
         """N_N(phi) = -grad_N . (beta |grad_N phi|^2 grad_N phi) + 2 grad_N . grad_N phi
@@ -190,7 +194,14 @@ class Model:
             return np.zeros(g.shape)
         gr = g.grad(phi)
         s = sum(gc * gc for gc in gr)
-        return -g.div([self.beta * s * gc for gc in gr]) + 2.0 * g.div(gr)
+        n = -g.div([self.beta * s * gc for gc in gr]) + 2.0 * g.div(gr)
+        if self.gamma3:
+            # + gamma3 phi^3, the variational derivative of gamma3/4 ||phi||_4^4, with its
+            # mean removed (N_hat_0 := 0: the divergence terms have none, and the zero mode
+            # of N never enters the scheme, whose solution keeps the mass)
+            c = self.gamma3 * phi ** 3
+            n = n + c - float(np.mean(c))
+        return n
 
     def mu(self, phi):
         """mu_N = N_N(phi) + L_N phi (eq. equation-SPFC at the grid level)."""
@@ -202,8 +213,11 @@ class Model:
         g = self.g
         s = self.grad_sq(phi)
         lp = g.lap(phi)
-        return (self.beta / 4.0) * g.hd * float(np.sum(s * s)) + 0.5 * self.a * g.inner(phi, phi) \
+        e = (self.beta / 4.0) * g.hd * float(np.sum(s * s)) + 0.5 * self.a * g.inner(phi, phi) \
             - g.hd * float(np.sum(s)) + 0.5 * g.inner(lp, lp)
+        if self.gamma3:
+            e += (self.gamma3 / 4.0) * g.hd * float(np.sum(phi ** 4))
+        return e
 
     def L_norm_sq(self, f) -> float:
         """||L_N^{1/2} f||^2 = <f, L_N f> (eq. spectral-coll-inner product-4)."""
@@ -327,10 +341,11 @@ def copy_start(model: Model, phi0):
 class Oracle:
     """State (phi^n, phi^{n-1}, r^n, r^{n-1}) advanced by bdf2_sav_step."""
 
-    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive", stab=0.0):
+    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive", stab=0.0, gamma3=0.0):
         self.grid = Grid(d, n, L, dft=dft)
         self.model = Model(self.grid, eps, beta, nonlinear=nonlinear)
         self.model.stab = float(stab)
+        self.model.gamma3 = float(gamma3)
         self.dt = float(dt)
         self.phi = self.phi_prev = None
         self.r = self.r_prev = None

@@ -213,9 +213,10 @@ def _case(n=16, L=8.0, dt=0.05, eps=0.25, beta=1.0, amp=0.4, d=2, smooth=0.2):
     return o, phi0
 
 
-def pin_residual(d=2) -> float:
+def pin_residual(d=2, gamma3=0.0) -> float:
     """Plug (phi^{n+1}, r^{n+1}) into eq. scheme-SAV-1 (a) and (b) directly."""
     o, phi0 = _case(d=d, n=16 if d == 2 else 8, L=8.0 if d == 2 else 5.0)
+    o.model.gamma3 = gamma3
     o.start(phi0, "ghost")
     worst = 0.0
     m, g, dt = o.model, o.grid, o.dt
@@ -494,3 +495,57 @@ def stab_zero_is_the_plain_scheme() -> float:
     o1.start(phi0, "bdf1").step(3)
     o2.start(phi0, "bdf1").step(3)
     return float(np.max(np.abs(o1.phi - o2.phi)))
+
+
+
+# --- the optional phi^4 term (gamma3/4 ||phi||_4^4 in E_1, gamma3 phi^3 in N) ---
+
+def pin_gamma3_cosine() -> float:
+    """phi = c0 + A cos(k x_c) with gamma3 on: N gains gamma3 (phi^3 - mean phi^3)
+    = gamma3 (3 c0^2 A cos kx + 3/2 c0 A^2 cos 2kx + A^3/4 (3 cos kx + cos 3kx)), and
+    E_1 gains gamma3/4 |Omega| (c0^4 + 3 c0^2 A^2 + 3/8 A^4)."""
+    worst = 0.0
+    for d, n, L in ((2, 32, 16.0), (3, 16, 8.0)):
+        g = so.Grid(d, n, L)
+        for c in range(d):
+            for beta, g3 in ((1.0, 0.6), (0.7, 1.3)):
+                m = so.Model(g, eps=0.25, beta=beta)
+                m.gamma3 = g3
+                A, c0 = 0.8, 0.3
+                ell = 3 if 3 * 3 < g.n[c] // 2 else 2
+                k = 2 * math.pi * ell / g.L[c]
+                coords = np.meshgrid(*[np.arange(g.shape[ax]) * g.h[d - 1 - ax] for ax in range(d)],
+                                     indexing="ij")
+                x = coords[g.axis_of[c]]
+                phi = c0 + A * np.cos(k * x)
+                Nref = 0.75 * beta * A ** 3 * k ** 4 * (np.cos(k * x) - np.cos(3 * k * x)) \
+                    - 2 * A * k * k * np.cos(k * x) \
+                    + g3 * (3 * c0 * c0 * A * np.cos(k * x) + 1.5 * c0 * A * A * np.cos(2 * k * x)
+                            + 0.25 * A ** 3 * (3 * np.cos(k * x) + np.cos(3 * k * x)))
+                worst = max(worst, _rel(m.N_op(phi), Nref))
+                E1ref = g.volume * (beta / 4 * 3 / 8 * A ** 4 * k ** 4 - 0.5 * A * A * k * k) \
+                    + (1.0 + 1.0 / beta) * g.volume \
+                    + g3 / 4 * g.volume * (c0 ** 4 + 3 * c0 * c0 * A * A + 3 / 8 * A ** 4)
+                worst = max(worst, abs(m.E1(phi) - E1ref) / abs(E1ref))
+    return worst
+
+
+def pin_gamma3_variational() -> float:
+    """N_N is the gradient of E_{1,N} along mass-preserving directions:
+    (E1(phi + e psi) - E1(phi - e psi)) / (2 e) = <N_N(phi), psi> for mean-free psi
+    (central differences with one Richardson step: error O(e^4)), with and without gamma3."""
+    worst = 0.0
+    for d, n, L in ((2, 16, 8.0), (3, 8, 5.0)):
+        g = so.Grid(d, n, L)
+        phi = noisy_field(g.shape, 0.25, 0.4, 31)
+        phi = g.idft(g.dft(phi) * np.exp(-0.2 * g.K2))
+        psi = noisy_field(g.shape, 0.0, 1.0, 32)
+        psi = psi - psi.mean()
+        for g3 in (0.0, 0.9):
+            m = so.Model(g, eps=0.25, beta=1.1)
+            m.gamma3 = g3
+            cd = lambda e: (m.E1(phi + e * psi) - m.E1(phi - e * psi)) / (2 * e)
+            fd = (4.0 * cd(5e-4) - cd(1e-3)) / 3.0      # Richardson: O(e^4)
+            an = g.inner(m.N_op(phi), psi)
+            worst = max(worst, abs(fd - an) / abs(an))
+    return worst

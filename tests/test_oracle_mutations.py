@@ -24,6 +24,8 @@ PINS = [
     (P.pin_stab_residual, lambda v: v < 1e-10),
     (P.pin_stab_dissipation, lambda v: v < 1e-9),
     (P.pin_stab_linear_closed_form, lambda v: v < 1e-12),
+    (P.pin_gamma3_cosine, lambda v: v < 1e-12),
+    (P.pin_gamma3_variational, lambda v: v < 1e-9),
 ]
 
 
@@ -160,11 +162,41 @@ def _m_stab_symbol_without_dt(mp):
     mp.setattr(so, "A_inv", A_inv)
 
 
+def _m_gamma3_dropped_from_N(mp):
+    orig = so.Model.N_op
+
+    def N_op(self, phi):
+        g3, self.gamma3 = self.gamma3, 0.0
+        try:
+            return orig(self, phi)
+        finally:
+            self.gamma3 = g3
+    mp.setattr(so.Model, "N_op", N_op)
+
+
+def _m_gamma3_energy_factor(mp):
+    orig = so.Model.E1
+
+    def E1(self, phi):
+        return orig(self, phi) + (self.gamma3 / 4.0) * self.g.hd * float(np.sum(phi ** 4))
+    mp.setattr(so.Model, "E1", E1)
+
+
+def _m_gamma3_mean_kept(mp):
+    orig = so.Model.N_op
+
+    def N_op(self, phi):
+        n = orig(self, phi)
+        return n + float(np.mean(self.gamma3 * phi ** 3)) if self.gamma3 else n
+    mp.setattr(so.Model, "N_op", N_op)
+
+
 MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_axis,
              _m_wrong_bdf2_operator, _m_wrong_r_coefficient, _m_E1_constant_ignores_beta,
              _m_energy_quarter_dropped, _m_first_order_extrapolation,
              _m_dft_missing_normalisation, _m_linear_operator_sign, _m_laplacian_drops_nyquist,
-             _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt]
+             _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt,
+             _m_gamma3_dropped_from_N, _m_gamma3_energy_factor, _m_gamma3_mean_kept]
 
 
 def test_pins_pass_unmutated():

@@ -98,3 +98,15 @@ def test_stabilised_linear_part_closed_form():
 
 def test_zero_stabiliser_is_the_plain_scheme():
     assert P.stab_zero_is_the_plain_scheme() == 0.0
+
+
+def test_phi4_term_closed_form():
+    assert P.pin_gamma3_cosine() < 1e-12
+
+
+def test_potential_is_the_variational_derivative_of_E1():
+    assert P.pin_gamma3_variational() < 1e-9
+
+
+def test_scheme_residual_with_phi4_term():
+    assert P.pin_residual(2, gamma3=0.8) < 1e-12
