@@ -233,6 +233,50 @@ def measure_cube(steps, warmup, precision, peak, flush):
                          "note": "step level: 27 half-spectrum passes (6 kernels)"}}
 
 
+def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):
+    """The 512^2 crystallisation workload with the optional phi^4 term
+    (gamma3 = 1): the lazy three-pass step (column inverse with the pending
+    update, row pass, column forward with the scalar solve); L2 flushed before
+    each timed step. Algorithmic bytes: 19 half-spectrum passes per step
+    (column inverse: 3 reads and 4 writes; row: 3 and 3; column forward: 5
+    reads and the N_hat write)."""
+    import torch
+    from paper_2012_15133_gb300 import Solver
+    from seeded_inputs import crystal_2d_case
+    c = crystal_2d_case(N_GRID)
+    s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], precision)
+    s.set_gamma3(gamma3).init(c["phi0"], "bdf1")
+    s.step(max(3, warmup))
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(st)
+        s.step(1)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    s.sync()
+    s.set_timing(True)
+    for i in range(steps):
+        flush.fill_(float(i))
+        s.step(1)
+    kt = s.kernel_times()
+    s.set_timing(False)
+    s.sync()
+    csize = 8 if precision == "fp32" else 16
+    bytes_step = 19 * N_GRID * (N_GRID // 2 + 1) * csize
+    P = N_GRID * N_GRID
+    return {"workload": f"2D SPFC + gamma3 phi^4 term, {N_GRID}^2, L=256, eps=0.25, dt=0.05, gamma3={gamma3}, "
+                        "phi0=0.2+0.02U seed 1",
+            "value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "l2": "flushed before every timed step",
+            "kernels": {k: {"launches": v[0], "avg_us": v[1] / v[0] * 1e3} for k, v in kt.items()},
+            "roofline": {"bound": "hbm", "achieved": bytes_step / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_step / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_step": bytes_step,
+                         "note": "step level: 19 half-spectrum passes (3 kernels)"}}
+
+
 def measure_patterns(precision="fp32", n=256):
     """The paper's square-pattern run (Sec. 5.2): a = 0.5 on [0, 100]^2,
     phi0 = 0.05 (2 r - 1) (seed 21), dt = 0.01 up to t = 1000, then the copy
@@ -457,6 +501,7 @@ def run_ours(args):
         extras["ensemble"] = measure_ensemble(min(args.steps, 200), args.warmup, args.precision, peak, rank, world,
                                               dist)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
+        extras["gamma3"] = measure_gamma3(min(args.steps, 200), args.warmup, args.precision, peak, flush)
         if rank == 0:
             extras["patterns"] = measure_patterns()
         if not args.no_surrogate and rank == 0:
@@ -498,8 +543,8 @@ def run_ours(args):
 def run_driver(args):
     """Profiling driver (for ncu): init, then K steps of the workload with the
     kernels launched one by one (single runs) or graph-replayed (ensemble);
-    no timing, no flush. --workload crystal (2D, --n), cube (3D 128^3) or
-    ensemble (256 runs)."""
+    no timing, no flush. --workload crystal (2D, --n), gamma3 (the same with
+    the phi^4 term, gamma3 = 1), cube (3D 128^3) or ensemble (256 runs)."""
     import torch
     from paper_2012_15133_gb300 import Solver, Batch, build
     build.build()
@@ -540,6 +585,8 @@ def run_driver(args):
     from seeded_inputs import crystal_2d_case
     c = crystal_2d_case(args.n)
     s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+    if args.workload == "gamma3":
+        s.set_gamma3(1.0)
     s.init(c["phi0"], "bdf1")
     s.set_timing(True)
     s.step(args.steps)
@@ -566,7 +613,7 @@ def main():
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
-    ap.add_argument("--workload", default="crystal", choices=["crystal", "cube", "ensemble", "surrogate"],
+    ap.add_argument("--workload", default="crystal", choices=["crystal", "gamma3", "cube", "ensemble", "surrogate"],
                     help="workload of --ncu-driver")
     args = ap.parse_args()
     if args.ncu_driver:

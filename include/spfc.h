@@ -145,10 +145,26 @@ int spfc_dt_change(spfc_t h, double dt_new);
  * non-finite A. */
 int spfc_set_stabilization(spfc_t h, double A);
 
+/* Optional phi^4 term (the local part of the PFC free energy, Sec. 1): E_1
+ * gains gamma3/4 ||phi||_4^4, so that E_1 >= |Omega| still holds, and the
+ * nonlinear chemical potential N_N gains gamma3 phi^3 with its mean removed
+ * (its zero mode never enters the mass-conserving scheme). The SAV scheme of
+ * Sec. 2.2-2.3 is otherwise unchanged. gamma3 >= 0; 0, the default, is the
+ * SPFC model. 2D single runs only: a 3D handle accepts gamma3 = 0 alone
+ * (SPFC_EINVAL otherwise). With gamma3 > 0 a step takes three kernels (the
+ * lazy form) instead of two, and the first call allocates one more
+ * half-spectrum work array (SPFC_ENOMEM if that fails). Set before spfc_init
+ * it also applies to the start-up step; set later it applies to the steps
+ * that follow (a pending update is completed first). Checkpoints record gamma3
+ * and spfc_load requires the same value. SPFC_EINVAL for a negative or
+ * non-finite gamma3. */
+int spfc_set_gamma3(spfc_t h, double gamma3);
+
 /* Write / read a checkpoint: the exact device state (both spectral levels in the
  * handle's precision, r^n, r^{n-1}, the step count) plus the grid and parameters.
  * A resumed run continues bit-identically. spfc_load rejects a file whose grid,
- * precision, L, dt, eps or beta differ from the handle's (SPFC_EINVAL). */
+ * precision, L, dt, eps, beta, stabiliser A or gamma3 differ from the
+ * handle's (SPFC_EINVAL). */
 int spfc_save(spfc_t h, const char* path);
 int spfc_load(spfc_t h, const char* path);
 

@@ -29,6 +29,13 @@ class SolverBase {
   virtual int get_field(double* out, bool on_device, int which) = 0;
   virtual int dt_change(double dt) = 0;
   virtual int set_stab(double A) = 0;  // stabiliser of Sec. 5.2 for the following steps
+  // optional phi^4 term (gamma3 >= 0) for the following steps; where a solver
+  // has no such kernels only gamma3 = 0 is accepted
+  virtual int set_gamma3(double g3) {
+    if (g3 == 0.0) return 0;
+    err = "the phi^4 term is implemented for 2D single runs only";
+    return 1;
+  }
   virtual int sync() = 0;
   virtual int set_timing(bool on) = 0;
   virtual int kernel_times(KernelTimes* kt) = 0;
@@ -54,6 +61,9 @@ inline void fill_float_params(Params* P) {
   P->invP_f = (float)P->invP;
   P->sdt = P->stab * P->dt;
   P->sdt_f = (float)P->sdt;
+  P->g3b = (P->beta > 0.0) ? P->g3 / P->beta : 0.0;
+  P->g3_f = (float)P->g3;
+  P->g3b_f = (float)P->g3b;
   auto split = [](double x, float* o) {
     o[0] = (float)x;
     o[1] = (float)(x - (double)o[0]);

@@ -38,15 +38,16 @@ template <typename R> __device__ __forceinline__ R kderiv(int i, int N, R kf) {
 // Per-run constants in the working precision (read, never converted, per thread).
 template <typename R> struct PC;
 template <> struct PC<double> {
-  double kfx, kfy, kfz, dt, a, beta, invP, sdt;
+  double kfx, kfy, kfz, dt, a, beta, invP, sdt, g3, g3b;
   __device__ __forceinline__ explicit PC(const Params& P)
-      : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP), sdt(P.sdt) {}
+      : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP), sdt(P.sdt),
+        g3(P.g3), g3b(P.g3b) {}
 };
 template <> struct PC<float> {
-  float kfx, kfy, kfz, dt, a, beta, invP, sdt;
+  float kfx, kfy, kfz, dt, a, beta, invP, sdt, g3, g3b;
   __device__ __forceinline__ explicit PC(const Params& P)
       : kfx(P.kf_f[0]), kfy(P.kf_f[1]), kfz(P.kf_f[2]), dt(P.dt_f), a(P.a_f), beta(P.beta_f), invP(P.invP_f),
-        sdt(P.sdt_f) {}
+        sdt(P.sdt_f), g3(P.g3_f), g3b(P.g3b_f) {}
 };
 template <typename R> __device__ __forceinline__ R read_alpha(const SavScal* sc);
 template <> __device__ __forceinline__ double read_alpha<double>(const SavScal* sc) { return sc->alpha; }
@@ -120,14 +121,19 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha, R s
 // rows y = lane + i T (i < E) of column kx0 + c, for every field of the pass
 // (one warp then reads 32/CT rows of CT adjacent columns). The column FFTs
 // keep their first and last stages in registers (fft_regs_multi).
+// G3 (the optional phi^4 term): the passes carry a third field, phi* itself
+// (inverse pass, into W2) and the x-transformed gamma3 phi*^3 (forward pass,
+// from W2), whose y-transform joins N_hat.
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int CT, int MODE>
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
                                                  C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
-                                                 SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
+                                                 SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which,
+                                                 C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
+  constexpr int NF = (MODE == CI_FIELD) ? 1 : (G3 ? 3 : 2);
+  static_assert(!G3 || MODE == CI_STEP || MODE == CI_GRAD, "the phi^4 channel is carried by the step and gradient modes");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
@@ -181,7 +187,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int ky = lane + i * T;
-    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
+    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0), g2 = mk<C>(0, 0);
     if (col) {
       const size_t off = (size_t)ky * NH + kx;
       C ph = vcur[i];
@@ -211,10 +217,12 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
         const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
         g0 = mk<C>(-ktx * ph.y, ktx * ph.x);  // i k~_x phi
         g1 = mk<C>(-kty * ph.y, kty * ph.x);  // i k~_y phi
+        g2 = ph;
       }
     }
     g[0][i] = g0;
-    if (NF == 2) g[NF - 1][i] = g1;
+    if constexpr (NF >= 2) g[1][i] = g1;
+    if constexpr (NF == 3) g[2][i] = g2;
   }
   fft_regs_multi<C, N, E, true, NF, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
   if (col) {
@@ -222,7 +230,8 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
     for (int i = 0; i < E; ++i) {
       const size_t off = (size_t)(lane + i * T) * NH + kx;
       W0[off] = g[0][i];
-      if (NF == 2) W1[off] = g[NF - 1][i];
+      if constexpr (NF >= 2) W1[off] = g[1][i];
+      if constexpr (NF == 3) W2[off] = g[2][i];
     }
   }
 }
@@ -234,15 +243,30 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   k2d_col_inv_body<R, N, E, CT, MODE>(P, S, Nhat, W0, W1, sc, tw, which);
 }
 
+// with the phi^4 channel (W2 receives the y-inverse of phi*)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k2d_col_inv_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
+               C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2, SavScal* __restrict__ sc,
+               const C_t<R>* __restrict__ tw, int which) {
+  k2d_col_inv_body<R, N, E, CT, MODE, true>(P, S, Nhat, W0, W1, sc, tw, which, W2);
+}
+
 // ---------------------------------------------------------------------------
 // Row pass. Grid: N/RPC blocks, RPC rows each, T = N/E lanes per row.
 // part: 2 x gridDim.x doubles: sum s^2 and sum s per block (without h^d).
+// G3: each row also inverse-transforms phi* (from W2), adds (gamma3/beta) phi*^4
+// to the sum of s^2 (E_1 takes that sum with beta/4) and, for the step,
+// forward-transforms gamma3 phi*^3 into W2; shared memory holds two sequences
+// per row.
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int RPC, int MODE>
+template <typename R, int N, int E, int RPC, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
                                              double* __restrict__ part, const SavScal* __restrict__ sc,
-                                             const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
+                                             const C_t<R>* __restrict__ tw, double* __restrict__ real_io,
+                                             C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
+  static_assert(!G3 || MODE == RW_NONLIN || MODE == RW_ENERGY, "the phi^4 channel is carried by the nonlinear and energy modes");
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NTH = RPC * T;
   constexpr int NH = N / 2 + 1;
@@ -259,7 +283,7 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
   if (sc->status != DEV_OK) return;
   const int rloc = threadIdx.x / T, lane = threadIdx.x % T;
   const int row = blockIdx.x * RPC + rloc;
-  C* z = sm + rloc * (SEQ + 1);
+  C* z = sm + rloc * (G3 ? 2 : 1) * (SEQ + 1);
   const size_t roff = (size_t)row * NH;
 
   if constexpr (MODE == RW_IN_REAL) {
@@ -290,6 +314,61 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
     fft_smem<C, N, E, true>(z, 1, lane, tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
+  } else if constexpr (G3) {
+    // sequence 0: Z = G_x + i G_y as below; sequence 1: the x-spectrum of phi*
+    // (Hermitian, so its inverse is real)
+    C v[2][E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = lane + i * T;
+      const bool direct = k <= N / 2;
+      const size_t off = roff + (direct ? k : N - k);
+      const C a = W0[off], b = W1[off], f = W2[off];
+      v[0][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
+      v[1][i] = direct ? f : cconj(f);
+    }
+    fft_regs_multi<C, N, E, true, 2, false>(v, z, SEQ + 1, 1, lane, tw);
+    typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
+    const PC<R> pc(P);
+    const R beta = pc.beta, g3 = pc.g3, g3b = pc.g3b;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const C g = v[0][i];
+      const R s = g.x * g.x + g.y * g.y;
+      const R ph = v[1][i].x, p2 = ph * ph;
+      acc2 = RD::add(acc2, s * s + g3b * (p2 * p2));
+      acc1 = RD::add(acc1, s);
+      if (MODE == RW_NONLIN) {
+        const R fac = beta * s - (R)2;
+        v[0][i] = mk<C>(fac * g.x, fac * g.y);
+        v[1][i] = mk<C>(g3 * p2 * ph, (R)0);
+      }
+    }
+    if constexpr (MODE == RW_NONLIN) {
+      fft_regs_multi<C, N, E, false, 2, false>(v, z, SEQ + 1, 1, lane, tw);
+      fft_sync<N, E>();
+#pragma unroll
+      for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = v[0][i];
+      fft_sync<N, E>();
+      const R half = (R)0.5 * pc.invP;
+#pragma unroll
+      for (int i = 0; i < KH + 1; ++i) {
+        if (i == KH && lane != 0) break;
+        const int kk = lane + i * T;
+        const C zk = v[0][i], zm = cconj(z[sp((N - kk) & (N - 1))]);
+        const C sx = cadd(zk, zm), dy = csub(zk, zm);
+        W0[roff + kk] = cscale(sx, half);
+        W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);
+        W2[roff + kk] = cscale(v[1][i], pc.invP);  // x-spectrum of gamma3 phi*^3, k <= N/2
+      }
+    }
+    typename RD::acc t21[2] = {acc2, acc1};
+    block_red_multi<R, 2>(t21, red2);
+    if (threadIdx.x == 0) {
+      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
+      ps[blockIdx.x] = t21[0];
+      ps[gridDim.x + blockIdx.x] = t21[1];
+    }
   } else {
     // Z = G_x + i G_y over the full x-spectrum, element k = lane + i T loaded
     // straight into registers: k <= N/2 from the half spectrum, k > N/2 as
@@ -356,6 +435,14 @@ __global__ void __launch_bounds__(RPC * (N / E))
 k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double* __restrict__ part,
         const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, double* __restrict__ real_io) {
   k2d_row_body<R, N, E, RPC, MODE>(P, W0, W1, part, sc, tw, real_io);
+}
+
+// with the phi^4 channel (W2: y-inverse of phi* in, x-spectrum of gamma3 phi*^3 out)
+template <typename R, int N, int E, int RPC, int MODE>
+__global__ void __launch_bounds__(RPC * (N / E))
+k2d_row_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+           double* __restrict__ part, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
+  k2d_row_body<R, N, E, RPC, MODE, true>(P, W0, W1, part, sc, tw, nullptr, W2);
 }
 
 // Scalar SAV solve (eqs. solver-2, solver-4 and solver-6 reduced to scalars).
@@ -512,15 +599,18 @@ __device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const type
 // Column forward pass (thread layout as the inverse pass).
 // partG: 3 x gridDim.x doubles (gamma, eta, theta partial sums, without |Omega|).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int CT, int MODE>
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ W0,
                                                  const C_t<R>* __restrict__ W1, C_t<R>* __restrict__ Nhat,
                                                  double* __restrict__ partG, const double* __restrict__ partE,
                                                  int nE, SavScal* __restrict__ sc, unsigned* __restrict__ counter,
-                                                 const C_t<R>* __restrict__ tw, int target) {
+                                                 const C_t<R>* __restrict__ tw, int target,
+                                                 const C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
+  constexpr int NF = (MODE == CF_TO_STATE) ? 1 : (G3 ? 3 : 2);
+  static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT,
+                "the phi^4 channel is carried by the modes that form N_hat");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
@@ -545,7 +635,8 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   for (int i = 0; i < E; ++i) {
     const size_t off = (size_t)(lane + i * T) * NH + kx;
     v[0][i] = col ? W0[off] : mk<C>(0, 0);
-    if (NF == 2) v[NF - 1][i] = col ? W1[off] : mk<C>(0, 0);
+    if constexpr (NF >= 2) v[1][i] = col ? W1[off] : mk<C>(0, 0);
+    if constexpr (NF == 3) v[2][i] = col ? W2[off] : mk<C>(0, 0);
   }
 
   if constexpr (MODE == CF_TO_STATE) {
@@ -587,11 +678,13 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       const int ky = lane + i * T;
       if (!col) continue;
       const size_t off = (size_t)ky * NH + kx;
-      const C wx = v[0][i], wy = v[NF - 1][i];
+      const C wx = v[0][i], wy = v[1][i];
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
       // N_hat = -i (k~_x W_x + k~_y W_y)
       const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
-      const C nh = mk<C>(uy, -ux);
+      C nh = mk<C>(uy, -ux);
+      // G3: + the transform of gamma3 phi*^3, whose mean is removed (N_hat_0 := 0)
+      if constexpr (G3) nh = (off == 0) ? mk<C>(0, 0) : cadd(nh, v[2][i]);
       Nhat[off] = nh;
       if (MODE == CF_NHAT) continue;
       const R K2 = sym_K2<R>(kx, ky, N, pc);
@@ -654,6 +747,16 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
             SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
             int target) {
   k2d_col_fwd_body<R, N, E, CT, MODE>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, target);
+}
+
+// with the phi^4 channel (W2: x-spectrum of gamma3 phi*^3)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k2d_col_fwd_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
+               const C_t<R>* __restrict__ W2, C_t<R>* __restrict__ Nhat, double* __restrict__ partG,
+               const double* __restrict__ partE, int nE, SavScal* __restrict__ sc, unsigned* __restrict__ counter,
+               const C_t<R>* __restrict__ tw) {
+  k2d_col_fwd_body<R, N, E, CT, MODE, true>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, 0, W2);
 }
 
 // ---------------------------------------------------------------------------

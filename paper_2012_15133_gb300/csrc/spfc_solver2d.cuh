@@ -180,8 +180,8 @@ class Solver2D final : public SolverBase {
     if (g16_) cudaGraphExecDestroy(g16_);
     for (auto ev : evpool_) cudaEventDestroy(ev);
     if (cap_st_) cudaStreamDestroy(cap_st_);
-    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], real_, partE_, partG_, partN_, partS_, sc_, counter_,
-                    sync64_, tw_};
+    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W2_, real_, partE_, partG_, partN_, partS_, sc_,
+                    counter_, sync64_, tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -192,7 +192,15 @@ class Solver2D final : public SolverBase {
   int init(const double* phi0, bool on_device, int mode) override {
     int rc = load_field(phi0, on_device, /*slot_rel=*/0, /*reset=*/true);
     if (rc) return rc;
-    if (mode == 0) {  // BDF1: the first step, which also prepares W for the second
+    if (mode == 0 && g3_on()) {  // BDF1 with the phi^4 term: the lazy form, completed at once
+      rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
+      rc = launch_row(RW_NONLIN); if (rc) return rc;
+      rc = launch_col_fwd(CF_BDF1, 0); if (rc) return rc;
+      rc = finalize(); if (rc) return rc;
+      w_ready_ = false;
+      inited = true;
+      return sync();
+    } else if (mode == 0) {  // BDF1: the first step, which also prepares W for the second
       rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
       rc = launch_row(RW_NONLIN); if (rc) return rc;
       rc = launch_fused(true); if (rc) return rc;
@@ -245,6 +253,35 @@ class Solver2D final : public SolverBase {
     return 0;
   }
 
+  // The phi^4 term's kernels carry a third work array, allocated when the
+  // term is first switched on. With it on, a step is the lazy three-pass form
+  // (column inverse with the pending update, row pass, column forward with
+  // the scalar solve) rather than row pass + fused column pass.
+  int set_gamma3(double g3) override {
+    if (inited) { int rc = finalize(); if (rc) return rc; }
+    if (g3 != 0.0 && !W2_) {
+      cudaError_t e = cudaMalloc((void**)&W2_, spec_bytes_);
+      if (e != cudaSuccess) {
+        W2_ = nullptr;
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return (e == cudaErrorMemoryAllocation) ? 2 : 3;
+      }
+      total_ += spec_bytes_;
+      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_STEP>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_GRAD>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_row_g3<R, N, E, RPC, RW_NONLIN>, 2 * smem_row()));
+      SPFC_CK(set_smem(k2d_row_g3<R, N, E, RPC, RW_ENERGY>, 2 * smem_row()));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF2>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF1>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_NHAT>, smem_col(3)));
+    }
+    P.g3 = g3;
+    fill_float_params(&P);
+    drop_graphs();
+    w_ready_ = false;
+    return 0;
+  }
+
   int dt_change(double dt) override {
     int rc = finalize(); if (rc) return rc;
     P.dt = dt;
@@ -262,7 +299,7 @@ class Solver2D final : public SolverBase {
   // ---- stepping ------------------------------------------------------------
   int step(long long n) override {
     if (n <= 0) return 0;
-    if (!w_ready_) {
+    if (!w_ready_ && !g3_on()) {
       // W <- inverse DFT in y of i k~ (2 phi^n - phi^{n-1}): the first half of a step
       int rc = finalize(); if (rc) return rc;
       rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
@@ -384,7 +421,7 @@ class Solver2D final : public SolverBase {
     }
     trecs_.clear();
     evnext_ = 0;
-    kt->names = {"row", "col_fused"};
+    kt->names = {"row", g3_on() ? "col_inv+col_fwd" : "col_fused"};
     kt->launches.assign(tcount_, tcount_ + 2);
     kt->ms.assign(tms_, tms_ + 2);
     for (int i = 0; i < 3; ++i) { tcount_[i] = 0; tms_[i] = 0.0; }
@@ -399,7 +436,17 @@ class Solver2D final : public SolverBase {
   static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * CTP * sizeof(C); }
   static constexpr size_t smem_row() { return (size_t)RPC * (sp_len(N) + 1) * sizeof(C); }
 
+  bool g3_on() const { return P.g3 != 0.0; }
+
   int launch_col_inv(int mode, int which) {
+    if (g3_on() && (mode == CI_STEP || mode == CI_GRAD)) {
+      if (mode == CI_STEP)
+        k2d_col_inv_g3<R, N, E, CT, CI_STEP><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
+      else
+        k2d_col_inv_g3<R, N, E, CT, CI_GRAD><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case CI_STEP:
         SPFC_CK(launch_k(k2d_col_inv<R, N, E, CT, CI_STEP>, GCOL, CT * T, smem_col(2), st_, pdl_, false, P, S_, Nhat_,
@@ -415,6 +462,14 @@ class Solver2D final : public SolverBase {
     return 0;
   }
   int launch_row(int mode) {
+    if (g3_on() && (mode == RW_NONLIN || mode == RW_ENERGY)) {
+      if (mode == RW_NONLIN)
+        k2d_row_g3<R, N, E, RPC, RW_NONLIN><<<GROW, RPC * T, 2 * smem_row(), st_>>>(P, W_[0], W_[1], W2_, partE_, sc_, tw_);
+      else
+        k2d_row_g3<R, N, E, RPC, RW_ENERGY><<<GROW, RPC * T, 2 * smem_row(), st_>>>(P, W_[0], W_[1], W2_, partE_, sc_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case RW_NONLIN:
         SPFC_CK(launch_k(k2d_row<R, N, E, RPC, RW_NONLIN>, GROW, RPC * T, smem_row(), st_, pdl_, false, P, W_[0], W_[1],
@@ -433,6 +488,16 @@ class Solver2D final : public SolverBase {
     return 0;
   }
   int launch_col_fwd(int mode, int target) {
+    if (g3_on() && mode != CF_TO_STATE) {
+      if (mode == CF_BDF2)
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      else if (mode == CF_BDF1)
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      else
+        k2d_col_fwd_g3<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case CF_BDF2:
         SPFC_CK(launch_k(k2d_col_fwd<R, N, E, CT, CF_BDF2>, GCOL, CT * T, smem_col(2), st_, pdl_, false, P, S_, W_[0],
@@ -510,6 +575,11 @@ class Solver2D final : public SolverBase {
   // one step with W prepared: row pass, then the fused column pass (which
   // prepares W for the next step)
   int launch_step_kernels() {
+    if (g3_on()) {  // lazy three-pass form: the update stays pending between steps
+      int rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
+      rc = launch_row(RW_NONLIN); if (rc) return rc;
+      return launch_col_fwd(CF_BDF2, 0);
+    }
     int rc = launch_row(RW_NONLIN); if (rc) return rc;
     return launch_fused(false);
   }
@@ -566,6 +636,21 @@ class Solver2D final : public SolverBase {
 
   int timed_step() {
     int e0, e1, e2, rc;
+    if (g3_on()) {  // row pass in class 0, the two column passes in class 1
+      int e3;
+      if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2)) || (rc = ev(&e3))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e0], st_));
+      if ((rc = launch_col_inv(CI_STEP, 0))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e1], st_));
+      if ((rc = launch_row(RW_NONLIN))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e2], st_));
+      if ((rc = launch_col_fwd(CF_BDF2, 0))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e3], st_));
+      trecs_.push_back({1, e0, e1});
+      trecs_.push_back({0, e1, e2});
+      trecs_.push_back({1, e2, e3});
+      return 0;
+    }
     if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2))) return rc;
     SPFC_CK(cudaEventRecord(evpool_[e0], st_));
     if ((rc = launch_row(RW_NONLIN))) return rc;
@@ -583,6 +668,7 @@ class Solver2D final : public SolverBase {
   Slots<R> S_{{nullptr, nullptr}};
   C* Nhat_ = nullptr;
   C* W_[2] = {nullptr, nullptr};
+  C* W2_ = nullptr;                 // third work array of the phi^4 term (allocated on demand)
   double* real_ = nullptr;
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
   SavScal* sc_ = nullptr;

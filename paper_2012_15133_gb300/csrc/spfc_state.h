@@ -29,6 +29,11 @@ struct Params {
   double stab;    // A
   double sdt;     // A dt
   float sdt_f;
+  // optional phi^4 term: E_1 gains gamma3/4 ||phi||_4^4 and N gains gamma3 phi^3
+  // with its mean removed (2D single runs); gamma3 = 0 is the SPFC model
+  double g3;      // gamma3
+  double g3b;     // gamma3 / beta (folded into the sum of s^2 that E_1 takes with beta/4)
+  float g3_f, g3b_f;
 };
 
 enum PendingKind : int { PEND_NONE = 0, PEND_BDF2 = 1, PEND_BDF1 = 2 };

@@ -43,6 +43,7 @@ _SIGS = {
     "spfc_get_field": (_I, [_P, _P, _I, _I]),
     "spfc_dt_change": (_I, [_P, _D]),
     "spfc_set_stabilization": (_I, [_P, _D]),
+    "spfc_set_gamma3": (_I, [_P, _D]),
     "spfc_save": (_I, [_P, ct.c_char_p]),
     "spfc_load": (_I, [_P, ct.c_char_p]),
     "spfc_sync": (_I, [_P]),
@@ -153,6 +154,7 @@ class Solver:
         L = [float(L)] * self.d if np.isscalar(L) else [float(v) for v in L]
         self.n, self.L = n, L
         self.eps, self.beta, self.dt = float(eps), float(beta), float(dt)
+        self.stab = self.gamma3 = 0.0
         self.shape = tuple(reversed(n))
         self.precision = _PREC[precision]
         if stream is None:
@@ -250,6 +252,13 @@ class Solver:
         """The stabilised scheme of Sec. 5.2 with constant A >= 0 (0: plain)."""
         self._check(self._lib.spfc_set_stabilization(self._h, float(A)))
         self.stab = float(A)
+        return self
+
+    def set_gamma3(self, gamma3):
+        """The optional phi^4 term: E_1 gains gamma3/4 ||phi||_4^4 and N gains
+        gamma3 phi^3 with its mean removed (2D single runs; 0: SPFC)."""
+        self._check(self._lib.spfc_set_gamma3(self._h, float(gamma3)))
+        self.gamma3 = float(gamma3)
         return self
 
     def save(self, path):
