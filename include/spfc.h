@@ -150,10 +150,10 @@ int spfc_set_stabilization(spfc_t h, double A);
  * nonlinear chemical potential N_N gains gamma3 phi^3 with its mean removed
  * (its zero mode never enters the mass-conserving scheme). The SAV scheme of
  * Sec. 2.2-2.3 is otherwise unchanged. gamma3 >= 0; 0, the default, is the
- * SPFC model. 2D single runs only: a 3D handle accepts gamma3 = 0 alone
- * (SPFC_EINVAL otherwise). With gamma3 > 0 a step takes three kernels (the
- * lazy form) instead of two, and the first call allocates one more
- * half-spectrum work array (SPFC_ENOMEM if that fails). Set before spfc_init
+ * SPFC model. Single runs in 2D and 3D (the batched ensemble runs SPFC). With
+ * gamma3 > 0 a 2D step takes three kernels (the lazy form) instead of two, a
+ * 3D step keeps its six, and the first call allocates one more half-spectrum
+ * work array (SPFC_ENOMEM if that fails). Set before spfc_init
  * it also applies to the start-up step; set later it applies to the steps
  * that follow (a pending update is completed first). Checkpoints record gamma3
  * and spfc_load requires the same value. SPFC_EINVAL for a negative or

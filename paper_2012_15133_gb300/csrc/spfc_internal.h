@@ -29,11 +29,11 @@ class SolverBase {
   virtual int get_field(double* out, bool on_device, int which) = 0;
   virtual int dt_change(double dt) = 0;
   virtual int set_stab(double A) = 0;  // stabiliser of Sec. 5.2 for the following steps
-  // optional phi^4 term (gamma3 >= 0) for the following steps; where a solver
-  // has no such kernels only gamma3 = 0 is accepted
+  // optional phi^4 term (gamma3 >= 0) for the following steps; a solver
+  // without such kernels accepts gamma3 = 0 only
   virtual int set_gamma3(double g3) {
     if (g3 == 0.0) return 0;
-    err = "the phi^4 term is implemented for 2D single runs only";
+    err = "this solver has no kernels for the phi^4 term";
     return 1;
   }
   virtual int sync() = 0;

@@ -121,9 +121,12 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha, R s
 // rows y = lane + i T (i < E) of column kx0 + c, for every field of the pass
 // (one warp then reads 32/CT rows of CT adjacent columns). The column FFTs
 // keep their first and last stages in registers (fft_regs_multi).
-// G3 (the optional phi^4 term): the passes carry a third field, phi* itself
-// (inverse pass, into W2) and the x-transformed gamma3 phi*^3 (forward pass,
-// from W2), whose y-transform joins N_hat.
+// G3 (the optional phi^4 term): the passes carry a third field with no third
+// transform, since k~_x is constant along a column. The inverse pass
+// transforms phi* and i k~_y phi* and forms G_x = i k~_x Y^-1 phi* in registers,
+// storing Y^-1 phi* in W2 as well. The forward pass transforms k~_x W_x + i W2
+// (W2 then holds the x-spectrum of gamma3 phi*^3) and W_y, so that
+// -i (first + k~_y second) is N_hat with the transform of gamma3 phi*^3 added.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
@@ -132,7 +135,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
                                                  C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CI_FIELD) ? 1 : (G3 ? 3 : 2);
+  constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
   static_assert(!G3 || MODE == CI_STEP || MODE == CI_GRAD, "the phi^4 channel is carried by the step and gradient modes");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
@@ -187,7 +190,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int ky = lane + i * T;
-    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0), g2 = mk<C>(0, 0);
+    C g0 = mk<C>(0, 0), g1 = mk<C>(0, 0);
     if (col) {
       const size_t off = (size_t)ky * NH + kx;
       C ph = vcur[i];
@@ -215,23 +218,27 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
         g0 = ph;
       } else {
         const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
-        g0 = mk<C>(-ktx * ph.y, ktx * ph.x);  // i k~_x phi
-        g1 = mk<C>(-kty * ph.y, kty * ph.x);  // i k~_y phi
-        g2 = ph;
+        g0 = G3 ? ph : mk<C>(-ktx * ph.y, ktx * ph.x);  // i k~_x phi (G3: phi)
+        g1 = mk<C>(-kty * ph.y, kty * ph.x);            // i k~_y phi
       }
     }
     g[0][i] = g0;
-    if constexpr (NF >= 2) g[1][i] = g1;
-    if constexpr (NF == 3) g[2][i] = g2;
+    if (NF == 2) g[NF - 1][i] = g1;
   }
   fft_regs_multi<C, N, E, true, NF, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
   if (col) {
+    const R ktx = kderiv<R>(kx, N, pc.kfx);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const size_t off = (size_t)(lane + i * T) * NH + kx;
-      W0[off] = g[0][i];
-      if constexpr (NF >= 2) W1[off] = g[1][i];
-      if constexpr (NF == 3) W2[off] = g[2][i];
+      if constexpr (G3) {
+        const C f = g[0][i];
+        W0[off] = mk<C>(-ktx * f.y, ktx * f.x);  // G_x = i k~_x Y^-1 phi*
+        W2[off] = f;                              // Y^-1 phi*
+      } else {
+        W0[off] = g[0][i];
+      }
+      if (NF == 2) W1[off] = g[NF - 1][i];
     }
   }
 }
@@ -608,7 +615,7 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
                                                  const C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CF_TO_STATE) ? 1 : (G3 ? 3 : 2);
+  constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
   static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT,
                 "the phi^4 channel is carried by the modes that form N_hat");
   constexpr int NTH = CT * T;
@@ -635,8 +642,12 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   for (int i = 0; i < E; ++i) {
     const size_t off = (size_t)(lane + i * T) * NH + kx;
     v[0][i] = col ? W0[off] : mk<C>(0, 0);
-    if constexpr (NF >= 2) v[1][i] = col ? W1[off] : mk<C>(0, 0);
-    if constexpr (NF == 3) v[2][i] = col ? W2[off] : mk<C>(0, 0);
+    if (NF == 2) v[NF - 1][i] = col ? W1[off] : mk<C>(0, 0);
+    if constexpr (G3) {  // k~_x W_x + i W2: one sequence for both
+      const R ktx = kderiv<R>(kx, N, PC<R>(P).kfx);
+      const C f = col ? W2[off] : mk<C>(0, 0), wx = v[0][i];
+      v[0][i] = mk<C>(ktx * wx.x - f.y, ktx * wx.y + f.x);
+    }
   }
 
   if constexpr (MODE == CF_TO_STATE) {
@@ -681,10 +692,16 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       const C wx = v[0][i], wy = v[1][i];
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
       // N_hat = -i (k~_x W_x + k~_y W_y)
-      const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
-      C nh = mk<C>(uy, -ux);
-      // G3: + the transform of gamma3 phi*^3, whose mean is removed (N_hat_0 := 0)
-      if constexpr (G3) nh = (off == 0) ? mk<C>(0, 0) : cadd(nh, v[2][i]);
+      C nh;
+      if constexpr (G3) {
+        // -i (Y(k~_x W_x + i W2) + k~_y W_y): the transform of gamma3 phi*^3 joins
+        // N_hat, whose zero mode (the mean of gamma3 phi*^3) is removed
+        const R ux = wx.x + kty * wy.x, uy = wx.y + kty * wy.y;
+        nh = (off == 0) ? mk<C>(0, 0) : mk<C>(uy, -ux);
+      } else {
+        const R ux = ktx * wx.x + kty * wy.x, uy = ktx * wx.y + kty * wy.y;
+        nh = mk<C>(uy, -ux);
+      }
       Nhat[off] = nh;
       if (MODE == CF_NHAT) continue;
       const R K2 = sym_K2<R>(kx, ky, N, pc);

@@ -16,6 +16,14 @@
 //   z-inv  : phi^{n+1} = alpha A^{-1} Delta N_hat + A^{-1} v (eq. solver-6), phi* =
 //            2 phi^{n+1} - phi^n, inverse DFT in z of phi* and of i k~_z phi*;
 //   y-inv  : inverse DFT in y of i k~_y F, F and G_z; W_x = i k~_x (.) of F's.
+//
+// The optional phi^4 term (G3 variants) needs no further z- or y-transform:
+// y-inv also stores Y^-1 F (the x-spectrum of phi*) in W3; the row pass
+// carries phi*(row 0) + i phi*(row 1) as a fourth sequence, adds
+// (gamma3/beta) phi*^4 to the sum of s^2 and returns gamma3 phi*^3 in W3; y-fwd
+// transforms k~_x W_x + i W3 as one sequence (k~_x is constant along y), so
+// that Q1 carries i Y(W3) and -i (Q1 + k~_z Q2) gains the transform of
+// gamma3 phi*^3; z-fwd removes its mean (N_hat_0 := 0).
 #pragma once
 
 #include "spfc_kernels2d.cuh"
@@ -45,11 +53,12 @@ template <int MODE> struct y3_nf { static constexpr int in = (MODE == Y3_FWD) ? 
 // ---------------------------------------------------------------------------
 
 // y pass: tile of CT kx columns in plane z = blockIdx.y.
-template <typename R, int N, int E, int CT, int MODE>
-__global__ void __launch_bounds__(CT * (N / E))
-k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
-          const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
+__device__ __forceinline__ void k3d_ypass_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
+                                               C_t<R>* __restrict__ W2, const SavScal* __restrict__ sc,
+                                               const C_t<R>* __restrict__ tw, C_t<R>* __restrict__ W3 = nullptr) {
   using C = C_t<R>;
+  static_assert(!G3 || MODE == Y3_FWD || MODE == Y3_INV, "the phi^4 channel rides on the gradient passes");
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = y3_nf<MODE>::fft;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;
@@ -79,6 +88,11 @@ k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<
       v[0][i] = W0[off];
       v[NF - 2][i] = W1[off];
       v[NF - 1][i] = W2[off];
+      if constexpr (G3) {  // k~_x W_x + i W3 as one sequence
+        const R ktx = kderiv<R>(kx, N, pc.kfx);
+        const C f = W3[off], wx = v[0][i];
+        v[0][i] = mk<C>(ktx * wx.x - f.y, ktx * wx.y + f.x);
+      }
     } else if constexpr (MODE == Y3_INV) {
       const C F = W0[off];
       const R kty = kderiv<R>(y, N, pc.kfy);
@@ -98,27 +112,45 @@ k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<
     if constexpr (MODE == Y3_FWD) {
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(y, N, pc.kfy);
       const C a = v[0][i], b = v[NF - 2][i];
-      W0[off] = mk<C>(ktx * a.x + kty * b.x, ktx * a.y + kty * b.y);  // Q1
-      W1[off] = v[NF - 1][i];                                         // Q2
+      if constexpr (G3) W0[off] = mk<C>(a.x + kty * b.x, a.y + kty * b.y);  // Q1 + i Y(W3)
+      else W0[off] = mk<C>(ktx * a.x + kty * b.x, ktx * a.y + kty * b.y);  // Q1
+      W1[off] = v[NF - 1][i];                                              // Q2
     } else if constexpr (MODE == Y3_INV) {
       const R ktx = kderiv<R>(kx, N, pc.kfx);
       const C Fy = v[NF - 2][i];
       W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);  // W_x = i k~_x Y^-1 F
       W1[off] = v[0][i];                          // W_y
       W2[off] = v[NF - 1][i];                     // W_z
+      if constexpr (G3) W3[off] = Fy;             // Y^-1 F: phi* along x as a spectrum
     } else {
       W0[off] = v[0][i];
     }
   }
 }
 
-// z forward pass: tile of CT kx columns at ky = blockIdx.y.
 template <typename R, int N, int E, int CT, int MODE>
 __global__ void __launch_bounds__(CT * (N / E))
-k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
-         C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const SavScal* __restrict__ sc,
-         const C_t<R>* __restrict__ tw, int target) {
+k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+          const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
+  k3d_ypass_body<R, N, E, CT, MODE>(P, W0, W1, W2, sc, tw);
+}
+
+// with the phi^4 channel (W3)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k3d_ypass_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+             C_t<R>* __restrict__ W3, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw) {
+  k3d_ypass_body<R, N, E, CT, MODE, true>(P, W0, W1, W2, sc, tw, W3);
+}
+
+// z forward pass: tile of CT kx columns at ky = blockIdx.y.
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
+__device__ __forceinline__ void k3d_zfwd_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ W0,
+                                              const C_t<R>* __restrict__ W1, C_t<R>* __restrict__ Nhat,
+                                              double* __restrict__ partG, const SavScal* __restrict__ sc,
+                                              const C_t<R>* __restrict__ tw, int target) {
   using C = C_t<R>;
+  static_assert(!G3 || MODE != Z3F_TO_STATE, "the phi^4 channel is carried by the modes that form N_hat");
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == Z3F_TO_STATE) ? 1 : 2;
@@ -175,7 +207,9 @@ k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>
       const C q1 = v[0][i], q2 = v[NF - 1][i];
       const R ktz = kderiv<R>(kz, N, pc.kfz);
       const R ux = q1.x + ktz * q2.x, uy = q1.y + ktz * q2.y;
-      const C nh = mk<C>(uy, -ux);  // -i (k~_x W_x + k~_y W_y + k~_z W_z)
+      // -i (k~_x W_x + k~_y W_y + k~_z W_z); G3: plus the transform of gamma3 phi*^3,
+      // whose mean is removed (N_hat_0 := 0)
+      const C nh = (G3 && off == 0) ? mk<C>(0, 0) : mk<C>(uy, -ux);
       Nhat[off] = nh;
       if (MODE == Z3F_NHAT) continue;
       const R K2 = sym_K2_3d<R>(kx, ky, kz, N, pc);
@@ -203,6 +237,23 @@ k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>
       }
     }
   }
+}
+
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k3d_zfwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
+         C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const SavScal* __restrict__ sc,
+         const C_t<R>* __restrict__ tw, int target) {
+  k3d_zfwd_body<R, N, E, CT, MODE>(P, S, W0, W1, Nhat, partG, sc, tw, target);
+}
+
+// with the phi^4 channel (N_hat_0 := 0)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k3d_zfwd_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
+            C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const SavScal* __restrict__ sc,
+            const C_t<R>* __restrict__ tw) {
+  k3d_zfwd_body<R, N, E, CT, MODE, true>(P, S, W0, W1, Nhat, partG, sc, tw, 0);
 }
 
 // One block: reduce the E_1 and gamma/eta/theta partial sums and solve the
@@ -330,15 +381,16 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
 // f(row 0) + i f(row 1). T lanes per pair.
 // part: 2 x gridDim.x accumulators (sum s^2, sum s).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int RP, int MODE>
-__global__ void __launch_bounds__(RP * (N / E))
-k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
-        double* __restrict__ part, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw,
-        double* __restrict__ real_io) {
+template <typename R, int N, int E, int RP, int MODE, bool G3 = false>
+__device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
+                                             C_t<R>* __restrict__ W2, double* __restrict__ part,
+                                             const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw,
+                                             double* __restrict__ real_io, C_t<R>* __restrict__ W3 = nullptr) {
   using C = C_t<R>;
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NS = (MODE == RW_NONLIN || MODE == RW_ENERGY) ? 3 : 1;
+  constexpr int NS = (MODE == RW_NONLIN || MODE == RW_ENERGY) ? (G3 ? 4 : 3) : 1;
+  static_assert(!G3 || MODE == RW_NONLIN || MODE == RW_ENERGY, "the phi^4 channel is carried by the nonlinear and energy modes");
   constexpr int NTH = RP * T;
   constexpr int NH = N / 2 + 1;
   constexpr int KH = (N / 2) / T;
@@ -396,14 +448,15 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
   } else {
     // Z_q = A_q + i B_q over the full x-spectrum, element k = lane + i T
     // straight into registers (k > N/2 from the Hermitian mirror N - k):
-    // q = 0/1: G_x + i G_y of row 0/1, q = 2: G_z(row 0) + i G_z(row 1)
+    // q = 0/1: G_x + i G_y of row 0/1, q = 2: G_z(row 0) + i G_z(row 1),
+    // q = 3 (G3): phi*(row 0) + i phi*(row 1)
     C v[NS][E];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-      const C* Aa = (q == 2) ? W2 : W0;
-      const C* Bb = (q == 2) ? W2 : W1;
+      const C* Aa = (q == 3) ? W3 : ((q == 2) ? W2 : W0);
+      const C* Bb = (q == 3) ? W3 : ((q == 2) ? W2 : W1);
       const size_t ra = row0 + (q == 1 ? 1 : 0);
-      const size_t rb = (q == 2) ? row0 + 1 : ra;
+      const size_t rb = (q >= 2) ? row0 + 1 : ra;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int k = lane + i * T;
@@ -422,10 +475,20 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
       const C g0 = v[0][i], g1 = v[1][i], gz = v[2][i];
       const R s0 = g0.x * g0.x + g0.y * g0.y + gz.x * gz.x;
       const R s1 = g1.x * g1.x + g1.y * g1.y + gz.y * gz.y;
-      acc[0] = RD::add(acc[0], s0 * s0);
-      acc[1] = RD::add(acc[1], s0);
-      acc[0] = RD::add(acc[0], s1 * s1);
-      acc[1] = RD::add(acc[1], s1);
+      if constexpr (G3) {  // (gamma3/beta) phi*^4 joins the sum of s^2 (E_1 takes it with beta/4)
+        const C ph = v[NS - 1][i];
+        const R q0 = ph.x * ph.x, q1 = ph.y * ph.y;
+        acc[0] = RD::add(acc[0], s0 * s0 + pc.g3b * (q0 * q0));
+        acc[1] = RD::add(acc[1], s0);
+        acc[0] = RD::add(acc[0], s1 * s1 + pc.g3b * (q1 * q1));
+        acc[1] = RD::add(acc[1], s1);
+        if (MODE == RW_NONLIN) v[NS - 1][i] = mk<C>(pc.g3 * q0 * ph.x, pc.g3 * q1 * ph.y);
+      } else {
+        acc[0] = RD::add(acc[0], s0 * s0);
+        acc[1] = RD::add(acc[1], s0);
+        acc[0] = RD::add(acc[0], s1 * s1);
+        acc[1] = RD::add(acc[1], s1);
+      }
       if (MODE == RW_NONLIN) {
         const R f0 = pc.beta * s0 - (R)2, f1 = pc.beta * s1 - (R)2;
         v[0][i] = mk<C>(f0 * g0.x, f0 * g0.y);
@@ -445,10 +508,10 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
       const R h = (R)0.5 * pc.invP;
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
-        C* Oa = (q == 2) ? W2 : W0;
-        C* Ob = (q == 2) ? W2 : W1;
+        C* Oa = (q == 3) ? W3 : ((q == 2) ? W2 : W0);
+        C* Ob = (q == 3) ? W3 : ((q == 2) ? W2 : W1);
         const size_t ra = row0 + (q == 1 ? 1 : 0);
-        const size_t rb = (q == 2) ? row0 + 1 : ra;
+        const size_t rb = (q >= 2) ? row0 + 1 : ra;
 #pragma unroll
         for (int i = 0; i < KH + 1; ++i) {
           if (i == KH && lane != 0) break;
@@ -467,6 +530,23 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
       ps[gridDim.x + blockIdx.x] = acc[1];
     }
   }
+}
+
+template <typename R, int N, int E, int RP, int MODE>
+__global__ void __launch_bounds__(RP * (N / E))
+k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+        double* __restrict__ part, const SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw,
+        double* __restrict__ real_io) {
+  k3d_row_body<R, N, E, RP, MODE>(P, W0, W1, W2, part, sc, tw, real_io);
+}
+
+// with the phi^4 channel (W3: phi* in, gamma3 phi*^3 out, both as x-spectra)
+template <typename R, int N, int E, int RP, int MODE>
+__global__ void __launch_bounds__(RP * (N / E))
+k3d_row_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
+           C_t<R>* __restrict__ W3, double* __restrict__ part, const SavScal* __restrict__ sc,
+           const C_t<R>* __restrict__ tw) {
+  k3d_row_body<R, N, E, RP, MODE, true>(P, W0, W1, W2, part, sc, tw, nullptr, W3);
 }
 
 // ---------------------------------------------------------------------------

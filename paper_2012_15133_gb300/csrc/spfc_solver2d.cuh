@@ -267,13 +267,13 @@ class Solver2D final : public SolverBase {
         return (e == cudaErrorMemoryAllocation) ? 2 : 3;
       }
       total_ += spec_bytes_;
-      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_STEP>, smem_col(3)));
-      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_GRAD>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_STEP>, smem_col(2)));
+      SPFC_CK(set_smem(k2d_col_inv_g3<R, N, E, CT, CI_GRAD>, smem_col(2)));
       SPFC_CK(set_smem(k2d_row_g3<R, N, E, RPC, RW_NONLIN>, 2 * smem_row()));
       SPFC_CK(set_smem(k2d_row_g3<R, N, E, RPC, RW_ENERGY>, 2 * smem_row()));
-      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF2>, smem_col(3)));
-      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF1>, smem_col(3)));
-      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_NHAT>, smem_col(3)));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF2>, smem_col(2)));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_BDF1>, smem_col(2)));
+      SPFC_CK(set_smem(k2d_col_fwd_g3<R, N, E, CT, CF_NHAT>, smem_col(2)));
     }
     P.g3 = g3;
     fill_float_params(&P);
@@ -441,9 +441,9 @@ class Solver2D final : public SolverBase {
   int launch_col_inv(int mode, int which) {
     if (g3_on() && (mode == CI_STEP || mode == CI_GRAD)) {
       if (mode == CI_STEP)
-        k2d_col_inv_g3<R, N, E, CT, CI_STEP><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
+        k2d_col_inv_g3<R, N, E, CT, CI_STEP><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
       else
-        k2d_col_inv_g3<R, N, E, CT, CI_GRAD><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
+        k2d_col_inv_g3<R, N, E, CT, CI_GRAD><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
       SPFC_CK(cudaGetLastError());
       return 0;
     }
@@ -490,11 +490,11 @@ class Solver2D final : public SolverBase {
   int launch_col_fwd(int mode, int target) {
     if (g3_on() && mode != CF_TO_STATE) {
       if (mode == CF_BDF2)
-        k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       else if (mode == CF_BDF1)
-        k2d_col_fwd_g3<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       else
-        k2d_col_fwd_g3<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(3), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       SPFC_CK(cudaGetLastError());
       return 0;
     }

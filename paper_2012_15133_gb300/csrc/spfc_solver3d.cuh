@@ -92,7 +92,8 @@ class Solver3D final : public SolverBase {
     if (g8_) cudaGraphExecDestroy(g8_);
     for (auto ev : evpool_) cudaEventDestroy(ev);
     if (cap_st_) cudaStreamDestroy(cap_st_);
-    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W_[2], real_, partE_, partG_, partN_, partS_, sc_, tw_};
+    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W_[2], W3_, real_, partE_, partG_, partN_, partS_, sc_,
+                    tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -142,6 +143,32 @@ class Solver3D final : public SolverBase {
 
   int set_stab(double A) override {
     P.stab = A;
+    fill_float_params(&P);
+    drop_graphs();
+    w_ready_ = false;
+    return 0;
+  }
+
+  // The phi^4 term's kernels carry a fourth work array (allocated when the
+  // term is first switched on); the step keeps its six kernels.
+  int set_gamma3(double g3) override {
+    if (g3 != 0.0 && !W3_) {
+      cudaError_t e = cudaMalloc((void**)&W3_, spec_bytes_);
+      if (e != cudaSuccess) {
+        W3_ = nullptr;
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return (e == cudaErrorMemoryAllocation) ? 2 : 3;
+      }
+      total_ += spec_bytes_;
+      SPFC_CK(set_smem(k3d_ypass_g3<R, N, E, CT, Y3_FWD>, smem_col(3)));
+      SPFC_CK(set_smem(k3d_ypass_g3<R, N, E, CT, Y3_INV>, smem_col(3)));
+      SPFC_CK(set_smem(k3d_zfwd_g3<R, N, E, CT, Z3F_BDF2>, smem_col(2)));
+      SPFC_CK(set_smem(k3d_zfwd_g3<R, N, E, CT, Z3F_BDF1>, smem_col(2)));
+      SPFC_CK(set_smem(k3d_zfwd_g3<R, N, E, CT, Z3F_NHAT>, smem_col(2)));
+      SPFC_CK(set_smem(k3d_row_g3<R, N, E, RP, RW_NONLIN>, smem_row(4)));
+      SPFC_CK(set_smem(k3d_row_g3<R, N, E, RP, RW_ENERGY>, smem_row(4)));
+    }
+    P.g3 = g3;
     fill_float_params(&P);
     drop_graphs();
     w_ready_ = false;
@@ -290,8 +317,18 @@ class Solver3D final : public SolverBase {
   static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * CTP * sizeof(C); }
   static constexpr size_t smem_row(int ns) { return (size_t)ns * RP * (sp_len(N) + 1) * sizeof(C); }
 
+  bool g3_on() const { return P.g3 != 0.0; }
+
   int ypass(int mode) {
     const dim3 g(GX, N);
+    if (g3_on() && (mode == Y3_FWD || mode == Y3_INV)) {
+      if (mode == Y3_FWD)
+        k3d_ypass_g3<R, N, E, CT, Y3_FWD><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], W3_, sc_, tw_);
+      else
+        k3d_ypass_g3<R, N, E, CT, Y3_INV><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], W3_, sc_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case Y3_FWD: k3d_ypass<R, N, E, CT, Y3_FWD><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
       case Y3_INV: k3d_ypass<R, N, E, CT, Y3_INV><<<g, CT * T, smem_col(3), st_>>>(P, W_[0], W_[1], W_[2], sc_, tw_); break;
@@ -305,6 +342,16 @@ class Solver3D final : public SolverBase {
   }
   int zfwd(int mode, int target) {
     const dim3 g(GX, N);
+    if (g3_on() && mode != Z3F_TO_STATE) {
+      if (mode == Z3F_BDF2)
+        k3d_zfwd_g3<R, N, E, CT, Z3F_BDF2><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_);
+      else if (mode == Z3F_BDF1)
+        k3d_zfwd_g3<R, N, E, CT, Z3F_BDF1><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_);
+      else
+        k3d_zfwd_g3<R, N, E, CT, Z3F_NHAT><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case Z3F_BDF2:
         k3d_zfwd<R, N, E, CT, Z3F_BDF2><<<g, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, sc_, tw_, target); break;
@@ -336,6 +383,14 @@ class Solver3D final : public SolverBase {
     return 0;
   }
   int row(int mode) {
+    if (g3_on() && (mode == RW_NONLIN || mode == RW_ENERGY)) {
+      if (mode == RW_NONLIN)
+        k3d_row_g3<R, N, E, RP, RW_NONLIN><<<GROW, RP * T, smem_row(4), st_>>>(P, W_[0], W_[1], W_[2], W3_, partE_, sc_, tw_);
+      else
+        k3d_row_g3<R, N, E, RP, RW_ENERGY><<<GROW, RP * T, smem_row(4), st_>>>(P, W_[0], W_[1], W_[2], W3_, partE_, sc_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     switch (mode) {
       case RW_NONLIN:
         k3d_row<R, N, E, RP, RW_NONLIN><<<GROW, RP * T, smem_row(3), st_>>>(P, W_[0], W_[1], W_[2], partE_, sc_, tw_, real_); break;
@@ -464,6 +519,7 @@ class Solver3D final : public SolverBase {
   Slots<R> S_{{nullptr, nullptr}};
   C* Nhat_ = nullptr;
   C* W_[3] = {nullptr, nullptr, nullptr};
+  C* W3_ = nullptr;  // fourth work array of the phi^4 term (allocated on demand)
   double* real_ = nullptr;
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
   SavScal* sc_ = nullptr;

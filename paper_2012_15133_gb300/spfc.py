@@ -256,7 +256,7 @@ class Solver:
 
     def set_gamma3(self, gamma3):
         """The optional phi^4 term: E_1 gains gamma3/4 ||phi||_4^4 and N gains
-        gamma3 phi^3 with its mean removed (2D single runs; 0: SPFC)."""
+        gamma3 phi^3 with its mean removed (0: SPFC)."""
         self._check(self._lib.spfc_set_gamma3(self._h, float(gamma3)))
         self.gamma3 = float(gamma3)
         return self

@@ -138,10 +138,43 @@ def test_gamma3_zero_is_the_plain_path_and_checkpoints_record_it(tmp_path):
         b.set_gamma3(float("nan"))
 
 
-def test_gamma3_is_refused_by_3d_handles():
-    from paper_2012_15133_gb300 import Solver, SPFCError
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gamma3_3d_steps_starts_and_energies(precision):
+    """3D on a box with three different side lengths: per step from an
+    identical state, then the BDF1 start with the term set before init, E_N and
+    the modified energy."""
+    from paper_2012_15133_gb300 import Solver
+    n, L = 16, (8.0, 6.0, 7.0)
+    phi0 = noisy_field((n, n, n), 0.4, 0.1, 33)
+    args = (3, n, L, 0.2, 1.0, 0.02)
+    o = Oracle(*args, gamma3=G3).start(phi0, "bdf1").step(1)
+    plain = Oracle(*args).set_state(o.phi, o.phi_prev, o.r, o.r_prev)
+    s = Solver(*args, precision).set_gamma3(G3).set_state(o.phi, o.phi_prev, o.r, o.r_prev)
+    phi_start = o.phi.copy()
+    for _ in range(3):
+        o.step()
+        plain.step()
+        s.step(1)
+        assert rel_l2(s.get_field(0), o.phi) < TOL[precision]
+        assert abs(s.sav_scalars()["r"] - o.r) / o.r < TOL[precision]
+        assert abs(s.sav_scalars()["E1"] - o.last_info["E1"]) / o.last_info["E1"] < TOL[precision]
+    assert rel_l2(o.phi - phi_start, plain.phi - phi_start) > 0.02  # about 5 % here
+    o2 = Oracle(*args, gamma3=G3).start(phi0, "bdf1")
+    s2 = Solver(*args, precision).set_gamma3(G3).init(phi0, "bdf1")
+    assert rel_l2(s2.get_field(0), o2.phi) < TOL[precision]
+    o2.step(2)
+    s2.step(2)
+    assert rel_l2(s2.get_field(0), o2.phi) < TOL[precision]
+    e_orig, e_mod, _ = s2.energy()
+    assert abs(e_orig - o2.original_energy()) / abs(o2.original_energy()) < TOL[precision]
+    assert abs(e_mod - o2.modified_energy()) / abs(o2.modified_energy()) < TOL[precision]
+
+
+def test_gamma3_3d_zero_is_the_plain_path():
+    from paper_2012_15133_gb300 import Solver
     c3 = cube_3d_case(16)
-    s3 = Solver(3, 16, c3["L"], c3["eps"], c3["beta"], c3["dt"], "fp64")
-    s3.set_gamma3(0.0)
-    with pytest.raises(SPFCError):
-        s3.set_gamma3(G3)
+    args = (3, 16, c3["L"], c3["eps"], c3["beta"], c3["dt"], "fp64")
+    a, b = Solver(*args), Solver(*args)
+    a.init(c3["phi0"], "bdf1").step(3)
+    b.set_gamma3(G3).set_gamma3(0.0).init(c3["phi0"], "bdf1").step(3)
+    assert np.array_equal(a.get_field(0), b.get_field(0))
