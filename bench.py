@@ -203,14 +203,19 @@ def measure_ensemble(steps, warmup, precision, peak, rank=0, world=1, dist=None)
             "status_ok": ok}
 
 
-def measure_cube(steps, warmup, precision, peak, flush):
+def measure_cube(steps, warmup, precision, peak, flush, gamma3=0.0):
     """The 3D workload: 128^3 on [0,64]^3, eps 0.2, beta 1, dt 0.02,
-    phi0 = 0.15 + 0.05 U (seed 2); L2 flushed before each timed step."""
+    phi0 = 0.15 + 0.05 U (seed 2); L2 flushed before each timed step.
+    gamma3 > 0 adds the phi^4 term, with the same 27 half-spectrum passes per
+    step (phi* replaces W_x between y-inv and the row pass, and the row pass
+    folds gamma3 phi*^3 into W_x)."""
     import torch
     from paper_2012_15133_gb300 import Solver
     from seeded_inputs import cube_3d_case
     c = cube_3d_case(128)
     s = Solver(3, 128, c["L"], c["eps"], c["beta"], c["dt"], precision)
+    if gamma3:
+        s.set_gamma3(gamma3)
     s.init(c["phi0"], "bdf1")
     s.step(max(3, warmup))
     st = torch.cuda.current_stream()
@@ -224,21 +229,25 @@ def measure_cube(steps, warmup, precision, peak, flush):
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     s.sync()
     csize = 8 if precision == "fp32" else 16
-    bytes_step = 27 * 128 * 128 * 65 * csize
+    passes = 27
+    bytes_step = passes * 128 * 128 * 65 * csize
     P = 128 ** 3
-    return {"workload": "3D SPFC 128^3, L=64, eps=0.2, dt=0.02, phi0=0.15+0.05U seed 2", "value": P / (ms * 1e-3) / 1e6,
+    work = "3D SPFC 128^3, L=64, eps=0.2, dt=0.02, phi0=0.15+0.05U seed 2"
+    if gamma3:
+        work += f", gamma3={gamma3} phi^4 term"
+    return {"workload": work, "value": P / (ms * 1e-3) / 1e6,
             "unit": UNIT, "ms_per_step": ms, "steps": steps, "l2": "flushed before every timed step",
             "roofline": {"bound": "hbm", "achieved": bytes_step / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": bytes_step / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_step": bytes_step,
-                         "note": "step level: 27 half-spectrum passes (6 kernels)"}}
+                         "note": f"step level: {passes} half-spectrum passes (6 kernels)"}}
 
 
 def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):
     """The 512^2 crystallisation workload with the optional phi^4 term
     (gamma3 = 1): the lazy three-pass step (column inverse with the pending
     update, row pass, column forward with the scalar solve); L2 flushed before
-    each timed step. Algorithmic bytes: 19 half-spectrum passes per step
-    (column inverse: 3 reads and 4 writes; row: 3 and 3; column forward: 5
+    each timed step. Algorithmic bytes: 15 half-spectrum passes per step
+    (column inverse: 3 reads and 3 writes; row: 2 and 2; column forward: 4
     reads and the N_hat write)."""
     import torch
     from paper_2012_15133_gb300 import Solver
@@ -265,7 +274,7 @@ def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):
     s.set_timing(False)
     s.sync()
     csize = 8 if precision == "fp32" else 16
-    bytes_step = 19 * N_GRID * (N_GRID // 2 + 1) * csize
+    bytes_step = 15 * N_GRID * (N_GRID // 2 + 1) * csize
     P = N_GRID * N_GRID
     return {"workload": f"2D SPFC + gamma3 phi^4 term, {N_GRID}^2, L=256, eps=0.25, dt=0.05, gamma3={gamma3}, "
                         "phi0=0.2+0.02U seed 1",
@@ -274,7 +283,7 @@ def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):
             "kernels": {k: {"launches": v[0], "avg_us": v[1] / v[0] * 1e3} for k, v in kt.items()},
             "roofline": {"bound": "hbm", "achieved": bytes_step / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": bytes_step / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes_per_step": bytes_step,
-                         "note": "step level: 19 half-spectrum passes (3 kernels)"}}
+                         "note": "step level: 15 half-spectrum passes (3 kernels)"}}
 
 
 def measure_patterns(precision="fp32", n=256):
@@ -502,6 +511,8 @@ def run_ours(args):
                                               dist)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
         extras["gamma3"] = measure_gamma3(min(args.steps, 200), args.warmup, args.precision, peak, flush)
+        extras["cube3d_gamma3"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush,
+                                               gamma3=1.0)
         if rank == 0:
             extras["patterns"] = measure_patterns()
         if not args.no_surrogate and rank == 0:
@@ -544,7 +555,8 @@ def run_driver(args):
     """Profiling driver (for ncu): init, then K steps of the workload with the
     kernels launched one by one (single runs) or graph-replayed (ensemble);
     no timing, no flush. --workload crystal (2D, --n), gamma3 (the same with
-    the phi^4 term, gamma3 = 1), cube (3D 128^3) or ensemble (256 runs)."""
+    the phi^4 term, gamma3 = 1), cube (3D 128^3), cube_gamma3 (the same with
+    gamma3 = 1) or ensemble (256 runs)."""
     import torch
     from paper_2012_15133_gb300 import Solver, Batch, build
     build.build()
@@ -572,15 +584,17 @@ def run_driver(args):
         b.sync()
         print(json.dumps({"driver": True, "workload": "ensemble", "steps": args.steps}))
         return 0
-    if args.workload == "cube":
+    if args.workload in ("cube", "cube_gamma3"):
         from seeded_inputs import cube_3d_case
         c = cube_3d_case(128)
         s = Solver(3, 128, c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+        if args.workload == "cube_gamma3":
+            s.set_gamma3(1.0)
         s.init(c["phi0"], "bdf1")
         s.set_timing(True)
         s.step(args.steps)
         s.sync()
-        print(json.dumps({"driver": True, "workload": "cube", "kernels": s.kernel_times()}))
+        print(json.dumps({"driver": True, "workload": args.workload, "kernels": s.kernel_times()}))
         return 0
     from seeded_inputs import crystal_2d_case
     c = crystal_2d_case(args.n)
@@ -613,7 +627,7 @@ def main():
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
-    ap.add_argument("--workload", default="crystal", choices=["crystal", "gamma3", "cube", "ensemble", "surrogate"],
+    ap.add_argument("--workload", default="crystal", choices=["crystal", "gamma3", "cube", "cube_gamma3", "ensemble", "surrogate"],
                     help="workload of --ncu-driver")
     args = ap.parse_args()
     if args.ncu_driver:

@@ -121,12 +121,13 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha, R s
 // rows y = lane + i T (i < E) of column kx0 + c, for every field of the pass
 // (one warp then reads 32/CT rows of CT adjacent columns). The column FFTs
 // keep their first and last stages in registers (fft_regs_multi).
-// G3 (the optional phi^4 term): the passes carry a third field with no third
-// transform, since k~_x is constant along a column. The inverse pass
-// transforms phi* and i k~_y phi* and forms G_x = i k~_x Y^-1 phi* in registers,
-// storing Y^-1 phi* in W2 as well. The forward pass transforms k~_x W_x + i W2
-// (W2 then holds the x-spectrum of gamma3 phi*^3) and W_y, so that
-// -i (first + k~_y second) is N_hat with the transform of gamma3 phi*^3 added.
+// G3 (the optional phi^4 term): no third transform and no third array across
+// the row pass, since k~_x is constant along a column and known in the row
+// pass. The inverse pass transforms phi* and i k~_y phi* and stores Y^-1 phi*
+// (W2) and G_y (W1); the row pass forms G_x = i k~_x Y^-1 phi* itself and
+// returns W0 = k~_x W_x + i F_x(gamma3 phi*^3) and W1 = W_y; the forward pass
+// transforms both, so that -i (Y W0 + k~_y Y W1) is N_hat with the transform of
+// gamma3 phi*^3 added.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
@@ -227,17 +228,11 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
   }
   fft_regs_multi<C, N, E, true, NF, true>(g, sm + c, SEQ * CTP, CTP, lane, tw);
   if (col) {
-    const R ktx = kderiv<R>(kx, N, pc.kfx);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const size_t off = (size_t)(lane + i * T) * NH + kx;
-      if constexpr (G3) {
-        const C f = g[0][i];
-        W0[off] = mk<C>(-ktx * f.y, ktx * f.x);  // G_x = i k~_x Y^-1 phi*
-        W2[off] = f;                              // Y^-1 phi*
-      } else {
-        W0[off] = g[0][i];
-      }
+      if constexpr (G3) W2[off] = g[0][i];  // Y^-1 phi* (the row pass forms G_x from it)
+      else W0[off] = g[0][i];
       if (NF == 2) W1[off] = g[NF - 1][i];
     }
   }
@@ -262,10 +257,11 @@ k2d_col_inv_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<
 // ---------------------------------------------------------------------------
 // Row pass. Grid: N/RPC blocks, RPC rows each, T = N/E lanes per row.
 // part: 2 x gridDim.x doubles: sum s^2 and sum s per block (without h^d).
-// G3: each row also inverse-transforms phi* (from W2), adds (gamma3/beta) phi*^4
-// to the sum of s^2 (E_1 takes that sum with beta/4) and, for the step,
-// forward-transforms gamma3 phi*^3 into W2; shared memory holds two sequences
-// per row.
+// G3: each row reads Y^-1 phi* (W2) and G_y (W1), forms G_x = i k~_x Y^-1 phi*,
+// also inverse-transforms phi*, adds (gamma3/beta) phi*^4 to the sum of s^2
+// (E_1 takes that sum with beta/4) and, for the step, forward-transforms
+// gamma3 phi*^3 and writes W0 = k~_x W_x + i F_x(gamma3 phi*^3), W1 = W_y;
+// shared memory holds two sequences per row.
 // ---------------------------------------------------------------------------
 template <typename R, int N, int E, int RPC, int MODE, bool G3 = false>
 __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
@@ -322,21 +318,23 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
   } else if constexpr (G3) {
-    // sequence 0: Z = G_x + i G_y as below; sequence 1: the x-spectrum of phi*
-    // (Hermitian, so its inverse is real)
+    // sequence 0: Z = G_x + i G_y as below, G_x = i k~_x Y^-1 phi*; sequence 1:
+    // the x-spectrum of phi* (Hermitian, so its inverse is real)
+    const PC<R> pc(P);
     C v[2][E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = lane + i * T;
       const bool direct = k <= N / 2;
-      const size_t off = roff + (direct ? k : N - k);
-      const C a = W0[off], b = W1[off], f = W2[off];
+      const int m = direct ? k : N - k;
+      const C f = W2[roff + m], b = W1[roff + m];
+      const R ktm = kderiv<R>(m, N, pc.kfx);
+      const C a = mk<C>(-ktm * f.y, ktm * f.x);
       v[0][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
       v[1][i] = direct ? f : cconj(f);
     }
     fft_regs_multi<C, N, E, true, 2, false>(v, z, SEQ + 1, 1, lane, tw);
     typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
-    const PC<R> pc(P);
     const R beta = pc.beta, g3 = pc.g3, g3b = pc.g3b;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -364,9 +362,10 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
         const int kk = lane + i * T;
         const C zk = v[0][i], zm = cconj(z[sp((N - kk) & (N - 1))]);
         const C sx = cadd(zk, zm), dy = csub(zk, zm);
-        W0[roff + kk] = cscale(sx, half);
+        const C f3 = cscale(v[1][i], pc.invP);  // x-spectrum of gamma3 phi*^3, k <= N/2
+        const R ktk = kderiv<R>(kk, N, pc.kfx);
+        W0[roff + kk] = mk<C>(ktk * sx.x * half - f3.y, ktk * sx.y * half + f3.x);  // k~_x W_x + i f3
         W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);
-        W2[roff + kk] = cscale(v[1][i], pc.invP);  // x-spectrum of gamma3 phi*^3, k <= N/2
       }
     }
     typename RD::acc t21[2] = {acc2, acc1};
@@ -444,7 +443,7 @@ k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double
   k2d_row_body<R, N, E, RPC, MODE>(P, W0, W1, part, sc, tw, real_io);
 }
 
-// with the phi^4 channel (W2: y-inverse of phi* in, x-spectrum of gamma3 phi*^3 out)
+// with the phi^4 channel (W2: y-inverse of phi* in; W0 out: k~_x W_x + i F_x(gamma3 phi*^3))
 template <typename R, int N, int E, int RPC, int MODE>
 __global__ void __launch_bounds__(RPC * (N / E))
 k2d_row_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
@@ -611,8 +610,7 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
                                                  const C_t<R>* __restrict__ W1, C_t<R>* __restrict__ Nhat,
                                                  double* __restrict__ partG, const double* __restrict__ partE,
                                                  int nE, SavScal* __restrict__ sc, unsigned* __restrict__ counter,
-                                                 const C_t<R>* __restrict__ tw, int target,
-                                                 const C_t<R>* __restrict__ W2 = nullptr) {
+                                                 const C_t<R>* __restrict__ tw, int target) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
@@ -641,13 +639,8 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const size_t off = (size_t)(lane + i * T) * NH + kx;
-    v[0][i] = col ? W0[off] : mk<C>(0, 0);
+    v[0][i] = col ? W0[off] : mk<C>(0, 0);  // G3: k~_x W_x + i F_x(gamma3 phi*^3)
     if (NF == 2) v[NF - 1][i] = col ? W1[off] : mk<C>(0, 0);
-    if constexpr (G3) {  // k~_x W_x + i W2: one sequence for both
-      const R ktx = kderiv<R>(kx, N, PC<R>(P).kfx);
-      const C f = col ? W2[off] : mk<C>(0, 0), wx = v[0][i];
-      v[0][i] = mk<C>(ktx * wx.x - f.y, ktx * wx.y + f.x);
-    }
   }
 
   if constexpr (MODE == CF_TO_STATE) {
@@ -766,14 +759,13 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
   k2d_col_fwd_body<R, N, E, CT, MODE>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, target);
 }
 
-// with the phi^4 channel (W2: x-spectrum of gamma3 phi*^3)
+// with the phi^4 channel (W0 holds k~_x W_x + i F_x(gamma3 phi*^3))
 template <typename R, int N, int E, int CT, int MODE>
 __global__ void __launch_bounds__(CT * (N / E))
 k2d_col_fwd_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t<R>* __restrict__ W1,
-               const C_t<R>* __restrict__ W2, C_t<R>* __restrict__ Nhat, double* __restrict__ partG,
-               const double* __restrict__ partE, int nE, SavScal* __restrict__ sc, unsigned* __restrict__ counter,
-               const C_t<R>* __restrict__ tw) {
-  k2d_col_fwd_body<R, N, E, CT, MODE, true>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, 0, W2);
+               C_t<R>* __restrict__ Nhat, double* __restrict__ partG, const double* __restrict__ partE, int nE,
+               SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw) {
+  k2d_col_fwd_body<R, N, E, CT, MODE, true>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,13 +17,14 @@
 //            2 phi^{n+1} - phi^n, inverse DFT in z of phi* and of i k~_z phi*;
 //   y-inv  : inverse DFT in y of i k~_y F, F and G_z; W_x = i k~_x (.) of F's.
 //
-// The optional phi^4 term (G3 variants) needs no further z- or y-transform:
-// y-inv also stores Y^-1 F (the x-spectrum of phi*) in W3; the row pass
-// carries phi*(row 0) + i phi*(row 1) as a fourth sequence, adds
-// (gamma3/beta) phi*^4 to the sum of s^2 and returns gamma3 phi*^3 in W3; y-fwd
-// transforms k~_x W_x + i W3 as one sequence (k~_x is constant along y), so
-// that Q1 carries i Y(W3) and -i (Q1 + k~_z Q2) gains the transform of
-// gamma3 phi*^3; z-fwd removes its mean (N_hat_0 := 0).
+// The optional phi^4 term (G3 variants) needs no further z- or y-transform
+// and no further array pass: y-inv stores Y^-1 F (phi* as an x-spectrum) in W3
+// instead of W_x = i k~_x Y^-1 F; the row pass forms W_x from it, carries
+// phi*(row 0) + i phi*(row 1) as a fourth sequence, adds (gamma3/beta) phi*^4
+// to the sum of s^2 and writes W0 = k~_x W_x + i F_x(gamma3 phi*^3) (k~_x is
+// known there and constant along y and z); y-fwd then forms Q1 = Y W0 +
+// k~_y Y W_y, so that -i (Q1 + k~_z Q2) gains the transform of gamma3 phi*^3;
+// z-fwd removes its mean (N_hat_0 := 0).
 #pragma once
 
 #include "spfc_kernels2d.cuh"
@@ -88,11 +89,6 @@ __device__ __forceinline__ void k3d_ypass_body(const Params& P, C_t<R>* __restri
       v[0][i] = W0[off];
       v[NF - 2][i] = W1[off];
       v[NF - 1][i] = W2[off];
-      if constexpr (G3) {  // k~_x W_x + i W3 as one sequence
-        const R ktx = kderiv<R>(kx, N, pc.kfx);
-        const C f = W3[off], wx = v[0][i];
-        v[0][i] = mk<C>(ktx * wx.x - f.y, ktx * wx.y + f.x);
-      }
     } else if constexpr (MODE == Y3_INV) {
       const C F = W0[off];
       const R kty = kderiv<R>(y, N, pc.kfy);
@@ -112,16 +108,16 @@ __device__ __forceinline__ void k3d_ypass_body(const Params& P, C_t<R>* __restri
     if constexpr (MODE == Y3_FWD) {
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(y, N, pc.kfy);
       const C a = v[0][i], b = v[NF - 2][i];
-      if constexpr (G3) W0[off] = mk<C>(a.x + kty * b.x, a.y + kty * b.y);  // Q1 + i Y(W3)
+      if constexpr (G3) W0[off] = mk<C>(a.x + kty * b.x, a.y + kty * b.y);  // W0 = k~_x W_x + i F_x(gamma3 phi*^3)
       else W0[off] = mk<C>(ktx * a.x + kty * b.x, ktx * a.y + kty * b.y);  // Q1
       W1[off] = v[NF - 1][i];                                              // Q2
     } else if constexpr (MODE == Y3_INV) {
       const R ktx = kderiv<R>(kx, N, pc.kfx);
       const C Fy = v[NF - 2][i];
-      W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);  // W_x = i k~_x Y^-1 F
+      if constexpr (G3) W3[off] = Fy;             // Y^-1 F: phi* as an x-spectrum (the row pass forms W_x)
+      else W0[off] = mk<C>(-ktx * Fy.y, ktx * Fy.x);  // W_x = i k~_x Y^-1 F
       W1[off] = v[0][i];                          // W_y
       W2[off] = v[NF - 1][i];                     // W_z
-      if constexpr (G3) W3[off] = Fy;             // Y^-1 F: phi* along x as a spectrum
     } else {
       W0[off] = v[0][i];
     }
@@ -135,7 +131,7 @@ k3d_ypass(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<
   k3d_ypass_body<R, N, E, CT, MODE>(P, W0, W1, W2, sc, tw);
 }
 
-// with the phi^4 channel (W3)
+// with the phi^4 channel (Y3_INV: W3 instead of W0; Y3_FWD: W0 with k~_x folded in)
 template <typename R, int N, int E, int CT, int MODE>
 __global__ void __launch_bounds__(CT * (N / E))
 k3d_ypass_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,
@@ -449,7 +445,8 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
     // Z_q = A_q + i B_q over the full x-spectrum, element k = lane + i T
     // straight into registers (k > N/2 from the Hermitian mirror N - k):
     // q = 0/1: G_x + i G_y of row 0/1, q = 2: G_z(row 0) + i G_z(row 1),
-    // q = 3 (G3): phi*(row 0) + i phi*(row 1)
+    // q = 3 (G3): phi*(row 0) + i phi*(row 1); G3 forms G_x = i k~_x phi* from W3
+    const PC<R> pc(P);
     C v[NS][E];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
@@ -462,14 +459,21 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
         const int k = lane + i * T;
         const bool direct = k <= N / 2;
         const int m = direct ? k : N - k;
-        const C a = Aa[ra * NH + m], b = Bb[rb * NH + m];
+        C a;
+        if (G3 && q < 2) {
+          const C f = W3[ra * NH + m];
+          const R ktm = kderiv<R>(m, N, pc.kfx);
+          a = mk<C>(-ktm * f.y, ktm * f.x);
+        } else {
+          a = Aa[ra * NH + m];
+        }
+        const C b = Bb[rb * NH + m];
         v[q][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
       }
     }
     fft_regs_multi<C, N, E, true, NS, false>(v, z, SEQ + 1, 1, lane, tw);
     // pointwise on x = lane + i T for both rows of the pair
     typename RD::acc acc[2] = {RD::zero(), RD::zero()};
-    const PC<R> pc(P);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const C g0 = v[0][i], g1 = v[1][i], gz = v[2][i];
@@ -506,20 +510,45 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
         for (int i = 0; i < E; ++i) z[q * (SEQ + 1) + sp(lane + i * T)] = v[q][i];
       fft_sync<N, E>();
       const R h = (R)0.5 * pc.invP;
-#pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        C* Oa = (q == 3) ? W3 : ((q == 2) ? W2 : W0);
-        C* Ob = (q == 3) ? W3 : ((q == 2) ? W2 : W1);
-        const size_t ra = row0 + (q == 1 ? 1 : 0);
-        const size_t rb = (q >= 2) ? row0 + 1 : ra;
+      if constexpr (G3) {
+        // W0 = k~_x W_x + i F_x(gamma3 phi*^3) for both rows, W1 = W_y, W2 = W_z
 #pragma unroll
         for (int i = 0; i < KH + 1; ++i) {
           if (i == KH && lane != 0) break;
           const int k = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
-          const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + sp((N - k) & (N - 1))]);
-          const C sx = cadd(zk, zm), dy = csub(zk, zm);
-          Oa[ra * NH + k] = cscale(sx, h);
-          Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);
+          const int km = sp((N - k) & (N - 1));
+          C sx[NS], dy[NS];
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + km]);
+            sx[q] = cadd(zk, zm);
+            dy[q] = csub(zk, zm);
+          }
+          const R ktk = kderiv<R>(k, N, pc.kfx);
+          const C f0 = cscale(sx[3], h), f1 = mk<C>(dy[3].y * h, -dy[3].x * h);  // gamma3 phi*^3 of rows 0, 1
+          W0[row0 * NH + k] = mk<C>(ktk * sx[0].x * h - f0.y, ktk * sx[0].y * h + f0.x);
+          W1[row0 * NH + k] = mk<C>(dy[0].y * h, -dy[0].x * h);
+          W0[(row0 + 1) * NH + k] = mk<C>(ktk * sx[1].x * h - f1.y, ktk * sx[1].y * h + f1.x);
+          W1[(row0 + 1) * NH + k] = mk<C>(dy[1].y * h, -dy[1].x * h);
+          W2[row0 * NH + k] = cscale(sx[2], h);
+          W2[(row0 + 1) * NH + k] = mk<C>(dy[2].y * h, -dy[2].x * h);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          C* Oa = (q == 2) ? W2 : W0;
+          C* Ob = (q == 2) ? W2 : W1;
+          const size_t ra = row0 + (q == 1 ? 1 : 0);
+          const size_t rb = (q == 2) ? row0 + 1 : ra;
+#pragma unroll
+          for (int i = 0; i < KH + 1; ++i) {
+            if (i == KH && lane != 0) break;
+            const int k = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
+            const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + sp((N - k) & (N - 1))]);
+            const C sx = cadd(zk, zm), dy = csub(zk, zm);
+            Oa[ra * NH + k] = cscale(sx, h);
+            Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);
+          }
         }
       }
     }
@@ -540,7 +569,7 @@ k3d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>
   k3d_row_body<R, N, E, RP, MODE>(P, W0, W1, W2, part, sc, tw, real_io);
 }
 
-// with the phi^4 channel (W3: phi* in, gamma3 phi*^3 out, both as x-spectra)
+// with the phi^4 channel (W3: phi* as an x-spectrum in; W0 out: k~_x W_x + i F_x(gamma3 phi*^3))
 template <typename R, int N, int E, int RP, int MODE>
 __global__ void __launch_bounds__(RP * (N / E))
 k3d_row_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t<R>* __restrict__ W2,

@@ -490,11 +490,11 @@ class Solver2D final : public SolverBase {
   int launch_col_fwd(int mode, int target) {
     if (g3_on() && mode != CF_TO_STATE) {
       if (mode == CF_BDF2)
-        k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       else if (mode == CF_BDF1)
-        k2d_col_fwd_g3<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       else
-        k2d_col_fwd_g3<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], W2_, Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+        k2d_col_fwd_g3<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
       SPFC_CK(cudaGetLastError());
       return 0;
     }
