@@ -399,6 +399,13 @@ template <typename R> __device__ __forceinline__ typename Red<R>::acc warp_red(t
   return v;
 }
 
+// Smallest power of two >= nw (nw >= 1). In the second stage of a block
+// reduction only lanes < nw hold values; an xor-shuffle level o >= this bound
+// pairs every lane below it with a zero, and adding an exact zero leaves a
+// (normalised) accumulator unchanged, so those levels are skipped with the
+// same result.
+__device__ __forceinline__ int pow2_ceil(int nw) { return 1 << (32 - __clz(nw - 1)); }
+
 // Block reduction of accumulators (fixed order); result valid in thread 0.
 template <typename R>
 __device__ __forceinline__ typename Red<R>::acc block_red(typename Red<R>::acc v, typename Red<R>::acc* scratch) {
@@ -410,7 +417,10 @@ __device__ __forceinline__ typename Red<R>::acc block_red(typename Red<R>::acc v
   typename Red<R>::acc t = Red<R>::zero();
   if (wid == 0) {
     t = (lane < nw) ? scratch[lane] : Red<R>::zero();
-    t = warp_red<R>(t);
+    const int p2 = pow2_ceil(nw);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      if (o < p2) t = Red<R>::add2(t, Red<R>::shfl(t, o));
   }
   return t;
 }
@@ -429,8 +439,15 @@ __device__ __forceinline__ void block_red_multi(typename Red<R>::acc* v, typenam
   }
   __syncthreads();
   if (wid == 0) {
+    const int p2 = pow2_ceil(nw);
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = warp_red<R>((lane < nw) ? scratch[k][lane] : Red<R>::zero());
+    for (int k = 0; k < K; ++k) v[k] = (lane < nw) ? scratch[k][lane] : Red<R>::zero();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      if (o >= p2) continue;
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = Red<R>::add2(v[k], Red<R>::shfl(v[k], o));
+    }
   }
 }
 
@@ -469,13 +486,21 @@ __device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* c
   int nmax = 0;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) nmax = n[q] > nmax ? n[q] : nmax;
-  for (int base = 0; base < nmax; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    typename RD::store v[NQ];
+  // two strides of loads in flight per round (the same per-thread order of
+  // additions), so that a grid of up to 2 x blockDim.x blocks needs one L2
+  // round trip, not two
+  for (int base = 0; base < nmax; base += 2 * blockDim.x) {
+    typename RD::store v[2][NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = (i < n[q]) ? __ldcg(arr[q] + i) : RD::zero();
+    for (int u = 0; u < 2; ++u) {
+      const int i = base + u * blockDim.x + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], v[q]);
+      for (int q = 0; q < NQ; ++q) v[u][q] = (i < n[q]) ? __ldcg(arr[q] + i) : RD::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], v[u][q]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -492,8 +517,10 @@ __device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* c
   if (wid == 0) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) a[q] = (lane < nw) ? scratch[q][lane] : RD::zero();
+    const int p2 = pow2_ceil(nw);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+      if (o >= p2) continue;
 #pragma unroll
       for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], RD::shfl(a[q], o));
     }

@@ -828,6 +828,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
 
   // ---- A: the W columns and the state of this thread's rows ky = lane + i T
   C g[2][E], vn[E], vo[E], nh[E];
+  R ia[E];  // A^{-1} of each row, kept for the update (the same rounded value)
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     g[0][i] = g[1][i] = vn[i] = vo[i] = mk<C>(0, 0);
@@ -860,6 +861,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   for (int i = 0; i < E; ++i) {
     const int ky = lane + i * T;
     nh[i] = mk<C>(0, 0);
+    ia[i] = (R)0;
     if (!col) continue;
     const C wx = g[0][i], wy = g[1][i];
     const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
@@ -867,6 +869,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
     nh[i] = mk<C>(uy, -ux);  // N_hat = -i (k~_x W_x + k~_y W_y)
     const R K2 = sym_K2<R>(kx, ky, N, pc);
     const R invA = sym_invA<R>(K2, c0, pc);
+    ia[i] = invA;
     C v;
     if (BDF1) v = vn[i];
     else v = mk<C>((R)2 * vn[i].x - (R)0.5 * vo[i].x, (R)2 * vn[i].y - (R)0.5 * vo[i].y);
@@ -940,8 +943,8 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
         nw = mk<C>((R)z, (R)0);
       } else {
         const R K2 = sym_K2<R>(kx, ky, N, pc);
-        if (BDF1) nw = bdf1_update<C, R>(cur, nh[i], K2, sym_invA<R>(K2, (R)1, pc), al, rn_mul(pc.sdt, K2));
-        else nw = bdf2_update<C, R>(cur, vo[i], nh[i], K2, sym_invA<R>(K2, (R)1.5, pc), al, rn_mul(pc.sdt, K2));
+        if (BDF1) nw = bdf1_update<C, R>(cur, nh[i], K2, ia[i], al, rn_mul(pc.sdt, K2));
+        else nw = bdf2_update<C, R>(cur, vo[i], nh[i], K2, ia[i], al, rn_mul(pc.sdt, K2));
       }
       sold[off] = nw;  // phi^{n+1} over phi^{n-1}
       const C ph = mk<C>((R)2 * nw.x - cur.x, (R)2 * nw.y - cur.y);
