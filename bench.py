@@ -485,7 +485,7 @@ def run_ours(args):
     # DRAM bytes (read + write) per launch of each kernel from the committed ncu
     # capture of the 512^2 step kernels (ncu --set full, cold caches); set to None whenever the
     # kernel changes after the capture
-    traffic_ncu = {("fp32", "col_fused"): 4294400}
+    traffic_ncu = {("fp32", "col_fused"): 4294400, ("fp32", "row"): 2132224}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,
