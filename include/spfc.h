@@ -250,6 +250,49 @@ int spfc_fno_loss_grad(spfc_fno_t f, int batch, const float* phi_n, const float*
 int spfc_fno_adam_step(spfc_fno_t f, float lr, float beta1, float beta2, float epsilon, float weight_decay);
 void spfc_fno_destroy(spfc_fno_t f);
 const char* spfc_fno_last_error(spfc_fno_t f);
+/* Weight file: magic "SPFCFNO1", int32 {n, width, modes1, modes2, layers,
+ * proj}, int64 parameter count, then the float32 parameters in the order of
+ * spfc_fno_set_params. spfc_fno_load requires a network of the same shape
+ * (SPFC_EINVAL otherwise, the weights unchanged) and resets Adam's moments
+ * as spfc_fno_set_params does. */
+int spfc_fno_save(spfc_fno_t f, const char* path);
+int spfc_fno_load(spfc_fno_t f, const char* path);
+
+/* The surrogate's jump-with-fallback loop, `jumps` rounds over `nruns` runs.
+ * The paper has no counterpart: the network is an accelerator of the SAV
+ * scheme, which stays its fallback and its judge. Each round:
+ *  1. one call of the network predicts phi^{n+K} of every run from
+ *     (phi^n, phi^{n-1}, eps, beta);
+ *  2. energy test: a run whose prediction has the larger E_N (eq.
+ *     energy-discrete-spectral) takes K plain SAV steps instead. After a copy
+ *     restart with r = sqrt(E_1) the modified energy is E_N + C_beta |Omega|,
+ *     so this is the modified-energy test;
+ *  3. every check_every rounds (round j with j % check_every == 0; 0: never)
+ *     a surviving prediction is compared with K plain steps that run's twin
+ *     takes from the same state (phi^n, phi^{n-1}, r^n, r^{n-1}); rel-L2 above
+ *     tol rejects the jump and the run takes the twin's state;
+ *  4. an accepted prediction restarts the run with the copy start (Sec. 5.2:
+ *     phi^{n+K-1} := phi^{n+K}, r = sqrt(E_1)).
+ * net: a network of grid size n <= 256 (the energy test's limit), nruns <= its
+ *    largest batch;
+ * runs: nruns initialised 2D handles on square n x n grids (their eps and
+ *    beta feed the network), owned by the caller;
+ * twins: nruns further 2D handles of the same grids and parameters, used as
+ *    scratch for the checks (their state is overwritten); may be NULL when
+ *    check_every == 0;
+ * counts (host, 5 values, nullable): rounds x runs, accepted, rejected by
+ *    energy, rejected by check, checks made;
+ * decisions (host, jumps x nruns, row-major by round, nullable): 0 accepted,
+ *    1 rejected by energy, 2 rejected by check;
+ * check_err (host, jumps x nruns, nullable): rel-L2 of each checked jump, NaN
+ *    where no check was made.
+ * Synchronous (the handles' and the network's streams are synchronised).
+ * Errors: SPFC_EINVAL, SPFC_ESTATE, SPFC_ENOMEM, SPFC_ECUDA, SPFC_ENONFINITE;
+ * after an error during the rounds the runs may be partly advanced and
+ * counts is not written. Message in spfc_surrogate_last_error(). */
+int spfc_surrogate_advance(spfc_fno_t net, spfc_t* runs, spfc_t* twins, int nruns, int K, int jumps, int check_every,
+                           double tol, int64_t* counts, int8_t* decisions, double* check_err);
+const char* spfc_surrogate_last_error(void);
 
 /* Allocation-free energy diagnostics of one 2D field (float64).
  * The paper has no counterpart: this exists for callers that cannot allocate

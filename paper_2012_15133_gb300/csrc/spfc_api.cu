@@ -10,11 +10,6 @@
 
 using spfc::SolverBase;
 
-struct spfc_s {
-  SolverBase* s = nullptr;
-  std::string err;
-};
-
 static thread_local std::string g_create_err;
 
 // phi[j] = mean + amp (2 u_j - 1), u_j = (x_j >> 11) 2^-53 with x_j output j of
@@ -84,8 +79,9 @@ int spfc_create_scheduled(int d, const int* n, const double* L, double eps, doub
   P.N = n[0];
   P.NH = n[0] / 2 + 1;
   double hd = 1.0, vol = 1.0;
-  for (int i = 0; i < 3; ++i) P.kf[i] = 0.0;
+  for (int i = 0; i < 3; ++i) P.kf[i] = P.Lbox[i] = 0.0;
   for (int i = 0; i < d; ++i) {
+    P.Lbox[i] = L[i];
     P.kf[i] = 2.0 * M_PI / L[i];
     hd *= L[i] / n[i];
     vol *= L[i];
@@ -94,6 +90,7 @@ int spfc_create_scheduled(int d, const int* n, const double* L, double eps, doub
   P.vol = vol;
   P.P = std::pow((double)n[0], d);
   P.a = 1.0 - eps;
+  P.eps = eps;
   P.beta = beta;
   P.C = 1.0 + 1.0 / beta;
   P.dt = dt;

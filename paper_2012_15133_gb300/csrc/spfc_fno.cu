@@ -11,8 +11,11 @@
 #include <string>
 #include <vector>
 
+#include <cstdio>
+
 #include "../../include/spfc.h"
 #include "spfc_common.cuh"
+#include "spfc_internal.h"
 #include "spfc_fno_gemm.cuh"
 
 using namespace spfc::fno;
@@ -570,6 +573,16 @@ struct spfc_fno_s {
 
 static thread_local std::string g_fno_err;
 
+void spfc::fno_shape(const spfc_fno_s* f, int* n, int* max_batch, cudaStream_t* st) {
+  *n = f->n;
+  *max_batch = f->Bmax;
+  *st = f->st;
+}
+
+// Weight file: magic, int32 {n, width, modes1, modes2, layers, proj}, int64
+// parameter count, then the float32 parameters in the documented order.
+static const char kFnoMagic[8] = {'S', 'P', 'F', 'C', 'F', 'N', 'O', '1'};
+
 extern "C" {
 
 int spfc_fno_create(int n, int width, int modes1, int modes2, int layers, int proj, int max_batch, void* stream,
@@ -591,6 +604,44 @@ int spfc_fno_create(int n, int width, int modes1, int modes2, int layers, int pr
 }
 
 int64_t spfc_fno_num_params(spfc_fno_t f) { return f ? f->np : 0; }
+
+int spfc_fno_save(spfc_fno_t f, const char* path) {
+  if (!f || !path) return SPFC_EINVAL;
+  std::vector<float> w((size_t)f->np);
+  int rc = spfc_fno_get_params(f, w.data());
+  if (rc) return rc;
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) { f->err = std::string("cannot open ") + path; return SPFC_EINVAL; }
+  const int32_t hdr[6] = {f->n, f->W, f->m1, f->m2, f->L, f->Q};
+  const int64_t cnt = f->np;
+  bool ok = std::fwrite(kFnoMagic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
+            std::fwrite(&cnt, sizeof(cnt), 1, fp) == 1 && std::fwrite(w.data(), 4, w.size(), fp) == w.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) { f->err = std::string("write failed: ") + path; return SPFC_EINVAL; }
+  return SPFC_OK;
+}
+
+int spfc_fno_load(spfc_fno_t f, const char* path) {
+  if (!f || !path) return SPFC_EINVAL;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) { f->err = std::string("cannot open ") + path; return SPFC_EINVAL; }
+  char magic[8];
+  int32_t hdr[6];
+  int64_t cnt = 0;
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kFnoMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, fp) == 1 && std::fread(&cnt, sizeof(cnt), 1, fp) == 1;
+  const int32_t want[6] = {f->n, f->W, f->m1, f->m2, f->L, f->Q};
+  if (!ok || std::memcmp(hdr, want, sizeof(hdr)) != 0 || cnt != f->np) {
+    std::fclose(fp);
+    f->err = "weight file does not match this network (grid size, width, modes, layers or projection)";
+    return SPFC_EINVAL;
+  }
+  std::vector<float> w((size_t)cnt);
+  ok = std::fread(w.data(), 4, w.size(), fp) == w.size();
+  std::fclose(fp);
+  if (!ok) { f->err = "truncated weight file"; return SPFC_EINVAL; }
+  return spfc_fno_set_params(f, w.data());
+}
 
 int spfc_fno_set_params(spfc_fno_t f, const float* host) {
   if (!f || !host) return SPFC_EINVAL;

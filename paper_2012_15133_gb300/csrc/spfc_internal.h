@@ -105,3 +105,16 @@ SolverBase* make_solver_3d_f64(const Params& P, cudaStream_t st, int* status, st
 SolverBase* make_solver_3d_f32(const Params& P, cudaStream_t st, int* status, std::string* err);
 
 }  // namespace spfc
+
+// The single-run handle behind spfc_t.
+struct spfc_s {
+  spfc::SolverBase* s = nullptr;
+  std::string err;
+};
+
+// Internal view of a network handle (spfc_fno_t) for the surrogate loop:
+// its grid size, largest batch and stream.
+struct spfc_fno_s;
+namespace spfc {
+void fno_shape(const spfc_fno_s* f, int* n, int* max_batch, cudaStream_t* st);
+}  // namespace spfc

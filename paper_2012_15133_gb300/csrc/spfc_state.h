@@ -34,6 +34,9 @@ struct Params {
   double g3;      // gamma3
   double g3b;     // gamma3 / beta (folded into the sum of s^2 that E_1 takes with beta/4)
   float g3_f, g3b_f;
+  // the box lengths and eps exactly as given at creation (kf and a derive from them)
+  double Lbox[3];
+  double eps;
 };
 
 enum PendingKind : int { PEND_NONE = 0, PEND_BDF2 = 1, PEND_BDF1 = 2 };

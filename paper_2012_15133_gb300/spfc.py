@@ -74,6 +74,11 @@ _SIGS = {
     "spfc_fno_adam_step": (_I, [_P, _F, _F, _F, _F, _F]),
     "spfc_fno_destroy": (None, [_P]),
     "spfc_fno_last_error": (ct.c_char_p, [_P]),
+    "spfc_fno_save": (_I, [_P, ct.c_char_p]),
+    "spfc_fno_load": (_I, [_P, ct.c_char_p]),
+    "spfc_surrogate_advance": (_I, [_P, ct.POINTER(_P), ct.POINTER(_P), _I, _I, _I, _I, _D,
+                                    ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int8), _DP]),
+    "spfc_surrogate_last_error": (ct.c_char_p, []),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 

@@ -3,8 +3,9 @@ and judge.
 
 The network (a Fourier neural operator, declared in include/spfc.h) runs in
 this library's CUDA kernels (BF16 tensor-core GEMMs, FP32 accumulation):
-forward, backward and Adam. This module marshals arguments, drives training
-on trajectories of the batched solver, and runs the jump-and-check loop:
+forward, backward and Adam, and so does the jump-and-check loop
+(spfc_surrogate_advance). This module marshals arguments and drives
+training on trajectories of the batched solver. The loop:
 
 * a jump maps (phi^{n-1}, phi^n, eps, beta) to a prediction of phi^{n+K};
 * after an accepted jump the two-level scheme restarts with the copy
@@ -103,6 +104,17 @@ class FNO:
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
         self._check(self._lib.spfc_fno_adam_step(self._h, lr, beta1, beta2, eps, weight_decay))
 
+    def save(self, path):
+        """Write the weights (with the network's shape) to a file."""
+        import os
+        self._check(self._lib.spfc_fno_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Read weights written by save() into a network of the same shape."""
+        import os
+        self._check(self._lib.spfc_fno_load(self._h, os.fsencode(path)))
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.spfc_fno_destroy(self._h)
@@ -192,11 +204,6 @@ def identity_loss(data):
     return float((inc * inc).mean())
 
 
-def _rel(a, b):
-    import torch
-    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-
-
 class JumpLog:
     def __init__(self):
         self.jumps = self.accepted = self.rejected_energy = self.rejected_check = self.checks = 0
@@ -220,13 +227,16 @@ def judges_for(solvers):
     return {i: _twin(s) for i, s in enumerate(solvers)}
 
 
+_KINDS = ("accept", "energy", "check")
+
+
 def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None, judges=None):
     """Advance 2D square runs (Solver objects of one grid size n <= 256) by
     jumps x K steps with the surrogate, falling back to K plain SAV steps per
-    rejected jump. One network call predicts all runs of a jump round.
-    judges: twins from judges_for(solvers), kept by the caller (else made on
-    first use and closed on return)."""
-    import torch
+    rejected jump (the loop runs in the library: spfc_surrogate_advance). One
+    network call predicts all runs of a jump round.
+    judges: twins from judges_for(solvers), kept by the caller (else made
+    here, when checks are on, and closed on return)."""
     if log is None:
         log = JumpLog()
     R = len(solvers)
@@ -235,50 +245,33 @@ def advance(solvers, fno: FNO, K, jumps, check_every=5, tol=1e-3, log=None, judg
         raise ValueError("the surrogate takes square 2D runs of one grid size")
     if R > fno.max_batch or n != fno.n:
         raise ValueError("runs do not fit the network (grid size or batch)")
-    eps = [s.eps for s in solvers]
-    beta = [s.beta for s in solvers]
-    cur = torch.empty((R, n, n), dtype=torch.float64, device="cuda")
-    prev = torch.empty_like(cur)
-    own = judges is None
-    judge = {} if own else judges
+    own = judges is None and check_every > 0
+    judge = judges_for(solvers) if own else judges
+    runs = (ct.c_void_p * R)(*[s._h.value for s in solvers])
+    twins = (ct.c_void_p * R)(*[judge[i]._h.value for i in range(R)]) if check_every > 0 else None
+    counts = (ct.c_int64 * 5)()
+    dec = (ct.c_int8 * max(1, jumps * R))()
+    errs = (ct.c_double * max(1, jumps * R))()
+    try:
+        rc = fno._lib.spfc_surrogate_advance(fno._h, runs, twins, R, int(K), int(jumps), int(check_every),
+                                             float(tol), counts, dec, errs)
+    finally:
+        if own:
+            for t in judge.values():
+                t.close()
+    if rc != 0:
+        raise SPFCError(rc, fno._lib.spfc_surrogate_last_error().decode())
+    log.jumps += counts[0]
+    log.accepted += counts[1]
+    log.rejected_energy += counts[2]
+    log.rejected_check += counts[3]
+    log.checks += counts[4]
     for j in range(jumps):
-        for i, s in enumerate(solvers):
-            s.get_field(0, out=cur[i])
-            s.get_field(1, out=prev[i])
-        pred = fno.predict(cur.float(), prev.float(), eps, beta).double()
-        check = check_every > 0 and j % check_every == 0
-        for i, s in enumerate(solvers):
-            log.jumps += 1
-            e_now = field_energy_noalloc(cur[i], s.L[0], s.eps, s.beta)[0]
-            e_new = field_energy_noalloc(pred[i], s.L[0], s.eps, s.beta)[0]
-            if e_new > e_now:
-                log.rejected_energy += 1
-                log.decisions.append((j, i, "energy"))
-                s.step(K)
-                continue
-            if check:
-                ref = judge.get(i)
-                if ref is None:
-                    ref = judge[i] = _twin(s)
-                sc = s.sav_scalars()
-                ref.set_state(cur[i], prev[i], sc["r"], sc["r_prev"])
-                ref.step(K)
-                plain = ref.get_field(0, out=torch.empty_like(cur[i]))
-                err = _rel(pred[i], plain)
-                log.checks += 1
-                log.check_errors.append(err)
-                if err > tol:
-                    log.rejected_check += 1
-                    log.decisions.append((j, i, "check"))
-                    rs = ref.sav_scalars()
-                    s.set_state(plain, ref.get_field(1, out=torch.empty_like(cur[i])), rs["r"], rs["r_prev"])
-                    continue
-            log.accepted += 1
-            log.decisions.append((j, i, "accept"))
-            s.init(pred[i].contiguous(), "copy")
-    if own:
-        for ref in judge.values():
-            ref.close()
+        for i in range(R):
+            log.decisions.append((j, i, _KINDS[dec[j * R + i]]))
+            e = errs[j * R + i]
+            if e == e:  # checked (NaN otherwise)
+                log.check_errors.append(e)
     return log
 
 

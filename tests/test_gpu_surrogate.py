@@ -105,6 +105,88 @@ def test_rejected_jumps_are_exactly_the_plain_steps():
         assert sa.sav_scalars()["r"] == sb.sav_scalars()["r"]
 
 
+def _reference_advance(solvers, net, K, jumps, check_every, tol):
+    """The jump loop composed in Python from the binding's single calls: the
+    decisions the library's native loop must reproduce."""
+    from paper_2012_15133_gb300 import Solver, field_energy_noalloc
+    R, n = len(solvers), solvers[0].n[0]
+    cur = torch.empty((R, n, n), dtype=torch.float64, device="cuda")
+    prev = torch.empty_like(cur)
+    twins = [Solver(2, n, s.L[0], s.eps, s.beta, s.dt, "fp32") for s in solvers]
+    decisions, errs = [], []
+    for j in range(jumps):
+        for i, s in enumerate(solvers):
+            s.get_field(0, out=cur[i])
+            s.get_field(1, out=prev[i])
+        pred = net.predict(cur.float(), prev.float(), [s.eps for s in solvers], [s.beta for s in solvers]).double()
+        check = check_every > 0 and j % check_every == 0
+        for i, s in enumerate(solvers):
+            e_now = field_energy_noalloc(cur[i], s.L[0], s.eps, s.beta)[0]
+            e_new = field_energy_noalloc(pred[i], s.L[0], s.eps, s.beta)[0]
+            if e_new > e_now:
+                decisions.append((j, i, "energy"))
+                s.step(K)
+                continue
+            if check:
+                sc, t = s.sav_scalars(), twins[i]
+                t.set_state(cur[i], prev[i], sc["r"], sc["r_prev"])
+                t.step(K)
+                plain = t.get_field(0, out=torch.empty_like(cur[i]))
+                err = float(torch.linalg.vector_norm(pred[i] - plain) / torch.linalg.vector_norm(plain))
+                errs.append(err)
+                if err > tol:
+                    decisions.append((j, i, "check"))
+                    ts = t.sav_scalars()
+                    s.set_state(plain, t.get_field(1, out=torch.empty_like(cur[i])), ts["r"], ts["r_prev"])
+                    continue
+            decisions.append((j, i, "accept"))
+            s.init(pred[i].contiguous(), "copy")
+    for t in twins:
+        t.close()
+    return decisions, errs
+
+
+@pytest.mark.parametrize("check_every,tol", [(0, 1e-3), (1, 1e-3), (2, 10.0)])
+def test_the_native_loop_makes_the_decisions_of_its_composition(trained, check_every, tol):
+    """spfc_surrogate_advance against the same loop composed from single calls:
+    the same decisions and check errors, and bit-identical runs afterwards."""
+    from paper_2012_15133_gb300 import surrogate as S
+    net = trained[0]
+    a, b = _solvers(4), _solvers(4)
+    log = S.advance(a, net, K, 4, check_every=check_every, tol=tol)
+    dec, errs = _reference_advance(b, net, K, 4, check_every, tol)
+    assert log.decisions == dec
+    assert log.jumps == 16 and log.accepted == sum(d == "accept" for _, _, d in dec)
+    assert len(log.check_errors) == len(errs) == log.checks
+    assert all(abs(x - y) <= 1e-12 * y for x, y in zip(log.check_errors, errs))
+    for sa, sb in zip(a, b):
+        assert np.array_equal(sa.get_field(0), sb.get_field(0))
+        assert np.array_equal(sa.get_field(1), sb.get_field(1))
+        assert sa.sav_scalars()["r"] == sb.sav_scalars()["r"]
+    if check_every == 1:
+        assert log.rejected_check > 0   # tol 1e-3 is tighter than the network
+    if tol > 1:
+        assert log.rejected_check == 0
+
+
+def test_weights_file_round_trip(trained, tmp_path):
+    from paper_2012_15133_gb300 import surrogate as S, SPFCError
+    net = trained[0]
+    path = str(tmp_path / "net.fno")
+    net.save(path)
+    other = S.FNO(n=N, width=32, modes1=16, modes2=16, layers=4, proj=64, max_batch=16)
+    other.set_params(S.init_params(other, 7))
+    other.load(path)
+    assert np.array_equal(other.get_params(), net.get_params())
+    x = torch.full((2, N, N), 0.2, device="cuda")
+    assert torch.equal(other.predict(x, x, [0.2, 0.1], [1.0, 0.8]), net.predict(x, x, [0.2, 0.1], [1.0, 0.8]))
+    small = S.FNO(n=N, width=8, modes1=4, modes2=4, layers=1, proj=8, max_batch=4)
+    with pytest.raises(SPFCError):
+        small.load(path)
+    other.close()
+    small.close()
+
+
 def test_what_the_trained_network_gains(trained):
     """Rel-L2 of K-step predictions against the plain scheme on held-out
     seeds (at the training pairs' times), for the trained network, the
