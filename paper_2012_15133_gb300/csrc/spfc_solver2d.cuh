@@ -128,6 +128,7 @@ class Solver2D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc_, sizeof(SavScal));  // pinned: small fast reads
     if (e == cudaSuccess) e = al((void**)&counter_, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = al((void**)&sync64_, sizeof(unsigned long long));
     if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
@@ -184,6 +185,7 @@ class Solver2D final : public SolverBase {
                     counter_, sync64_, tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    if (hsc_) cudaFreeHost(hsc_);
   }
 
   int64_t device_bytes() const override { return (int64_t)total_; }
@@ -299,6 +301,7 @@ class Solver2D final : public SolverBase {
   // ---- stepping ------------------------------------------------------------
   int step(long long n) override {
     if (n <= 0) return 0;
+    if (g3_on()) pend_ = true;  // the lazy three-pass steps leave their update pending
     if (!w_ready_ && !g3_on()) {
       // W <- inverse DFT in y of i k~ (2 phi^n - phi^{n-1}): the first half of a step
       int rc = finalize(); if (rc) return rc;
@@ -363,8 +366,9 @@ class Solver2D final : public SolverBase {
 
   int sync() override {
     SPFC_CK(cudaStreamSynchronize(st_));
-    SavScal h;
-    SPFC_CK(cudaMemcpy(&h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost));
+    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaStreamSynchronize(st_));
+    SavScal h = *hsc_;
     if (sizeof(R) == 4) scal_from_ff(&h);
     if (h.status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
@@ -488,6 +492,7 @@ class Solver2D final : public SolverBase {
     return 0;
   }
   int launch_col_fwd(int mode, int target) {
+    if (mode == CF_BDF2 || mode == CF_BDF1) pend_ = true;  // the scalar solve leaves the update pending
     if (g3_on() && mode != CF_TO_STATE) {
       if (mode == CF_BDF2)
         k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
@@ -521,8 +526,9 @@ class Solver2D final : public SolverBase {
     return 0;
   }
   int read_scal(SavScal* h) {
-    SPFC_CK(cudaMemcpyAsync(h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
+    *h = *hsc_;
     if (sizeof(R) == 4) scal_from_ff(h);
     if (h->status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
@@ -531,11 +537,16 @@ class Solver2D final : public SolverBase {
     return 0;
   }
 
-  // materialise a pending update (no-op otherwise)
+  // materialise a pending update (no-op otherwise). Only the lazy column
+  // forward pass leaves one (the fused pass commits its update), so with no
+  // such pass since the last finalize there is nothing to launch.
   int finalize() {
+    if (!pend_) return 0;
     k2d_finalize<R><<<gpw_, PW_THREADS, 0, st_>>>(P, S_, Nhat_, sc_);
     SPFC_CK(cudaGetLastError());
-    return scalar_op(SO_FLIP, nullptr, 0, nullptr, 0, 0);
+    int rc = scalar_op(SO_FLIP, nullptr, 0, nullptr, 0, 0);
+    if (!rc) pend_ = false;
+    return rc;
   }
 
   int copy_newest_to_prev() {
@@ -672,6 +683,7 @@ class Solver2D final : public SolverBase {
   double* real_ = nullptr;
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
   SavScal* sc_ = nullptr;
+  SavScal* hsc_ = nullptr;  // pinned host copy of the record
   unsigned* counter_ = nullptr;
   unsigned long long* sync64_ = nullptr;  // arrival counter of the fused pass's grid barrier
   C* tw_ = nullptr;
@@ -680,6 +692,7 @@ class Solver2D final : public SolverBase {
   cudaGraphExec_t g1_ = nullptr, g16_ = nullptr;
   bool timing_ = false;
   bool w_ready_ = false;            // W holds the first half of the next step
+  bool pend_ = false;               // a lazy pass may have left an update pending on the device
   bool pdl_ = false;                // launch the step kernels with programmatic serialization
   bool use_pdl_ = false;
   std::vector<cudaEvent_t> evpool_;

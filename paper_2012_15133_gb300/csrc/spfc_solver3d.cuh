@@ -53,6 +53,7 @@ class Solver3D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc_, sizeof(SavScal));  // pinned: small fast reads
     if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -96,6 +97,7 @@ class Solver3D final : public SolverBase {
                     tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    if (hsc_) cudaFreeHost(hsc_);
   }
 
   int64_t device_bytes() const override { return (int64_t)total_; }
@@ -246,8 +248,9 @@ class Solver3D final : public SolverBase {
 
   int sync() override {
     SPFC_CK(cudaStreamSynchronize(st_));
-    SavScal h;
-    SPFC_CK(cudaMemcpy(&h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost));
+    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaStreamSynchronize(st_));
+    SavScal h = *hsc_;
     if (h.status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
       return h.status;
@@ -420,8 +423,9 @@ class Solver3D final : public SolverBase {
     return rc ? rc : ypass(Y3_INV);
   }
   int read_scal(SavScal* h) {
-    SPFC_CK(cudaMemcpyAsync(h, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
+    *h = *hsc_;
     if (sizeof(R) == 4) scal_from_ff(h);
     if (h->status != DEV_OK) {
       err = "device status: non-finite value, infeasible SAV scalar system or timeout";
@@ -523,6 +527,7 @@ class Solver3D final : public SolverBase {
   double* real_ = nullptr;
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
   SavScal* sc_ = nullptr;
+  SavScal* hsc_ = nullptr;  // pinned host copy of the record
   C* tw_ = nullptr;
   int gpw_ = 0, nE_ = 0, nG_ = 0;
   size_t spec_bytes_ = 0, total_ = 0;
