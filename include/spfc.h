@@ -277,9 +277,9 @@ int spfc_fno_load(spfc_fno_t f, const char* path);
  *    largest batch;
  * runs: nruns initialised 2D handles on square n x n grids (their eps and
  *    beta feed the network), owned by the caller;
- * twins: nruns further 2D handles of the same grids and parameters, used as
- *    scratch for the checks (their state is overwritten); may be NULL when
- *    check_every == 0;
+ * twins: nruns further 2D handles, distinct and none of them a run, each with
+ *    its run's grid, parameters and precision, used as scratch for the
+ *    checks (their state is overwritten); may be NULL when check_every == 0;
  * counts (host, 5 values, nullable): rounds x runs, accepted, rejected by
  *    energy, rejected by check, checks made;
  * decisions (host, jumps x nruns, row-major by round, nullable): 0 accepted,

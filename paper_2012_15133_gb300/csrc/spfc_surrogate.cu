@@ -88,9 +88,15 @@ int spfc_surrogate_advance(spfc_fno_t net, spfc_t* runs, spfc_t* twins, int nrun
     const spfc::Params& P = h->s->P;
     if (P.d != 2 || P.N != n || P.Lbox[0] != P.Lbox[1])
       return failx(SPFC_EINVAL, "runs must be square 2D grids of the network's size");
+    for (int k = 0; k < i; ++k)
+      if (runs[k] == h) return failx(SPFC_EINVAL, "a run appears twice");
     if (check_every > 0) {
       const spfc_t t = twins[i];
-      if (!t || t == h) return failx(SPFC_EINVAL, "each run needs a twin handle of its own");
+      if (!t) return failx(SPFC_EINVAL, "each run needs a twin handle of its own");
+      for (int k = 0; k < nruns; ++k)
+        if (runs[k] == t) return failx(SPFC_EINVAL, "a twin must not be one of the runs");
+      for (int k = 0; k < i; ++k)
+        if (twins[k] == t) return failx(SPFC_EINVAL, "a twin appears twice");
       const spfc::Params& Q = t->s->P;
       if (Q.d != 2 || Q.N != n || Q.Lbox[0] != P.Lbox[0] || Q.Lbox[1] != P.Lbox[1] || Q.eps != P.eps ||
           Q.beta != P.beta || Q.dt != P.dt || Q.stab != P.stab || Q.g3 != P.g3 ||

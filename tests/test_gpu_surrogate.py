@@ -169,6 +169,34 @@ def test_the_native_loop_makes_the_decisions_of_its_composition(trained, check_e
         assert log.rejected_check == 0
 
 
+def test_the_native_loop_refuses_mismatched_handles(trained):
+    """Twins must match their runs (grid, parameters, precision); runs must be
+    initialised square grids of the network's size; checks need twins."""
+    import ctypes as ct
+    from paper_2012_15133_gb300 import Solver
+    from paper_2012_15133_gb300.spfc import load_library
+    lib = load_library()
+    net = trained[0]
+    a = _solvers(2)
+    good = [Solver(2, N, s.L[0], s.eps, s.beta, s.dt, "fp32") for s in a]
+    wrong = [Solver(2, N, s.L[0], s.eps + 0.01, s.beta, s.dt, "fp32") for s in a]
+    fresh = Solver(2, N, a[0].L[0], a[0].eps, a[0].beta, a[0].dt, "fp32")
+    arr = lambda hs: (ct.c_void_p * len(hs))(*[h._h.value for h in hs])
+    call = lambda runs, twins, check: lib.spfc_surrogate_advance(net._h, runs, twins, 2, K, 1, check, 1e-3,
+                                                                 None, None, None)
+    assert call(arr(a), arr(wrong), 1) == 1
+    assert "parameters" in lib.spfc_surrogate_last_error().decode()
+    assert call(arr(a), None, 1) == 1
+    assert call(arr([a[0], fresh]), arr(good), 1) == 6       # not initialised
+    assert call(arr(a), arr([good[0], a[0]]), 1) == 1       # a run as a twin of another
+    assert "one of the runs" in lib.spfc_surrogate_last_error().decode()
+    assert call(arr(a), arr([good[0], good[0]]), 1) == 1     # one twin for two runs
+    assert call(arr([a[0], a[0]]), arr(good), 1) == 1        # a run twice
+    assert call(arr(a), arr(good), 1) == 0
+    for h in good + wrong + [fresh]:
+        h.close()
+
+
 def test_weights_file_round_trip(trained, tmp_path):
     from paper_2012_15133_gb300 import surrogate as S, SPFCError
     net = trained[0]
