@@ -283,7 +283,10 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
 
   pdl_wait();
   pdl_trigger();
-  if (sc->status != DEV_OK) return;
+  // the nonlinear and energy modes check the status after issuing their W
+  // loads (valid whatever the status), so that its round trip overlaps them
+  constexpr bool LATE_CHECK = (MODE == RW_NONLIN || MODE == RW_ENERGY);
+  if (!LATE_CHECK && sc->status != DEV_OK) return;
   const int rloc = threadIdx.x / T, lane = threadIdx.x % T;
   const int row = blockIdx.x * RPC + rloc;
   C* z = sm + rloc * (G3 ? 2 : 1) * (SEQ + 1);
@@ -333,6 +336,7 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
       v[0][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
       v[1][i] = direct ? f : cconj(f);
     }
+    if (sc->status != DEV_OK) return;
     fft_regs_multi<C, N, E, true, 2, false>(v, z, SEQ + 1, 1, lane, tw);
     typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
     const R beta = pc.beta, g3 = pc.g3, g3b = pc.g3b;
@@ -388,6 +392,7 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
       const C a = W0[off], b = W1[off];
       v[i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
     }
+    if (sc->status != DEV_OK) return;
     fft_regs<C, N, E, true>(v, z, 1, lane, tw);
     // pointwise on x = lane + i T: s = g_x^2 + g_y^2, partial sums, w = (beta s - 2) g
     typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
@@ -816,26 +821,35 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   __shared__ typename RD::acc qres[5];
   __shared__ int bar_ok;
 
+  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
+  const int kx = blockIdx.x * CT + c;
+  const bool col = kx < NH;
+
+  // ---- A: the W columns and the state of this thread's rows ky = lane + i T.
+  // The W loads go out first (valid whatever the status); the status, the
+  // slot index and r (one round trip) follow, then the state loads.
+  C g[2][E], vn[E], vo[E], nh[E];
+  R ia[E];  // A^{-1} of each row, kept for the update (the same rounded value)
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    g[0][i] = g[1][i] = mk<C>(0, 0);
+    if (col) {
+      const size_t off = (size_t)(lane + i * T) * NH + kx;
+      g[0][i] = W0[off];
+      g[1][i] = W1[off];
+    }
+  }
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
   const int p = sc->p;  // phi^n in slot p, phi^{n-1} in slot 1-p (nothing pending)
   const RIn<R> rin(sc);  // read before arriving at the barrier (block 0 rewrites them after it)
   C* scur = S.at(p);
   C* sold = S.at(1 - p);
-  const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
-  const int kx = blockIdx.x * CT + c;
-  const bool col = kx < NH;
-
-  // ---- A: the W columns and the state of this thread's rows ky = lane + i T
-  C g[2][E], vn[E], vo[E], nh[E];
-  R ia[E];  // A^{-1} of each row, kept for the update (the same rounded value)
 #pragma unroll
   for (int i = 0; i < E; ++i) {
-    g[0][i] = g[1][i] = vn[i] = vo[i] = mk<C>(0, 0);
+    vn[i] = vo[i] = mk<C>(0, 0);
     if (col) {
       const size_t off = (size_t)(lane + i * T) * NH + kx;
-      g[0][i] = W0[off];
-      g[1][i] = W1[off];
       vn[i] = scur[off];
       vo[i] = sold[off];
     }
