@@ -257,6 +257,50 @@ def measure_cube(steps, warmup, precision, peak, flush, gamma3=0.0):
                          "note": f"step level: {passes} half-spectrum passes (6 kernels)"}}
 
 
+# Nominal FP64 rate of GB300 as unit counts and clocks: 152 SMs x 2.07 GHz x
+# 2 FP64 FMA (4 flops) per SM per cycle = 1,259 GFLOP/s (1.25 TFLOP/s).
+FP64_PEAK_GFLOPS = 152 * 2.07 * 4
+
+
+def measure_fp64(steps, warmup, hbm_peak, flush):
+    """The 512^2 crystallisation workload on the plain FP64 path (its default
+    schedule), L2 flushed before each timed step. Its bound is FP64
+    arithmetic, not HBM: the roofline counts the transforms' flops only
+    (5 N log2 N per complex length-N transform; 2N row and 4(N/2+1) column
+    transforms per step), a lower bound on the work, against the nominal FP64
+    rate; the HBM fraction of its 11 half-spectrum passes is given beside it."""
+    import math
+    import torch
+    from paper_2012_15133_gb300 import Solver
+    from seeded_inputs import crystal_2d_case
+    c = crystal_2d_case(N_GRID)
+    s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], "fp64")
+    s.init(c["phi0"], "bdf1")
+    s.step(max(3, warmup))
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(st)
+        s.step(1)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    s.sync()
+    n = N_GRID
+    flops = (2 * n + 4 * (n // 2 + 1)) * 5 * n * math.log2(n)
+    bytes_step = 11 * n * (n // 2 + 1) * 16
+    achieved = flops / (ms * 1e-3) / 1e9
+    return {"workload": "2D SPFC 512^2 crystallisation (the headline's workload) on the plain FP64 path",
+            "value": n * n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "schedule": s.schedule, "l2": "flushed before every timed step",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_step": flops,
+                         "peak_source": "nominal FP64 rate: 152 SMs x 2.07 GHz x 2 FMA per SM per cycle",
+                         "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / hbm_peak,
+                         "note": "transform flops only (a lower bound); 11 half-spectrum passes for hbm_frac"}}
+
+
 def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):
     """The 512^2 crystallisation workload with the optional phi^4 term
     (gamma3 = 1): the lazy three-pass step (column inverse with the pending
@@ -532,6 +576,7 @@ def run_ours(args):
         extras["ensemble"] = measure_ensemble(min(args.steps, 200), args.warmup, args.precision, peak, rank, world,
                                               dist)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
+        extras["fp64"] = measure_fp64(min(args.steps, 100), args.warmup, peak, flush)
         extras["gamma3"] = measure_gamma3(min(args.steps, 200), args.warmup, args.precision, peak, flush)
         extras["cube3d_gamma3"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush,
                                                gamma3=1.0)
