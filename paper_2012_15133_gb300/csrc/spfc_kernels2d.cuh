@@ -6,7 +6,13 @@
 // Work arrays W0, W1 have the same shape and hold, between passes, data that
 // is transformed along y only ([y][kx]).
 //
-// One step = col_inv -> row -> col_fwd:
+// The step replayed in production is row -> col_fused (the fused column pass
+// below: the forward half, a grid barrier with the scalar solve, then the
+// update and the inverse half for the next step). The same work split into
+// three separate passes, with the update left pending between steps (the
+// lazy form, used by the start-up and the phi^4 term), is
+// col_inv -> row -> col_fwd; the batched ensemble runs these passes with a
+// separate scalar kernel between col_fwd and col_inv:
 //  col_inv : phi^{n+1} = alpha b + c (lazy update of the previous step),
 //            phi* = 2 phi^{n+1} - phi^n, G_d = i k~_d phi*, inverse DFT in y.
 //  row     : inverse DFT in x of G_x + i G_y (one complex FFT for both real
