@@ -207,6 +207,16 @@ int spfc_batch_create(int nruns, const int* n, const double* L, const double* ep
                       int precision, void* cuda_stream, spfc_batch_t* out);
 /* Start run `run` from phi0 (host, n[run]^2 float64 values) with spfc_start `mode`. */
 int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode);
+/* The optional phi^4 term of one run (as spfc_set_gamma3: gamma3/4 ||phi||_4^4
+ * in E_1, gamma3 phi^3 with its mean removed in N; gamma3 >= 0, 0 the
+ * default). A grid-size class with any run that has the term steps with
+ * passes that carry it (one more half-spectrum work array per run of the
+ * class, allocated on first need; runs with gamma3 = 0 there add zeros).
+ * Set before spfc_batch_init it also applies to that run's start-up; set
+ * later it applies to the following steps. Synchronises the batch's stream.
+ * SPFC_EINVAL for a bad run index or a negative or non-finite gamma3,
+ * SPFC_ENOMEM if the work array cannot be allocated. */
+int spfc_batch_set_gamma3(spfc_batch_t b, int run, double gamma3);
 /* Advance every run by nsteps (asynchronous; a run whose device status
  * latches an error stops, the others continue). */
 int spfc_batch_step(spfc_batch_t b, int64_t nsteps);

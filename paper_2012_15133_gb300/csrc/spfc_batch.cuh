@@ -22,6 +22,7 @@ template <typename R> struct BatchView {
   C_t<R>* Nhat;
   C_t<R>* W0;
   C_t<R>* W1;
+  C_t<R>* W2;   // third work array of the phi^4 term (allocated when a run of the class has one)
   double* partE;
   double* partG;
   SavScal* sc;
@@ -64,6 +65,37 @@ k2b_col_inv(BatchView<R> B, const C_t<R>* __restrict__ tw) {
                                       tw, 0);
 }
 
+// The same passes with the phi^4 channel (a class with a run whose gamma3 is
+// not 0; runs with gamma3 = 0 in it add zeros). No residency bound: the extra
+// sequence of the row pass would not fit 85 registers.
+template <typename R, int N, int E, int RPC>
+__global__ void __launch_bounds__(RPC * (N / E))
+k2b_row_g3(BatchView<R> B, const C_t<R>* __restrict__ tw) {
+  const int r = blockIdx.y;
+  k2d_row_body<R, N, E, RPC, RW_NONLIN, true>(B.P[r], B.W0 + r * B.spec, B.W1 + r * B.spec,
+                                              B.partE + (size_t)r * 2 * B.nE, B.sc + r, tw, nullptr,
+                                              B.W2 + r * B.spec);
+}
+
+template <typename R, int N, int E, int CT>
+__global__ void __launch_bounds__(CT * (N / E))
+k2b_col_fwd_g3(BatchView<R> B, const C_t<R>* __restrict__ tw) {
+  const int r = blockIdx.y;
+  Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};
+  k2d_col_fwd_body<R, N, E, CT, CF_PART, true>(B.P[r], S, B.W0 + r * B.spec, B.W1 + r * B.spec,
+                                              B.Nhat + r * B.spec, B.partG + (size_t)r * 3 * B.nG, nullptr, 0,
+                                              B.sc + r, nullptr, tw, 0);
+}
+
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k2b_col_inv_g3(BatchView<R> B, const C_t<R>* __restrict__ tw) {
+  const int r = blockIdx.y;
+  Slots<R> S{{B.S0 + r * B.spec, B.S1 + r * B.spec}};
+  k2d_col_inv_body<R, N, E, CT, MODE, true>(B.P[r], S, B.Nhat + r * B.spec, B.W0 + r * B.spec, B.W1 + r * B.spec,
+                                            B.sc + r, tw, 0, B.W2 + r * B.spec);
+}
+
 // One block per run: reduce the run's partial sums and solve its scalar
 // system; the inverse column pass then applies the update into slot p.
 template <typename R>
@@ -97,6 +129,7 @@ class BatchClassBase {
   virtual int run_field(int local, double* out, int which) = 0;
   virtual int run_scalars(int local, SavScal* out) = 0;
   virtual int run_energy(int local, double* e3) = 0;
+  virtual int set_gamma3(int local, double g3) = 0;     // the phi^4 term of one run
   virtual int64_t device_bytes() const = 0;
   int N = 0, nruns = 0;
   std::vector<int> runs;  // global run indices
@@ -170,7 +203,7 @@ class BatchClass final : public BatchClassBase {
 
   ~BatchClass() override {
     delete one_;
-    void* ptrs[] = {v_.S0, v_.S1, v_.Nhat, v_.W0, v_.W1, v_.partE, v_.partG, v_.sc, Pdev_, tw_};
+    void* ptrs[] = {v_.S0, v_.S1, v_.Nhat, v_.W0, v_.W1, v_.W2, v_.partE, v_.partG, v_.sc, Pdev_, tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -180,6 +213,14 @@ class BatchClass final : public BatchClassBase {
   int launch_step(cudaStream_t st) override {
     const size_t smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);
     const size_t smr = (size_t)RPC * (sp_len(N_) + 1) * sizeof(C);
+    if (g3_) {
+      k2b_row_g3<R, N_, E, RPC><<<dim3(GROW, nruns), RPC * T, 2 * smr, st>>>(v_, tw_);
+      k2b_col_fwd_g3<R, N_, E, CT><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
+      k2b_scalar<R><<<nruns, 256, 0, st>>>(v_);
+      k2b_col_inv_g3<R, N_, E, CT, CI_STEP_COMMITTED><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     k2b_row<R, N_, E, RPC><<<dim3(GROW, nruns), RPC * T, smr, st>>>(v_, tw_);
     k2b_col_fwd<R, N_, E, CT><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
     k2b_scalar<R><<<nruns, 256, 0, st>>>(v_);
@@ -190,7 +231,8 @@ class BatchClass final : public BatchClassBase {
 
   int prepare(cudaStream_t st) override {
     const size_t smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);
-    k2b_col_inv<R, N_, E, CT, CI_STEP><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
+    if (g3_) k2b_col_inv_g3<R, N_, E, CT, CI_STEP><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
+    else k2b_col_inv<R, N_, E, CT, CI_STEP><<<dim3(GCOL, nruns), CT * T, smc, st>>>(v_, tw_);
     SPFC_CK(cudaGetLastError());
     return 0;
   }
@@ -232,6 +274,37 @@ class BatchClass final : public BatchClassBase {
     return rc;
   }
 
+  // The run's constants (host and device) take the term; a class with any
+  // run that has it steps with the G3 passes, W2 allocated on first need.
+  int set_gamma3(int local, double g3) override {
+    params_[local].g3 = g3;
+    fill_float_params(&params_[local]);
+    SPFC_CK(cudaMemcpy(Pdev_ + local, &params_[local], sizeof(Params), cudaMemcpyHostToDevice));
+    if (g3 != 0.0 && !v_.W2) {
+      cudaError_t e = cudaMalloc((void**)&v_.W2, v_.spec * sizeof(C) * nruns);
+      if (e != cudaSuccess) {
+        v_.W2 = nullptr;
+        err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? 2 : 3;
+      }
+      total_ += v_.spec * sizeof(C) * nruns;
+      const size_t smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);
+      const size_t smr = (size_t)RPC * (sp_len(N_) + 1) * sizeof(C);
+      SPFC_CK(cudaFuncSetAttribute(k2b_row_g3<R, N_, E, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * smr)));
+      SPFC_CK(cudaFuncSetAttribute(k2b_col_fwd_g3<R, N_, E, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smc));
+      SPFC_CK(cudaFuncSetAttribute(k2b_col_inv_g3<R, N_, E, CT, CI_STEP_COMMITTED>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+      SPFC_CK(cudaFuncSetAttribute(k2b_col_inv_g3<R, N_, E, CT, CI_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smc));
+    }
+    g3_ = false;
+    for (const Params& q : params_) g3_ = g3_ || q.g3 != 0.0;
+    one_run_ = -1;  // the single-run solver takes the new constants at its next use
+    return 0;
+  }
+
  private:
   int ensure_one(int local) {
     if (one_ && one_run_ == local) return 0;
@@ -242,6 +315,8 @@ class BatchClass final : public BatchClassBase {
       one_ = s;
     }
     one_->P = params_[local];  // kernels read the per-run constants at launch
+    int rc = one_->set_gamma3(params_[local].g3);  // and its phi^4 kernels their work array
+    if (rc) { err = one_->err; return rc; }
     one_run_ = local;
     return 0;
   }
@@ -290,6 +365,7 @@ class BatchClass final : public BatchClassBase {
   size_t total_ = 0;
   Solver2D<R, N_, 0>* one_ = nullptr;
   int one_run_ = -1;
+  bool g3_ = false;  // some run of the class has the phi^4 term
 };
 
 template <typename R>

@@ -158,6 +158,22 @@ int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode) {
   return SPFC_OK;
 }
 
+int spfc_batch_set_gamma3(spfc_batch_t b, int run, double gamma3) {
+  if (!b) return SPFC_EINVAL;
+  if (run < 0 || run >= (int)b->where.size()) return b->fail(SPFC_EINVAL, "run index out of range");
+  if (!(gamma3 >= 0.0) || !std::isfinite(gamma3)) return b->fail(SPFC_EINVAL, "gamma3 must be finite and >= 0");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return b->fail(SPFC_ECUDA, cudaGetErrorString(e));
+  auto w = b->where[run];
+  int rc = b->classes[w.first]->set_gamma3(w.second, gamma3);
+  if (rc) return b->fail(rc, b->classes[w.first]->err);
+  // the class may switch to the phi^4 passes: new graphs, and W prepared again
+  if (b->g1) { cudaGraphExecDestroy(b->g1); b->g1 = nullptr; }
+  if (b->g8) { cudaGraphExecDestroy(b->g8); b->g8 = nullptr; }
+  b->w_ready = false;
+  return SPFC_OK;
+}
+
 int spfc_batch_step(spfc_batch_t b, int64_t nsteps) {
   if (!b) return SPFC_EINVAL;
   if (nsteps < 0) return b->fail(SPFC_EINVAL, "nsteps must be >= 0");

@@ -143,7 +143,8 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
-  static_assert(!G3 || MODE == CI_STEP || MODE == CI_GRAD, "the phi^4 channel is carried by the step and gradient modes");
+  static_assert(!G3 || MODE == CI_STEP || MODE == CI_GRAD || MODE == CI_STEP_COMMITTED,
+                "the phi^4 channel is carried by the step and gradient modes");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
@@ -625,7 +626,7 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
-  static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT,
+  static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT || MODE == CF_PART,
                 "the phi^4 channel is carried by the modes that form N_hat");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)

@@ -55,6 +55,7 @@ _SIGS = {
     "spfc_last_error": (ct.c_char_p, [_P]),
     "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
     "spfc_batch_init": (_I, [_P, _I, _P, _I]),
+    "spfc_batch_set_gamma3": (_I, [_P, _I, _D]),
     "spfc_batch_step": (_I, [_P, ct.c_int64]),
     "spfc_batch_sync": (_I, [_P]),
     "spfc_batch_get_field": (_I, [_P, _I, _P, _I]),
@@ -366,6 +367,11 @@ class Batch:
         out = (ct.c_double * 3)()
         self._check(self._lib.spfc_batch_energy(self._h, int(run), out))
         return out[0], out[1], out[2]
+
+    def set_gamma3(self, run, gamma3):
+        """The optional phi^4 term of one run (see Solver.set_gamma3)."""
+        self._check(self._lib.spfc_batch_set_gamma3(self._h, int(run), float(gamma3)))
+        return self
 
     @property
     def points(self):

@@ -178,3 +178,24 @@ def test_gamma3_3d_zero_is_the_plain_path():
     a.init(c3["phi0"], "bdf1").step(3)
     b.set_gamma3(G3).set_gamma3(0.0).init(c3["phi0"], "bdf1").step(3)
     assert np.array_equal(a.get_field(0), b.get_field(0))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gamma3_in_the_batched_ensemble(precision):
+    """Three runs in two grid-size classes: gamma3 = 1 and gamma3 = 0 share the
+    64^2 class (which then steps with the phi^4 passes), gamma3 = 0.5 alone at
+    32^2. BDF1 start and four steps against the oracle, with E_N."""
+    from paper_2012_15133_gb300 import Batch, SPFCError
+    runs = [dict(n=n, L=0.5 * n, eps=0.25, beta=1.0, g3=g, phi0=noisy_field((n, n), 0.4, 0.1, 40 + i))
+            for i, (n, g) in enumerate(((64, 1.0), (64, 0.0), (32, 0.5)))]
+    b = Batch(runs, 0.05, precision)
+    for i, r in enumerate(runs):
+        b.set_gamma3(i, r["g3"]).init(i, r["phi0"], "bdf1")
+    b.step(4)
+    for i, r in enumerate(runs):
+        o = Oracle(2, r["n"], r["L"], r["eps"], r["beta"], 0.05, gamma3=r["g3"]).start(r["phi0"], "bdf1").step(4)
+        assert rel_l2(b.get_field(i, 0), o.phi) < TOL[precision], i
+        e = b.energy(i)[0]
+        assert abs(e - o.original_energy()) / abs(o.original_energy()) < TOL[precision], i
+    with pytest.raises(SPFCError):
+        b.set_gamma3(0, -1.0)
