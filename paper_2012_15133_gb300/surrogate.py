@@ -218,7 +218,14 @@ class JumpLog:
 
 
 def _twin(s):
-    return Solver(2, s.n[0], s.L[0], s.eps, s.beta, s.dt, "fp64" if s.precision == 0 else "fp32")
+    """A solver with the run's grid, parameters and precision (stabiliser and
+    phi^4 term included), for the periodic plain-step check."""
+    t = Solver(2, s.n[0], s.L[0], s.eps, s.beta, s.dt, "fp64" if s.precision == 0 else "fp32")
+    if s.stab:
+        t.set_stabilization(s.stab)
+    if s.gamma3:
+        t.set_gamma3(s.gamma3)
+    return t
 
 
 def judges_for(solvers):

@@ -197,6 +197,22 @@ def test_the_native_loop_refuses_mismatched_handles(trained):
         h.close()
 
 
+def test_twins_follow_the_runs_stabiliser_and_phi4_term(trained):
+    """judges_for gives each twin its run's stabiliser and gamma3, which the
+    native loop requires of a twin; the checked loop then runs."""
+    from paper_2012_15133_gb300 import surrogate as S
+    net = trained[0]
+    a = _solvers(2)
+    a[0].set_stabilization(2.0)
+    a[1].set_gamma3(0.5)
+    judges = S.judges_for(a)
+    assert judges[0].stab == 2.0 and judges[1].gamma3 == 0.5
+    log = S.advance(a, net, K, 2, check_every=1, tol=1e-3, judges=judges)
+    assert log.jumps == 4
+    for t in judges.values():
+        t.close()
+
+
 def test_weights_file_round_trip(trained, tmp_path):
     from paper_2012_15133_gb300 import surrogate as S, SPFCError
     net = trained[0]
