@@ -57,6 +57,31 @@ def test_create_rejects_invalid_arguments_before_touching_the_gpu(lib):
     assert b"same N" in L.spfc_last_error(None)
 
 
+def test_other_entry_points_refuse_bad_arguments_before_touching_the_gpu(lib):
+    """NULL handles and out-of-range arguments come back as SPFC_EINVAL (1),
+    with a message, before any device work."""
+    import ctypes as ct
+    from paper_2012_15133_gb300 import spfc
+    L = spfc.load_library()
+    assert L.spfc_set_gamma3(None, 1.0) == 1
+    assert L.spfc_set_stabilization(None, 1.0) == 1
+    assert L.spfc_batch_set_gamma3(None, 0, 1.0) == 1
+    assert L.spfc_surrogate_advance(None, None, None, 1, 20, 1, 0, 1e-3, None, None, None) == 1
+    assert b"bad argument" in L.spfc_surrogate_last_error()
+    assert L.spfc_fno_save(None, b"w.fno") == 1 and L.spfc_fno_load(None, b"w.fno") == 1
+    f = ct.c_void_p()
+    assert L.spfc_fno_create(48, 32, 16, 16, 4, 64, 16, None, ct.byref(f)) == 1   # n not a power of two
+    assert L.spfc_fno_create(256, 32, 200, 16, 4, 64, 16, None, ct.byref(f)) == 1  # modes beyond n/2
+    assert b"invalid network size" in L.spfc_fno_last_error(None)
+    b = ct.c_void_p()
+    n1, L1 = (ct.c_int * 1)(64), (ct.c_double * 1)(32.0)
+    assert L.spfc_batch_create(0, n1, L1, (ct.c_double * 1)(0.1), (ct.c_double * 1)(1.0), 0.02, 1, None,
+                               ct.byref(b)) == 1
+    assert L.spfc_batch_create(1, n1, L1, (ct.c_double * 1)(1.2), (ct.c_double * 1)(1.0), 0.02, 1, None,
+                               ct.byref(b)) == 1                                  # a = 1 - eps <= 0
+    assert b"1 - eps" in L.spfc_batch_last_error(None)
+
+
 def test_product_path_has_no_oracle_dependency():
     pkg = os.path.join(ROOT, "paper_2012_15133_gb300")
     for dirpath, _, files in os.walk(pkg):
