@@ -75,8 +75,16 @@ def test_ghost_point_closed_form():
 
 
 def test_second_order_manufactured_solution():
-    slope = P.manufactured_slope()
-    assert -2.2 < slope < -1.8, slope
+    """The convergence test of Sec. 5.1 as the paper states it (tests/golden/
+    sec5_1_convergence.json): the same exact solution, a and T, and the
+    slope it reports, in both the l2 and the l-infinity norm."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sec5_1_convergence.json")) as f:
+        gold = json.load(f)
+    for norm in ("l2", "linf"):
+        slope = P.manufactured_slope(norm=norm, a=gold["a"], T=gold["T"])
+        assert abs(slope - gold["slope"]) < gold["slope_tolerance"], (norm, slope)
 
 
 def test_self_convergence_ratio():
