@@ -553,3 +553,82 @@ def pin_gamma3_variational() -> float:
             an = g.inner(m.N_op(phi), psi)
             worst = max(worst, abs(fd - an) / abs(an))
     return worst
+
+
+# --- energies and mass of the diagnostics in closed form ----------------------
+
+def _coords(g):
+    d = g.d
+    cs = np.meshgrid(*[np.arange(g.shape[ax]) * g.h[d - 1 - ax] for ax in range(d)], indexing="ij")
+    return {c: cs[g.axis_of[c]] for c in range(d)}
+
+
+def pin_energies_closed_form() -> float:
+    """E_N (eq. energy-discrete-spectral), the modified energy of eq. discrete
+    energy, E_breve (Sec. 5.2) and the mass <phi, 1> of trigonometric
+    polynomials whose grid sums are exact (every harmonic of the quartic terms
+    below N/2, so no aliasing):
+
+    * phi = c0 + A cos(k x_c) along each coordinate c:
+      ||phi||^2 = |Omega| (c0^2 + A^2/2), ||grad phi||^2 = |Omega| A^2 k^2 / 2,
+      ||Delta_N phi||^2 = |Omega| A^2 k^4 / 2, ||grad phi||_4^4 = |Omega| 3/8 A^4 k^4,
+      ||phi||_4^4 = |Omega| (c0^4 + 3 c0^2 A^2 + 3/8 A^4);
+    * the 2D product mode phi = c0 + A cos(k1 x) cos(k2 y):
+      ||phi||^2 = |Omega| (c0^2 + A^2/4), ||grad phi||^2 = |Omega| A^2 (k1^2 + k2^2)/4,
+      ||Delta_N phi||^2 = |Omega| A^2 (k1^2 + k2^2)^2 / 4,
+      ||grad phi||_4^4 = |Omega| A^4 (9/64 (k1^4 + k2^4) + 2/64 k1^2 k2^2),
+      ||phi||_4^4 = |Omega| (c0^4 + 3/2 c0^2 A^2 + 9/64 A^4);
+    then E_N = beta/4 G4 + a/2 P2 - G2 + 1/2 D2 + gamma3/4 Q4,
+    ||L_N^{1/2} f||^2 = a P2(f) + D2(f), E_mod = 1/4 (||L^{1/2} phi^{n+1}||^2 +
+    ||L^{1/2} (2 phi^{n+1} - phi^n)||^2) + 1/2 (r^{n+1 2} + (2 r^{n+1} - r^n)^2) and
+    E_breve = a/2 P2 + 1/2 D2 + r^2 (r, r^n given numbers)."""
+    worst = 0.0
+
+    def energies(m, P2, G2, D2, G4, Q4):
+        return (m.beta / 4 * G4 + 0.5 * m.a * P2 - G2 + 0.5 * D2 + m.gamma3 / 4 * Q4,
+                0.5 * m.a * P2 + 0.5 * D2)
+
+    for d, n, L in ((2, (32, 24), (16.0, 12.0)), (3, 16, (8.0, 6.0, 5.0))):
+        g = so.Grid(d, n, L)
+        X = _coords(g)
+        V = g.volume
+        for c in range(d):
+            for eps, beta, g3 in ((0.25, 1.0, 0.0), (0.6, 0.7, 1.3)):
+                m = so.Model(g, eps=eps, beta=beta)
+                m.gamma3 = g3
+                ell = 2 if 4 * 3 >= g.n[c] else 3              # 4 ell < N: no aliasing
+                k = 2 * math.pi * ell / g.L[c]
+                terms = {}
+                for key, c0, A in (("new", 0.3, 0.8), ("old", -0.1, 0.5), ("psi", 0.7, 1.1)):
+                    terms[key] = (V * (c0 ** 2 + A ** 2 / 2), V * A ** 2 * k ** 2 / 2, V * A ** 2 * k ** 4 / 2,
+                                  V * 3 / 8 * A ** 4 * k ** 4, V * (c0 ** 4 + 3 * c0 ** 2 * A ** 2 + 3 / 8 * A ** 4))
+                phi = 0.3 + 0.8 * np.cos(k * X[c])
+                old = -0.1 + 0.5 * np.cos(k * X[c])           # 2 phi - old = 0.7 + 1.1 cos
+                EN, EL = energies(m, *terms["new"])
+                worst = max(worst, abs(m.E_orig(phi) - EN) / abs(EN))
+                r, r_old = 1.7, 1.9
+                worst = max(worst, abs(m.E_breve(phi, r) - (EL + r * r)) / (EL + r * r))
+                Lnew = m.a * terms["new"][0] + terms["new"][2]
+                Lpsi = m.a * terms["psi"][0] + terms["psi"][2]
+                Emod = 0.25 * (Lnew + Lpsi) + 0.5 * (r * r + (2 * r - r_old) ** 2)
+                worst = max(worst, abs(m.E_mod(phi, old, r, r_old) - Emod) / Emod)
+                worst = max(worst, abs(g.mean_value(phi) - 0.3 * V) / (0.3 * V))
+        if d == 2:
+            for eps, beta, g3 in ((0.25, 1.0, 0.0), (0.4, 1.4, 0.9)):
+                m = so.Model(g, eps=eps, beta=beta)
+                m.gamma3 = g3
+                k1, k2 = 2 * math.pi * 3 / g.L[0], 2 * math.pi * 2 / g.L[1]
+                c0, A = 0.2, 0.9
+                phi = c0 + A * np.cos(k1 * X[0]) * np.cos(k2 * X[1])
+                KK = k1 * k1 + k2 * k2
+                P2 = V * (c0 ** 2 + A ** 2 / 4)
+                G2 = V * A ** 2 * KK / 4
+                D2 = V * A ** 2 * KK ** 2 / 4
+                G4 = V * A ** 4 * (9 / 64 * (k1 ** 4 + k2 ** 4) + 2 / 64 * k1 ** 2 * k2 ** 2)
+                Q4 = V * (c0 ** 4 + 1.5 * c0 ** 2 * A ** 2 + 9 / 64 * A ** 4)
+                EN, EL = energies(m, P2, G2, D2, G4, Q4)
+                worst = max(worst, abs(m.E_orig(phi) - EN) / abs(EN))
+                worst = max(worst, abs(m.E_breve(phi, 0.4) - (EL + 0.16)) / (EL + 0.16))
+                worst = max(worst, abs(m.L_norm_sq(phi) - (m.a * P2 + D2)) / (m.a * P2 + D2))
+                worst = max(worst, abs(g.mean_value(phi) - c0 * V) / (c0 * V))
+    return worst

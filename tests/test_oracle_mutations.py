@@ -26,6 +26,7 @@ PINS = [
     (P.pin_stab_linear_closed_form, lambda v: v < 1e-12),
     (P.pin_gamma3_cosine, lambda v: v < 1e-12),
     (P.pin_gamma3_variational, lambda v: v < 1e-9),
+    (P.pin_energies_closed_form, lambda v: v < 1e-12),
 ]
 
 
@@ -191,12 +192,51 @@ def _m_gamma3_mean_kept(mp):
     mp.setattr(so.Model, "N_op", N_op)
 
 
+def _m_original_energy_half_dropped(mp):
+    def E_orig(self, phi):
+        g = self.g
+        s = self.grad_sq(phi)
+        lp = g.lap(phi)
+        return (self.beta / 4.0) * g.hd * float(np.sum(s * s)) + 0.5 * self.a * g.inner(phi, phi) \
+            - g.hd * float(np.sum(s)) + g.inner(lp, lp) + (self.gamma3 / 4.0) * g.hd * float(np.sum(phi ** 4))
+    mp.setattr(so.Model, "E_orig", E_orig)
+
+
+def _m_original_energy_gamma3_dropped(mp):
+    orig = so.Model.E_orig
+
+    def E_orig(self, phi):
+        return orig(self, phi) - (self.gamma3 / 4.0) * self.g.hd * float(np.sum(phi ** 4))
+    mp.setattr(so.Model, "E_orig", E_orig)
+
+
+def _m_breve_energy_without_a(mp):
+    def E_breve(self, phi, r):
+        g = self.g
+        lp = g.lap(phi)
+        return 0.5 * g.inner(phi, phi) + 0.5 * g.inner(lp, lp) + r * r
+    mp.setattr(so.Model, "E_breve", E_breve)
+
+
+def _m_modified_energy_swapped_levels(mp):
+    def E_mod(self, pn, po, rn, ro):
+        psi = 2 * po - pn
+        return 0.25 * (self.L_norm_sq(pn) + self.L_norm_sq(psi)) + 0.5 * (rn ** 2 + (2 * rn - ro) ** 2)
+    mp.setattr(so.Model, "E_mod", E_mod)
+
+
+def _m_mass_without_cell_volume(mp):
+    mp.setattr(so.Grid, "mean_value", lambda self, f: float(np.sum(f)))
+
+
 MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_axis,
              _m_wrong_bdf2_operator, _m_wrong_r_coefficient, _m_E1_constant_ignores_beta,
              _m_energy_quarter_dropped, _m_first_order_extrapolation,
              _m_dft_missing_normalisation, _m_linear_operator_sign, _m_laplacian_drops_nyquist,
              _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt,
-             _m_gamma3_dropped_from_N, _m_gamma3_energy_factor, _m_gamma3_mean_kept]
+             _m_gamma3_dropped_from_N, _m_gamma3_energy_factor, _m_gamma3_mean_kept,
+             _m_original_energy_half_dropped, _m_original_energy_gamma3_dropped, _m_breve_energy_without_a,
+             _m_modified_energy_swapped_levels, _m_mass_without_cell_volume]
 
 
 def test_pins_pass_unmutated():

@@ -118,3 +118,10 @@ def test_potential_is_the_variational_derivative_of_E1():
 
 def test_scheme_residual_with_phi4_term():
     assert P.pin_residual(2, gamma3=0.8) < 1e-12
+
+
+def test_energies_and_mass_closed_form():
+    """E_N, the modified energy, E_breve and the mass of trigonometric
+    polynomials against their closed forms (single modes along each axis of a
+    non-square 2D and a non-cubic 3D box, and a 2D product mode)."""
+    assert P.pin_energies_closed_form() < 1e-12
