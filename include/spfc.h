@@ -207,6 +207,14 @@ int spfc_batch_create(int nruns, const int* n, const double* L, const double* ep
                       int precision, void* cuda_stream, spfc_batch_t* out);
 /* Start run `run` from phi0 (host, n[run]^2 float64 values) with spfc_start `mode`. */
 int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode);
+/* Set both time levels and the auxiliary scalars of one run directly, as
+ * spfc_set_state does for a single run: phi = phi^n, phi_prev = phi^{n-1}
+ * (host, n[run]^2 float64 values each, x fastest), r = r^n, r_prev =
+ * r^{n-1} (eq. scheme-SAV-1 advances from this state). Used for restarts and
+ * for per-step comparisons from a given state. Synchronises the batch's
+ * stream. SPFC_EINVAL for a bad run index, a NULL field or a non-finite r. */
+int spfc_batch_set_state(spfc_batch_t b, int run, const double* phi, const double* phi_prev, double r,
+                         double r_prev);
 /* The optional phi^4 term of one run (as spfc_set_gamma3: gamma3/4 ||phi||_4^4
  * in E_1, gamma3 phi^3 with its mean removed in N; gamma3 >= 0, 0 the
  * default). A grid-size class with any run that has the term steps with

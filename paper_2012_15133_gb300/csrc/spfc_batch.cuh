@@ -126,6 +126,7 @@ class BatchClassBase {
   virtual int launch_step(cudaStream_t st) = 0;         // one step of every run in the class
   virtual int prepare(cudaStream_t st) = 0;             // W <- first half of the next step
   virtual int load_run(int local, const double* phi0, int mode) = 0;
+  virtual int set_run_state(int local, const double* phi, const double* phi_prev, double r, double r_prev) = 0;
   virtual int run_field(int local, double* out, int which) = 0;
   virtual int run_scalars(int local, SavScal* out) = 0;
   virtual int run_energy(int local, double* e3) = 0;
@@ -251,6 +252,16 @@ class BatchClass final : public BatchClassBase {
       SPFC_CK(cudaMemcpy(v_.sc + local, &h, sizeof(SavScal), cudaMemcpyHostToDevice));
       return rc;
     }
+    return export_one(local);
+  }
+
+  // Both time levels and r of one run set directly (the single-run solver
+  // transforms them, then its state is copied in).
+  int set_run_state(int local, const double* phi, const double* phi_prev, double r, double r_prev) override {
+    int rc = ensure_one(local);
+    if (rc) return rc;
+    rc = one_->set_state(phi, phi_prev, r, r_prev, false);
+    if (rc) { err = one_->err; return rc; }
     return export_one(local);
   }
 

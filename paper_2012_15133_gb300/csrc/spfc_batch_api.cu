@@ -158,6 +158,20 @@ int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode) {
   return SPFC_OK;
 }
 
+int spfc_batch_set_state(spfc_batch_t b, int run, const double* phi, const double* phi_prev, double r,
+                         double r_prev) {
+  if (!b || !phi || !phi_prev) return SPFC_EINVAL;
+  if (run < 0 || run >= (int)b->where.size()) return b->fail(SPFC_EINVAL, "run index out of range");
+  if (!std::isfinite(r) || !std::isfinite(r_prev)) return b->fail(SPFC_EINVAL, "r and r_prev must be finite");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return b->fail(SPFC_ECUDA, cudaGetErrorString(e));
+  auto w = b->where[run];
+  int rc = b->classes[w.first]->set_run_state(w.second, phi, phi_prev, r, r_prev);
+  if (rc) return b->fail(rc, b->classes[w.first]->err);
+  b->w_ready = false;
+  return SPFC_OK;
+}
+
 int spfc_batch_set_gamma3(spfc_batch_t b, int run, double gamma3) {
   if (!b) return SPFC_EINVAL;
   if (run < 0 || run >= (int)b->where.size()) return b->fail(SPFC_EINVAL, "run index out of range");

@@ -55,6 +55,7 @@ _SIGS = {
     "spfc_last_error": (ct.c_char_p, [_P]),
     "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
     "spfc_batch_init": (_I, [_P, _I, _P, _I]),
+    "spfc_batch_set_state": (_I, [_P, _I, _P, _P, _D, _D]),
     "spfc_batch_set_gamma3": (_I, [_P, _I, _D]),
     "spfc_batch_step": (_I, [_P, ct.c_int64]),
     "spfc_batch_sync": (_I, [_P]),
@@ -339,6 +340,17 @@ class Batch:
         if arr.size != n * n:
             raise ValueError("field has the wrong size")
         self._check(self._lib.spfc_batch_init(self._h, int(run), arr.ctypes.data_as(ct.c_void_p), _START[mode]))
+        return self
+
+    def set_state(self, run, phi, phi_prev, r, r_prev):
+        """Both time levels (host arrays) and r^n, r^{n-1} of one run."""
+        n = int(self.runs[run]["n"])
+        a = np.ascontiguousarray(phi, dtype=np.float64)
+        b = np.ascontiguousarray(phi_prev, dtype=np.float64)
+        if a.size != n * n or b.size != n * n:
+            raise ValueError("field has the wrong size")
+        self._check(self._lib.spfc_batch_set_state(self._h, int(run), a.ctypes.data_as(ct.c_void_p),
+                                                   b.ctypes.data_as(ct.c_void_p), float(r), float(r_prev)))
         return self
 
     def step(self, nsteps=1):

@@ -66,6 +66,7 @@ def test_other_entry_points_refuse_bad_arguments_before_touching_the_gpu(lib):
     assert L.spfc_set_gamma3(None, 1.0) == 1
     assert L.spfc_set_stabilization(None, 1.0) == 1
     assert L.spfc_batch_set_gamma3(None, 0, 1.0) == 1
+    assert L.spfc_batch_set_state(None, 0, None, None, 1.0, 1.0) == 1
     assert L.spfc_surrogate_advance(None, None, None, 1, 20, 1, 0, 1e-3, None, None, None) == 1
     assert b"bad argument" in L.spfc_surrogate_last_error()
     assert L.spfc_fno_save(None, b"w.fno") == 1 and L.spfc_fno_load(None, b"w.fno") == 1

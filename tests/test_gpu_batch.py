@@ -44,6 +44,39 @@ def test_small_ensemble_matches_oracle(precision, tol):
         assert sc["nsteps"] == 5  # the BDF1 start plus four steps
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_ensemble_sizes_per_step_match_oracle(precision, tol):
+    """Per step from an identical state, at the scheme's gates (rel-L2 of
+    phi^{n+1} and |r^{n+1} - r|/r at 1e-12 on the FP64 path, 1e-5 on the FP32
+    bulk): one batch holding the ensemble workload's four grid classes 64^2,
+    128^2, 256^2 and 512^2 (L = N/2, eps, beta and mean drawn per run, two
+    runs per class), each run set to the oracle's state after its BDF1 start
+    and two BDF2 steps. The first batched step runs after the preparing
+    column pass, the second inside the replayed step (committed update in
+    the column pass); the second is compared with the oracle advanced from
+    the same state, so its error holds two steps of rounding."""
+    from paper_2012_15133_gb300 import Batch
+    runs = _runs((64, 128, 256, 512), 8)
+    b = Batch(runs, 0.02, precision)
+    oracles = []
+    for i, r in enumerate(runs):
+        o = Oracle(2, r["n"], r["L"], r["eps"], r["beta"], r["dt"], dft="numpy").start(r["phi0"], "bdf1")
+        o.step(2)
+        b.set_state(i, o.phi, o.phi_prev, o.r, o.r_prev)
+        oracles.append(o)
+    for k in range(2):
+        b.step(1)
+        for i, (r, o) in enumerate(zip(runs, oracles)):
+            o.step(1)
+            err = rel_l2(b.get_field(i), o.phi)
+            assert err < tol, (k, i, r["n"], err)
+            sc = b.scalars(i)
+            assert abs(sc["r"] - o.r) / o.r < tol, (k, i, r["n"])
+            assert abs(sc["E1"] - o.last_info["E1"]) / o.last_info["E1"] < tol, (k, i, r["n"])
+            assert abs(sc["gamma"] - o.last_info["gamma"]) / abs(o.last_info["gamma"]) < tol, (k, i, r["n"])
+            assert sc["status"] == 0
+
+
 def test_ensemble_workload_sizes_match_single_runs():
     """Two runs of each of 64, 128, 256, 512 (the ensemble workload's sizes and
     parameter draws), FP32 bulk, against independent single-run solvers."""
