@@ -257,22 +257,33 @@ def measure_cube(steps, warmup, precision, peak, flush, gamma3=0.0):
                          "note": f"step level: {passes} half-spectrum passes (6 kernels)"}}
 
 
-# Nominal FP64 rate of GB300 as unit counts and clocks: 152 SMs x 2.07 GHz x
-# 2 FP64 FMA (4 flops) per SM per cycle = 1,259 GFLOP/s (1.25 TFLOP/s).
-FP64_PEAK_GFLOPS = 152 * 2.07 * 4
+def fp64_flops_per_step(n):
+    """Algorithmic float64 flops of one 2D BDF2-SAV step on an n x n grid (an
+    FMA counts 2, a division 1):
+    transforms 5 N log2 N per complex length-N FFT, 2N row transforms (inverse
+    and forward x-DFT of G_x + i G_y) and 4(N/2+1) column transforms (two
+    fields, both directions); per grid point 10 in the row pass (s, the E_1
+    sums, w); per half-spectrum mode 8 for the W_x/W_y split, 44 in the
+    forward column pass (N_hat, |k|^2, the symbol and 1/A, v and the gamma,
+    eta, theta products and sums) and 27 for the update, the next phi* and
+    its gradients."""
+    nh = n // 2 + 1
+    fft = (2 * n + 4 * nh) * 5 * n * math.log2(n)
+    return fft + 10 * n * n + (8 + 44 + 27) * n * nh
 
 
 def measure_fp64(steps, warmup, hbm_peak, flush):
     """The 512^2 crystallisation workload on the plain FP64 path (its default
-    schedule), L2 flushed before each timed step. Its bound is FP64
-    arithmetic, not HBM: the roofline counts the transforms' flops only
-    (5 N log2 N per complex length-N transform; 2N row and 4(N/2+1) column
-    transforms per step), a lower bound on the work, against the nominal FP64
-    rate; the HBM fraction of its 11 half-spectrum passes is given beside it."""
-    import math
+    schedule), L2 flushed before each timed step. Its bound is float64
+    arithmetic: the roofline is the step's algorithmic float64 flops
+    (fp64_flops_per_step) per step time against the float64 FMA rate measured
+    on this GPU by the library's own dependence-free FMA kernel; the HBM
+    fraction of the step's 15 half-spectrum passes (SURVEY's bytes) is given
+    beside it."""
     import torch
-    from paper_2012_15133_gb300 import Solver
+    from paper_2012_15133_gb300 import Solver, fp64_fma_rate
     from seeded_inputs import crystal_2d_case
+    peak = fp64_fma_rate()
     c = crystal_2d_case(N_GRID)
     s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], "fp64")
     s.init(c["phi0"], "bdf1")
@@ -288,17 +299,18 @@ def measure_fp64(steps, warmup, hbm_peak, flush):
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     s.sync()
     n = N_GRID
-    flops = (2 * n + 4 * (n // 2 + 1)) * 5 * n * math.log2(n)
-    bytes_step = 11 * n * (n // 2 + 1) * 16
+    flops = fp64_flops_per_step(n)
+    bytes_step = 15 * n * (n // 2 + 1) * 16
     achieved = flops / (ms * 1e-3) / 1e9
     return {"workload": "2D SPFC 512^2 crystallisation (the headline's workload) on the plain FP64 path",
             "value": n * n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "schedule": s.schedule, "l2": "flushed before every timed step",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "flops_per_step": flops,
-                         "peak_source": "nominal FP64 rate: 152 SMs x 2.07 GHz x 2 FMA per SM per cycle",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "flops_per_step": flops,
+                         "peak_source": "measured: float64 FMA rate of this GPU (spfc_fp64_fma_rate)",
                          "hbm_frac": bytes_step / (ms * 1e-3) / 1e9 / hbm_peak,
-                         "note": "transform flops only (a lower bound); 11 half-spectrum passes for hbm_frac"}}
+                         "note": "all float64 flops of the step (transforms, pointwise, symbols, 1/A, sums); "
+                                 "15 half-spectrum passes for hbm_frac"}}
 
 
 def measure_gamma3(steps, warmup, precision, peak, flush, gamma3=1.0):

@@ -125,7 +125,10 @@ int spfc_mass(spfc_t h, double* mass, double* mean);
 /* Scalars of the current state and of the last SAV solve (synchronising):
  * out[0] = r^n, out[1] = r^{n-1}, out[2] = xi = r^n / sqrt(E_1), out[3] = gamma =
  * <N, A^{-1} Delta N> (<= 0, eq. solver-5), out[4] = E_1 at the extrapolation,
- * out[5] = the steps taken since init. `nout` entries (<= 6) are written. */
+ * out[5] = the steps taken since init, and of the last solve out[6] = eta =
+ * <N, A^{-1}(2 phi^n - phi^{n-1}/2)>, out[7] = theta = <N, 2 phi^n - phi^{n-1}/2>,
+ * out[8] = 1 - dt gamma / (2 E_1), out[9] = LHS (eq. solver-4). All of them
+ * are float64 on both precision paths. `nout` entries (<= 10) are written. */
 int spfc_sav_scalars(spfc_t h, double* out, int nout);
 
 /* Copy phi^n (which = 0) or phi^{n-1} (which = 1) to `out` (N^d float64 values). */
@@ -189,6 +192,15 @@ int64_t spfc_device_bytes(spfc_t h);
  * ran out (target > 0), SPFC_OK when it was already satisfied (target == 0),
  * SPFC_EINVAL for a bad poll count. The context stays usable either way. */
 int spfc_wait_selftest(unsigned long long target, long long polls, void* cuda_stream);
+
+/* Measured float64 FMA throughput of the current device in GFLOP/s (one FMA
+ * = 2 flops), the arithmetic roofline of the float64 step (the paper has no
+ * counterpart): 4 x SM-count blocks of 256 threads, each thread 8
+ * independent chains of 4096 FMAs, best of three timed launches after one
+ * warm-up (CUDA events on cuda_stream, synchronising). Allocates and frees
+ * one small output buffer. SPFC_EINVAL for a NULL pointer, SPFC_ENOMEM,
+ * SPFC_ECUDA. */
+int spfc_fp64_fma_rate(double* gflops, void* cuda_stream);
 
 void spfc_destroy(spfc_t h);
 

@@ -290,8 +290,26 @@ def bdf2_sav_step(model: Model, dt: float, phi_n, phi_nm1, r_n: float, r_nm1: fl
     phi_np1 = (dt / (2.0 * E1)) * LHS * Ainv_lapN + Ainv_g         # eq. solver-6
     r_np1 = (4.0 / 3.0) * r_n - (1.0 / 3.0) * r_nm1 \
         + g.inner(Nh, 1.5 * phi_np1 - 2.0 * phi_n + 0.5 * phi_nm1) / (3.0 * sqE1)  # eq. solver-2
-    info = dict(E1=E1, sqrtE1=sqE1, gamma=gam, denom=denom, LHS=LHS, xi=r_np1 / sqE1)
+    # the two remaining inner products of the scalar form of the solve (diagnostics):
+    # eta = <N, A^{-1} (2 phi^n - phi^{n-1}/2 + stabiliser)>, theta = <N, 2 phi^n - phi^{n-1}/2>
+    eta = g.inner(Nh, A_inv(model, 2.0 * phi_n - 0.5 * phi_nm1 + stab_rhs(model, dt, phi_n), dt, 1.5))
+    theta = g.inner(Nh, 2.0 * phi_n - 0.5 * phi_nm1)
+    info = dict(E1=E1, sqrtE1=sqE1, gamma=gam, denom=denom, LHS=LHS, xi=r_np1 / sqE1, eta=eta, theta=theta)
     return phi_np1, r_np1, info
+
+
+def sav_r_update(E1: float, gamma: float, eta: float, theta: float, r_n: float, r_nm1: float, dt: float,
+                 bdf1: bool = False) -> float:
+    """r^{n+1} from the step's scalars alone: eq. solver-2 with <N, phi^{n+1}> = LHS
+    (eq. solver-4 and eq. solver-6), i.e.
+    rho = 4/3 r^n - 1/3 r^{n-1} - theta / (3 sqrt(E1)),
+    LHS = (dt rho gamma / sqrt(E1) + eta) / (1 - dt gamma / (2 E1)),
+    r^{n+1} = rho + LHS / (2 sqrt(E1)).
+    The first-order start has rho = r^0 - theta / (2 sqrt(E1)) with r^0 = sqrt(E1)."""
+    S = math.sqrt(E1)
+    rho = (S - theta / (2.0 * S)) if bdf1 else (4.0 * r_n - r_nm1 - theta / S) / 3.0
+    LHS = (dt * rho * gamma / S + eta) / (1.0 - dt * gamma / (2.0 * E1))
+    return rho + LHS / (2.0 * S)
 
 
 def bdf1_sav_step(model: Model, dt: float, phi0, forcing=None):
@@ -316,7 +334,9 @@ def bdf1_sav_step(model: Model, dt: float, phi0, forcing=None):
     LHS = g.inner(Nh, Ainv_g) / denom
     phi1 = (dt / (2.0 * E1)) * LHS * Ainv_lapN + Ainv_g
     r1 = r0 + g.inner(Nh, phi1 - phi0) / (2.0 * sqE1)
-    info = dict(E1=E1, sqrtE1=sqE1, gamma=gam, denom=denom, LHS=LHS, xi=r1 / sqE1)
+    eta = g.inner(Nh, A_inv(model, phi0 + stab_rhs(model, dt, phi0), dt, 1.0))
+    theta = g.inner(Nh, phi0)
+    info = dict(E1=E1, sqrtE1=sqE1, gamma=gam, denom=denom, LHS=LHS, xi=r1 / sqE1, eta=eta, theta=theta)
     return phi1, r1, r0, info
 
 

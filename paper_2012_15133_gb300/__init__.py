@@ -8,8 +8,8 @@ solver without the built library raises.
 """
 from .spfc import (Solver, SPFCError, lib_path, load_library, FP64, FP32_BULK,
                    START_BDF1, START_GHOST, START_COPY, EXPORTED_SYMBOLS, field_energy_noalloc,
-                   num_schedules, Batch)
+                   num_schedules, Batch, fp64_fma_rate)
 
 __all__ = ["Solver", "SPFCError", "lib_path", "load_library", "FP64", "FP32_BULK",
            "START_BDF1", "START_GHOST", "START_COPY", "EXPORTED_SYMBOLS", "field_energy_noalloc",
-           "num_schedules", "Batch"]
+           "num_schedules", "Batch", "fp64_fma_rate"]

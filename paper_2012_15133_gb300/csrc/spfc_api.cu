@@ -35,13 +35,12 @@ static int fail(spfc_t h, int code, const std::string& msg) {
   return code;
 }
 
-// Default launch schedule per grid: the fastest measured on GB300 (flushed
-// plus L2-resident step time); the float64 path is bound by its arithmetic
-// and prefers the shapes with the most threads (schedule 5: 4 values per lane).
+// Default launch schedule per grid: the persistent step (the last schedule
+// of every 2D grid: 6 from N = 128, 1 below), the fastest measured on GB300.
 static int default_schedule(int d, int n, int precision) {
+  (void)precision;
   if (d != 2) return 0;
-  if (precision == SPFC_FP64) return n == 512 ? 1 : ((n == 128 || n == 256) ? 5 : 0);
-  return (n == 128 || n == 256) ? 2 : 0;
+  return n >= 128 ? 6 : 1;
 }
 
 static int wrap(spfc_t h, int rc) {
@@ -165,8 +164,8 @@ int spfc_sav_scalars(spfc_t h, double* out, int nout) {
   spfc::SavScal sc;
   int rc = h->s->scalars(&sc);
   if (rc) return wrap(h, rc);
-  const double v[6] = {sc.r1, sc.r0, sc.xi, sc.gamma, sc.E1, (double)sc.nsteps};
-  for (int i = 0; i < nout && i < 6; ++i) out[i] = v[i];
+  const double v[10] = {sc.r1, sc.r0, sc.xi, sc.gamma, sc.E1, (double)sc.nsteps, sc.eta, sc.theta, sc.denom, sc.LHS};
+  for (int i = 0; i < nout && i < 10; ++i) out[i] = v[i];
   return SPFC_OK;
 }
 
@@ -205,7 +204,7 @@ int spfc_dt_change(spfc_t h, double dt_new) {
 // float64 {kf0, kf1, kf2, dt, a, beta, A, gamma3}, then the raw state blob
 // (scalar record and both spectral levels), so that a resumed run is
 // bit-identical.
-static const char kMagic[8] = {'S', 'P', 'F', 'C', 'C', 'K', 'P', '4'};
+static const char kMagic[8] = {'S', 'P', 'F', 'C', 'C', 'K', 'P', '5'};
 
 int spfc_save(spfc_t h, const char* path) {
   if (!h || !path) return fail(h, SPFC_EINVAL, "NULL argument");
@@ -266,7 +265,7 @@ int spfc_set_timing(spfc_t h, int on) {
 int spfc_kernel_times(spfc_t h, int max, const char** names, int64_t* launches, double* ms) {
   if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
   static const char* kNames[] = {"col_inv",  "row",    "col_fwd", "col_fused", "y_fwd",
-                                 "z_fwd",    "scalar", "z_inv",   "y_inv",     "col_inv+col_fwd"};
+                                 "z_fwd",    "scalar", "z_inv",   "y_inv",     "col_inv+col_fwd", "step"};
   spfc::KernelTimes kt;
   int rc = h->s->kernel_times(&kt);
   if (rc) return wrap(h, rc);

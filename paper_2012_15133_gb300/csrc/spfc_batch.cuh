@@ -101,20 +101,18 @@ k2b_col_inv_g3(BatchView<R> B, const C_t<R>* __restrict__ tw) {
 template <typename R>
 __global__ void __launch_bounds__(256)
 k2b_scalar(BatchView<R> B) {
-  using RD = Red<R>;
-  using ST = typename RD::store;
-  __shared__ typename RD::acc red5[5][32];
-  __shared__ typename RD::acc qres[5];
+  __shared__ double red5[5][32];
+  __shared__ double qres[5];
   const int r = blockIdx.x;
   SavScal* sc = B.sc + r;
   if (sc->status != DEV_OK) return;
-  const ST* pe = reinterpret_cast<const ST*>(B.partE + (size_t)r * 2 * B.nE);
-  const ST* pg = reinterpret_cast<const ST*>(B.partG + (size_t)r * 3 * B.nG);
-  const ST* arr[5] = {pe, pe + B.nE, pg, pg + B.nG, pg + 2 * B.nG};
+  const double* pe = B.partE + (size_t)r * 2 * B.nE;
+  const double* pg = B.partG + (size_t)r * 3 * B.nG;
+  const double* arr[5] = {pe, pe + B.nE, pg, pg + B.nG, pg + 2 * B.nG};
   const int cnt[5] = {B.nE, B.nE, B.nG, B.nG, B.nG};
-  block_red_arrays<R, 5>(arr, cnt, qres, red5);
+  block_sum_arrays<5>(arr, cnt, qres, red5);
   if (threadIdx.x == 0) {
-    const SolveOut<R> o = sav_solve(B.P[r], qres, false, RIn<R>(sc));
+    const SolveOut o = sav_solve(B.P[r], qres, false, RIn(sc));
     sav_commit(sc, o, 1 - sc->p, PEND_NONE);
   }
 }
@@ -274,7 +272,6 @@ class BatchClass final : public BatchClassBase {
 
   int run_scalars(int local, SavScal* out) override {
     SPFC_CK(cudaMemcpy(out, v_.sc + local, sizeof(SavScal), cudaMemcpyDeviceToHost));
-    if (sizeof(R) == 4) scal_from_ff(out);
     return out->status;
   }
 

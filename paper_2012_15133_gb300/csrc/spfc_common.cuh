@@ -85,6 +85,16 @@ template <typename C, int RAD, bool INV> __device__ __forceinline__ void dft_r(C
 // Largest twiddle table length; table[m] = exp(-2 pi i m / TW_N).
 constexpr int TW_N = 512;
 
+// Where the FFT stages read the twiddle table from: global memory through the
+// read-only path (TwGlobal, the default), or a copy in shared memory
+// (TwShared; a generic load, valid for a shared-memory pointer).
+struct TwGlobal {
+  template <typename C> __device__ __forceinline__ static C ld(const C* p) { return __ldg(p); }
+};
+struct TwShared {
+  template <typename C> __device__ __forceinline__ static C ld(const C* p) { return *p; }
+};
+
 // Shared-memory position of element i of an FFT sequence: one pad slot every
 // 8 elements spreads the strided writes of the first radix-8 stage over the
 // banks. A sequence of length N occupies sp_len(N) slots.
@@ -141,7 +151,7 @@ __device__ __forceinline__ void stage_load(C* v, const C* s, int es, int lane) {
     for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sp(lane + m * T + r * STRIDE) * es];
 }
 
-template <typename C, int N, int E, bool INV, int NS, int RAD>
+template <typename C, int N, int E, bool INV, int NS, int RAD, class TWL = TwGlobal>
 __device__ __forceinline__ void stage_compute(C* v, int lane, const C* __restrict__ tw) {
   constexpr int T = fft_shape<N, E>::T, NB = E / RAD, TWS = TW_N / (NS * RAD);
 #pragma unroll
@@ -150,7 +160,7 @@ __device__ __forceinline__ void stage_compute(C* v, int lane, const C* __restric
     if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = __ldg(tw + r * k * TWS);
+        C w = TWL::template ld<C>(tw + r * k * TWS);
         if (INV) w.y = -w.y;
         v[m * RAD + r] = cmul(v[m * RAD + r], w);
       }
@@ -237,7 +247,7 @@ __device__ __forceinline__ void fft_regs(C* v, C* s, int es, int lane, const C* 
 // fft_regs for NSEQ sequences of one lane at once (sequence q in shared
 // memory at s + q * qs), sharing the barriers; BS forces block-wide barriers
 // (for lanes of one sequence spread over several warps).
-template <typename C, int N, int E, bool INV, int NSEQ, bool BS, int NS, int NSL>
+template <typename C, int N, int E, bool INV, int NSEQ, bool BS, int NS, int NSL, class TWL = TwGlobal>
 __device__ __forceinline__ void fft_mid_multi(C* s, int qs, int es, int lane, const C* __restrict__ tw) {
   if constexpr (NS < NSL) {
     constexpr int RAD = stage_rad<N, E, NS>::value;
@@ -247,15 +257,15 @@ __device__ __forceinline__ void fft_mid_multi(C* s, int qs, int es, int lane, co
     fft_sync<N, E, BS>();
 #pragma unroll
     for (int q = 0; q < NSEQ; ++q) {
-      stage_compute<C, N, E, INV, NS, RAD>(v[q], lane, tw);
+      stage_compute<C, N, E, INV, NS, RAD, TWL>(v[q], lane, tw);
       stage_store<C, N, E, NS, RAD>(v[q], s + q * qs, es, lane);
     }
     fft_sync<N, E, BS>();
-    fft_mid_multi<C, N, E, INV, NSEQ, BS, NS * RAD, NSL>(s, qs, es, lane, tw);
+    fft_mid_multi<C, N, E, INV, NSEQ, BS, NS * RAD, NSL, TWL>(s, qs, es, lane, tw);
   }
 }
 
-template <typename C, int N, int E, bool INV, int NSEQ, bool BS>
+template <typename C, int N, int E, bool INV, int NSEQ, bool BS, class TWL = TwGlobal>
 __device__ __forceinline__ void fft_regs_multi(C (*v)[E], C* s, int qs, int es, int lane,
                                                const C* __restrict__ tw) {
   constexpr int R1 = stage_rad<N, E, 1>::value, NB1 = E / R1;
@@ -270,16 +280,16 @@ __device__ __forceinline__ void fft_regs_multi(C (*v)[E], C* s, int qs, int es, 
     for (int m = 0; m < NB1; ++m)
 #pragma unroll
       for (int r = 0; r < R1; ++r) w[m * R1 + r] = v[q][m + r * NB1];
-    stage_compute<C, N, E, INV, 1, R1>(w, lane, tw);
+    stage_compute<C, N, E, INV, 1, R1, TWL>(w, lane, tw);
     stage_store<C, N, E, 1, R1>(w, s + q * qs, es, lane);
   }
   fft_sync<N, E, BS>();
-  fft_mid_multi<C, N, E, INV, NSEQ, BS, R1, NSL>(s, qs, es, lane, tw);
+  fft_mid_multi<C, N, E, INV, NSEQ, BS, R1, NSL, TWL>(s, qs, es, lane, tw);
 #pragma unroll
   for (int q = 0; q < NSEQ; ++q) {
     C w[E];
     stage_load<C, N, E, RL>(w, s + q * qs, es, lane);
-    stage_compute<C, N, E, INV, NSL, RL>(w, lane, tw);
+    stage_compute<C, N, E, INV, NSL, RL, TWL>(w, lane, tw);
 #pragma unroll
     for (int m = 0; m < NBL; ++m)
 #pragma unroll
@@ -350,17 +360,21 @@ __device__ __forceinline__ double warp_sum_array(const double* a, int n, int lan
   return warp_sum(t);
 }
 
-// Accumulators of the SAV inner products and of E_1.
-// float64 path: plain float64 sums.
-// float32-bulk path: float-float sums (hi + lo, Knuth's two-sum on every
-// addition), which carry the exact sum of the float32 products to ~2^-48
-// relative, i.e. what a float64 accumulator of those products gives, while
-// running on the float32 pipes (float64 issue is scarce on this GPU).
+// Accumulators of the SAV inner products and of E_1 (the precision split of
+// the FP32-bulk path keeps these sums and everything derived from them in
+// float64).
+// Per thread and per block, the float64 path adds in float64. The
+// float32-bulk path adds its float32 products in float-float (hi + lo,
+// Knuth's two-sum on every addition): the exact sum of a thread's and then a
+// block's float32 products to ~2^-48 relative, on the float32 pipes (float64
+// issue is scarce on this GPU). Each block's result is stored as a float64
+// (hi + lo is exact in float64: two 24-bit significands within 48 bits), and
+// everything after that -- the sums over blocks, E_1, S, gamma, eta, theta,
+// rho, LHS and r -- is float64 on both paths.
 template <typename R> struct Red;
 
 template <> struct Red<double> {
   using acc = double;
-  using store = double;
   __device__ static acc zero() { return 0.0; }
   __device__ static acc add(acc a, double x) { return a + x; }
   __device__ static acc add2(acc a, acc b) { return a + b; }
@@ -370,7 +384,6 @@ template <> struct Red<double> {
 
 template <> struct Red<float> {
   using acc = float2;   // (hi, lo)
-  using store = float2;
   __device__ static acc zero() { return make_float2(0.f, 0.f); }
   __device__ static acc add(acc a, float x) {
     const float s = __fadd_rn(a.x, x);
@@ -451,38 +464,17 @@ __device__ __forceinline__ void block_red_multi(typename Red<R>::acc* v, typenam
   }
 }
 
-// Sum of n stored accumulators by one warp, fixed order; returned as double
-// to every lane. L1 is bypassed (values written by other blocks).
-template <typename R>
-__device__ __forceinline__ double warp_red_array(const typename Red<R>::store* a, int n, int lane) {
-  using ST = typename Red<R>::store;
-  typename Red<R>::acc t = Red<R>::zero();
-  // batches of 8 independent loads per lane, so that the L2 round trips overlap
-  for (int base = 0; base < n; base += 256) {
-    ST v[8];
+// Grid-level reduction of NQ float64 partial-sum arrays by a whole block,
+// in float64, all NQ chains interleaved: thread t sums entries t,
+// t + blockDim, .. of each array (L1 bypassed: the entries were written by
+// other blocks of the grid), then a shuffle tree and a shared-memory tree.
+// Fixed order; results in thread 0.
+template <int NQ>
+__device__ __forceinline__ void block_sum_arrays(const double* const* arr, const int* n, double* out,
+                                                 double (*scratch)[32]) {
+  double a[NQ];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = base + lane + 32 * u;
-      v[u] = (i < n) ? __ldcg(a + i) : Red<R>::zero();
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t = Red<R>::add2(t, v[u]);
-  }
-  return Red<R>::to_double(warp_red<R>(t));
-}
-
-// Grid-level reduction of NQ partial-sum arrays by a whole block, all NQ
-// chains interleaved: thread t sums entries t, t + blockDim, .. of each array
-// (L1 bypassed: the entries were written by other blocks of the grid), then a
-// shuffle tree and a shared-memory tree. Fixed order; results in thread 0.
-template <typename R, int NQ>
-__device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* const* arr, const int* n,
-                                                 typename Red<R>::acc* out,
-                                                 typename Red<R>::acc (*scratch)[32]) {
-  using RD = Red<R>;
-  typename RD::acc a[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) a[q] = RD::zero();
+  for (int q = 0; q < NQ; ++q) a[q] = 0.0;
   int nmax = 0;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) nmax = n[q] > nmax ? n[q] : nmax;
@@ -490,22 +482,22 @@ __device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* c
   // additions), so that a grid of up to 2 x blockDim.x blocks needs one L2
   // round trip, not two
   for (int base = 0; base < nmax; base += 2 * blockDim.x) {
-    typename RD::store v[2][NQ];
+    double v[2][NQ];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int i = base + u * blockDim.x + threadIdx.x;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) v[u][q] = (i < n[q]) ? __ldcg(arr[q] + i) : RD::zero();
+      for (int q = 0; q < NQ; ++q) v[u][q] = (i < n[q]) ? __ldcg(arr[q] + i) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], v[u][q]);
+      for (int q = 0; q < NQ; ++q) a[q] += v[u][q];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], RD::shfl(a[q], o));
+    for (int q = 0; q < NQ; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
@@ -516,36 +508,19 @@ __device__ __forceinline__ void block_red_arrays(const typename Red<R>::store* c
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) a[q] = (lane < nw) ? scratch[q][lane] : RD::zero();
+    for (int q = 0; q < NQ; ++q) a[q] = (lane < nw) ? scratch[q][lane] : 0.0;
     const int p2 = pow2_ceil(nw);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       if (o >= p2) continue;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) a[q] = RD::add2(a[q], RD::shfl(a[q], o));
+      for (int q = 0; q < NQ; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
     }
     if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) out[q] = a[q];
     }
   }
-}
-
-// Sum of n stored float-float accumulators by one warp, fixed order, kept in
-// float-float (every lane gets the result).
-__device__ __forceinline__ float2 warp_red_array_ff(const float2* a, int n, int lane) {
-  float2 t = Red<float>::zero();
-  for (int base = 0; base < n; base += 256) {
-    float2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = base + lane + 32 * u;
-      v[u] = (i < n) ? __ldcg(a + i) : Red<float>::zero();
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t = Red<float>::add2(t, v[u]);
-  }
-  return warp_red<float>(t);
 }
 
 }  // namespace spfc

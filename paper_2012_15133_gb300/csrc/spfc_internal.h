@@ -64,37 +64,6 @@ inline void fill_float_params(Params* P) {
   P->g3b = (P->beta > 0.0) ? P->g3 / P->beta : 0.0;
   P->g3_f = (float)P->g3;
   P->g3b_f = (float)P->g3b;
-  auto split = [](double x, float* o) {
-    o[0] = (float)x;
-    o[1] = (float)(x - (double)o[0]);
-  };
-  split(P->hd, P->hd_ff);
-  split(P->vol, P->vol_ff);
-  split(P->C * P->vol, P->Cvol_ff);
-  split(0.25 * P->beta, P->qbeta_ff);
-  split(P->dt, P->dt_ff);
-}
-
-// float-float pair -> double, and back
-inline double ff_to_double(const float* v) { return (double)v[0] + (double)v[1]; }
-inline void double_to_ff(double x, float* o) {
-  o[0] = (float)x;
-  o[1] = (float)(x - (double)o[0]);
-}
-
-// Fill the float64 fields of a scalar record from its float-float fields
-// (float32-bulk path).
-inline void scal_from_ff(SavScal* h) {
-  h->r1 = ff_to_double(h->r1f);
-  h->r0 = ff_to_double(h->r0f);
-  h->E1 = ff_to_double(h->E1f);
-  h->S = ff_to_double(h->Sf);
-  h->gamma = ff_to_double(h->gammaf);
-  h->eta = ff_to_double(h->etaf);
-  h->theta = ff_to_double(h->thetaf);
-  h->denom = ff_to_double(h->denomf);
-  h->LHS = ff_to_double(h->LHSf);
-  h->xi = ff_to_double(h->xif);
 }
 
 // Factories (one translation unit per precision); return nullptr and set err on failure.

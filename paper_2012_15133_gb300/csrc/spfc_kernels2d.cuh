@@ -25,7 +25,6 @@
 #pragma once
 
 #include "spfc_common.cuh"
-#include "spfc_ff.cuh"
 #include "spfc_state.h"
 
 namespace spfc {
@@ -382,9 +381,8 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
     typename RD::acc t21[2] = {acc2, acc1};
     block_red_multi<R, 2>(t21, red2);
     if (threadIdx.x == 0) {
-      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
-      ps[blockIdx.x] = t21[0];
-      ps[gridDim.x + blockIdx.x] = t21[1];
+      part[blockIdx.x] = RD::to_double(t21[0]);
+      part[gridDim.x + blockIdx.x] = RD::to_double(t21[1]);
     }
   } else {
     // Z = G_x + i G_y over the full x-spectrum, element k = lane + i T loaded
@@ -437,9 +435,8 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
     typename RD::acc t21[2] = {acc2, acc1};
     block_red_multi<R, 2>(t21, red2);
     if (threadIdx.x == 0) {
-      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
-      ps[blockIdx.x] = t21[0];
-      ps[gridDim.x + blockIdx.x] = t21[1];
+      part[blockIdx.x] = RD::to_double(t21[0]);
+      part[gridDim.x + blockIdx.x] = RD::to_double(t21[1]);
     }
   }
 }
@@ -468,137 +465,85 @@ k2d_row_g3(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, C_t
 // half-spectrum sums of gamma, eta, theta without |Omega|} and r of the two
 // current levels; BDF1 is the first-order start (r^0 = sqrt(E_1(phi^0))).
 // sav_solve computes, sav_commit writes the record.
-template <typename R> struct SolveOut;
-template <> struct SolveOut<double> {
+struct SolveOut {
   double E1, S, gamma, eta, theta, denom, LHS, xi, r_new, r_prev_new, alpha;
   bool ok;
 };
-template <> struct SolveOut<float> {
-  ff E1, S, gamma, eta, theta, denom, LHS, xi, r_new, r_prev_new;
-  float alpha;
-  bool ok;
-};
-template <typename R> struct RIn;
-template <> struct RIn<double> {
+// r of the two current levels (float64 on both paths)
+struct RIn {
   double r1, r0;
   __device__ explicit RIn(const SavScal* sc) : r1(sc->r1), r0(sc->r0) {}
   __device__ RIn() : r1(0), r0(0) {}
 };
-__device__ __forceinline__ ff ffp(const float* v) { return ff{v[0], v[1]}; }
-__device__ __forceinline__ void ffs(float* o, ff x) { o[0] = x.hi; o[1] = x.lo; }
-template <> struct RIn<float> {
-  ff r1, r0;
-  __device__ explicit RIn(const SavScal* sc) : r1(ffp(sc->r1f)), r0(ffp(sc->r0f)) {}
-  __device__ RIn() : r1{0.f, 0.f}, r0{0.f, 0.f} {}
+
+// The solve in two parts. Everything that needs only the row pass's sums
+// (q[0], q[1]) and r^n, r^{n-1} -- E_1, S = sqrt(E_1), 1/S and the
+// coefficients below -- is formed first (it can overlap the gamma/eta/theta
+// reduction); what is left once gamma, eta, theta arrive is a chain of five
+// multiply-adds and one division:
+//   denom = 1 - (dt/(2 E_1)) gamma,   rho = rb - ct theta,
+//   LHS = ((dt/S) rho gamma + eta) / denom,   r^{n+1} = rho + LHS/(2S),
+// with rb = (4 r^n - r^{n-1})/3 and ct = 1/(3S) (eqs. solver-2 and solver-4),
+// or rb = S = r^0 and ct = 1/(2S) for the first-order start.
+struct SolvePre {
+  double E1, S, iS;
+  double dt_iS;       // dt / S
+  double h;           // dt / (2 E_1)
+  double rb, ct;      // rho = rb - ct theta
+  double r_prev_new;  // r^n, the new level's predecessor
 };
 
-// The solve in two parts: E_1, S = sqrt(E_1) and 1/S need only the row
-// pass's sums (q[0], q[1]); the rest needs gamma, eta, theta (qg[0..2]).
-template <typename R> struct SolvePre;
-template <> struct SolvePre<double> { double E1, S, iS; };
-template <> struct SolvePre<float> { ff E1, S, iS; };
-
-// float64 path: float64 scalar algebra, one square root and two divisions.
-__device__ inline SolvePre<double> sav_solve_pre(const Params& P, const double* q) {
-  SolvePre<double> o;
+// float64 scalar algebra (both paths).
+__device__ inline SolvePre sav_solve_pre(const Params& P, const double* q, bool bdf1, const RIn& rin) {
+  SolvePre o;
   o.E1 = P.hd * (0.25 * P.beta * q[0] - q[1]) + P.C * P.vol;
   o.S = sqrt(o.E1);
   o.iS = 1.0 / o.S;
+  o.dt_iS = P.dt * o.iS;
+  o.h = 0.5 * P.dt * (o.iS * o.iS);
+  if (bdf1) {
+    o.rb = o.S;
+    o.ct = 0.5 * o.iS;
+    o.r_prev_new = o.S;
+  } else {
+    o.rb = (4.0 * rin.r1 - rin.r0) * (1.0 / 3.0);
+    o.ct = o.iS * (1.0 / 3.0);
+    o.r_prev_new = rin.r1;
+  }
   return o;
 }
 
-__device__ inline SolveOut<double> sav_solve_post(const Params& P, const SolvePre<double>& pre, const double* qg,
-                                                  bool bdf1, const RIn<double>& rin) {
-  SolveOut<double> o;
-  const double gs = qg[0], es = qg[1], ts = qg[2];
+__device__ inline SolveOut sav_solve_post(const Params& P, const SolvePre& pre, const double* qg) {
+  SolveOut o;
   o.E1 = pre.E1;
   o.S = pre.S;
-  const double iS = pre.iS;
-  o.gamma = P.vol * gs; o.eta = P.vol * es; o.theta = P.vol * ts;
-  const double dt = P.dt;
-  o.denom = 1.0 - 0.5 * dt * o.gamma * (iS * iS);
-  double rho;
-  if (bdf1) {
-    rho = o.S - 0.5 * o.theta * iS;
-    o.r_prev_new = o.S;
-  } else {
-    rho = (4.0 * rin.r1 - rin.r0 - o.theta * iS) * (1.0 / 3.0);
-    o.r_prev_new = rin.r1;
-  }
-  o.LHS = (dt * rho * o.gamma * iS + o.eta) / o.denom;
-  o.r_new = rho + 0.5 * o.LHS * iS;
-  o.xi = o.r_new * iS;
-  o.alpha = dt * o.r_new * iS;
+  o.gamma = P.vol * qg[0]; o.eta = P.vol * qg[1]; o.theta = P.vol * qg[2];
+  o.denom = fma(-pre.h, o.gamma, 1.0);
+  const double rho = fma(-pre.ct, o.theta, pre.rb);
+  o.LHS = fma(pre.dt_iS * rho, o.gamma, o.eta) / o.denom;
+  o.r_new = fma(0.5 * pre.iS, o.LHS, rho);
+  o.r_prev_new = pre.r_prev_new;
+  o.xi = o.r_new * pre.iS;
+  o.alpha = pre.dt_iS * o.r_new;
   o.ok = isfinite(o.E1) && o.E1 > 0.0 && isfinite(o.gamma) && isfinite(o.eta) && isfinite(o.theta) &&
          o.denom > 0.0 && isfinite(o.r_new);
   return o;
 }
 
-__device__ inline SolveOut<double> sav_solve(const Params& P, const double* q, bool bdf1, const RIn<double>& rin) {
-  return sav_solve_post(P, sav_solve_pre(P, q), q + 2, bdf1, rin);
+__device__ inline SolveOut sav_solve(const Params& P, const double* q, bool bdf1, const RIn& rin) {
+  return sav_solve_post(P, sav_solve_pre(P, q, bdf1, rin), q + 2);
 }
 
-// float32-bulk path: the same algebra in float-float (float32 pipes; about
-// 48 significant bits, float64-class for these well-conditioned formulas).
-__device__ inline SolvePre<float> sav_solve_pre(const Params& P, const float2* q) {
-  SolvePre<float> o;
-  const ff s2{q[0].x, q[0].y}, s1{q[1].x, q[1].y};
-  o.E1 = ff_add(ff_mul(ffp(P.hd_ff), ff_sub(ff_mul(ffp(P.qbeta_ff), s2), s1)), ffp(P.Cvol_ff));
-  o.S = ff_sqrt(o.E1);
-  o.iS = ff_div(ff_make(1.f), o.S);
-  return o;
-}
-
-__device__ inline SolveOut<float> sav_solve_post(const Params& P, const SolvePre<float>& pre, const float2* qg,
-                                                 bool bdf1, const RIn<float>& rin) {
-  SolveOut<float> o;
-  const ff gs{qg[0].x, qg[0].y}, es{qg[1].x, qg[1].y}, ts{qg[2].x, qg[2].y};
-  const ff vol = ffp(P.vol_ff), dt = ffp(P.dt_ff);
-  o.E1 = pre.E1;
-  o.S = pre.S;
-  const ff iS = pre.iS;
-  o.gamma = ff_mul(vol, gs); o.eta = ff_mul(vol, es); o.theta = ff_mul(vol, ts);
-  o.denom = ff_sub(ff_make(1.f), ff_mulf(ff_mul(ff_mul(dt, o.gamma), ff_mul(iS, iS)), 0.5f));
-  ff rho;
-  if (bdf1) {
-    rho = ff_sub(o.S, ff_mulf(ff_mul(o.theta, iS), 0.5f));
-    o.r_prev_new = o.S;
-  } else {
-    rho = ff_div(ff_sub(ff_sub(ff_mulf(rin.r1, 4.f), rin.r0), ff_mul(o.theta, iS)), ff_make(3.f));
-    o.r_prev_new = rin.r1;
-  }
-  o.LHS = ff_div(ff_add(ff_mul(ff_mul(ff_mul(dt, rho), o.gamma), iS), o.eta), o.denom);
-  o.r_new = ff_add(rho, ff_mulf(ff_mul(o.LHS, iS), 0.5f));
-  o.xi = ff_mul(o.r_new, iS);
-  o.alpha = ff_mul(ff_mul(dt, o.r_new), iS).hi;
-  o.ok = ff_isfinite(o.E1) && o.E1.hi > 0.f && ff_isfinite(o.gamma) && ff_isfinite(o.eta) &&
-         ff_isfinite(o.theta) && o.denom.hi > 0.f && ff_isfinite(o.r_new);
-  return o;
-}
-
-__device__ inline SolveOut<float> sav_solve(const Params& P, const float2* q, bool bdf1, const RIn<float>& rin) {
-  return sav_solve_post(P, sav_solve_pre(P, q), q + 2, bdf1, rin);
-}
-
-// Write a solve into the record: r shifts, p and pending as given.
-__device__ inline void sav_commit(SavScal* sc, const SolveOut<double>& o, int p_new, int pending) {
+// Write a solve into the record: r shifts, p and pending as given; alpha also
+// rounded to float32 for the float32-bulk kernels.
+__device__ inline void sav_commit(SavScal* sc, const SolveOut& o, int p_new, int pending) {
   sc->E1 = o.E1; sc->S = o.S; sc->gamma = o.gamma; sc->eta = o.eta; sc->theta = o.theta;
   sc->denom = o.denom; sc->LHS = o.LHS; sc->xi = o.xi;
   if (!o.ok) { sc->status = DEV_NONFINITE; return; }
   sc->r0 = o.r_prev_new;
   sc->r1 = o.r_new;
   sc->alpha = o.alpha;
-  sc->p = p_new;
-  sc->pending = pending;
-  sc->nsteps += 1;
-}
-__device__ inline void sav_commit(SavScal* sc, const SolveOut<float>& o, int p_new, int pending) {
-  ffs(sc->E1f, o.E1); ffs(sc->Sf, o.S); ffs(sc->gammaf, o.gamma); ffs(sc->etaf, o.eta); ffs(sc->thetaf, o.theta);
-  ffs(sc->denomf, o.denom); ffs(sc->LHSf, o.LHS); ffs(sc->xif, o.xi);
-  if (!o.ok) { sc->status = DEV_NONFINITE; return; }
-  ffs(sc->r0f, o.r_prev_new);
-  ffs(sc->r1f, o.r_new);
-  sc->alpha_f = o.alpha;
+  sc->alpha_f = (float)o.alpha;
   sc->p = p_new;
   sc->pending = pending;
   sc->nsteps += 1;
@@ -606,10 +551,8 @@ __device__ inline void sav_commit(SavScal* sc, const SolveOut<float>& o, int p_n
 
 // Lazy-update form used by the separate forward column pass: newest holds
 // phi^n, the update stays pending (materialised later into slot 1-newest).
-template <typename R>
-__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const typename Red<R>::acc* q, bool bdf1,
-                                        int newest) {
-  const SolveOut<R> o = sav_solve(P, q, bdf1, RIn<R>(sc));
+__device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const double* q, bool bdf1, int newest) {
+  const SolveOut o = sav_solve(P, q, bdf1, RIn(sc));
   sav_commit(sc, o, newest, bdf1 ? PEND_BDF1 : PEND_BDF2);
 }
 
@@ -637,8 +580,8 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   __shared__ typename RD::acc red[32];
-  __shared__ typename RD::acc red5[5][32];
-  __shared__ typename RD::acc qres[5];
+  __shared__ double red5[5][32];
+  __shared__ double qres[5];
   __shared__ bool am_last;
 
   pdl_wait();
@@ -732,10 +675,9 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       const typename RD::acc te = block_red<R>(ae, red);
       const typename RD::acc tt = block_red<R>(at, red);
       if (threadIdx.x == 0) {
-        typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
-        ps[blockIdx.x] = tg;
-        ps[gridDim.x + blockIdx.x] = te;
-        ps[2 * gridDim.x + blockIdx.x] = tt;
+        partG[blockIdx.x] = RD::to_double(tg);
+        partG[gridDim.x + blockIdx.x] = RD::to_double(te);
+        partG[2 * gridDim.x + blockIdx.x] = RD::to_double(tt);
         if (MODE != CF_PART) {
           __threadfence();
           const unsigned prev = atomicAdd(counter, 1u);
@@ -747,14 +689,11 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       __syncthreads();
       if (am_last) {
         __threadfence();
-        using ST = typename RD::store;
-        const ST* pe = reinterpret_cast<const ST*>(partE);
-        const ST* pg = reinterpret_cast<const ST*>(partG);
-        const ST* arr[5] = {pe, pe + nE, pg, pg + gridDim.x, pg + 2 * gridDim.x};
+        const double* arr[5] = {partE, partE + nE, partG, partG + gridDim.x, partG + 2 * gridDim.x};
         const int cnt[5] = {nE, nE, (int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
-        block_red_arrays<R, 5>(arr, cnt, qres, red5);
+        block_sum_arrays<5>(arr, cnt, qres, red5);
         if (threadIdx.x == 0) {
-          sav_scalar_solve<R>(P, sc, qres, MODE == CF_BDF1, newest);
+          sav_scalar_solve(P, sc, qres, MODE == CF_BDF1, newest);
           *counter = 0u;
         }
       }
@@ -824,8 +763,9 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   static_assert(NTH % 32 == 0, "tile must fill whole warps");
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ typename RD::acc red5[5][32];
-  __shared__ typename RD::acc qres[5];
+  __shared__ typename RD::acc redb[3][32];
+  __shared__ double red5[5][32];
+  __shared__ double qres[5];
   __shared__ int bar_ok;
 
   const int lane = threadIdx.x / CT, c = threadIdx.x % CT;
@@ -849,7 +789,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   if (sc->status != DEV_OK) return;
   const PC<R> pc(P);
   const int p = sc->p;  // phi^n in slot p, phi^{n-1} in slot 1-p (nothing pending)
-  const RIn<R> rin(sc);  // read before arriving at the barrier (block 0 rewrites them after it)
+  const RIn rin(sc);  // read before arriving at the barrier (block 0 rewrites them after it)
   C* scur = S.at(p);
   C* sold = S.at(1 - p);
 #pragma unroll
@@ -864,11 +804,9 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   // the row pass's E_1 sums (complete before this launch), reduced while the
   // loads above are in flight; the float64 zero modes for the update
   {
-    using ST = typename RD::store;
-    const ST* pe = reinterpret_cast<const ST*>(partE);
-    const ST* arr[2] = {pe, pe + nE};
+    const double* arr[2] = {partE, partE + nE};
     const int cnt[2] = {nE, nE};
-    block_red_arrays<R, 2>(arr, cnt, qres, red5);
+    block_sum_arrays<2>(arr, cnt, qres, red5);
   }
   double zm_n = 0.0, zm_o = 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -904,7 +842,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
     at = RD::add(at, w * nv);
   }
   typename RD::acc t3[3] = {ag, ae, at};
-  block_red_multi<R, 3>(t3, red5);
+  block_red_multi<R, 3>(t3, redb);
 
   // ---- grid barrier: publish the partial sums, arrive, wait for all blocks
   // (bounded; thread 0 takes E_1 and S meanwhile); then every block reduces
@@ -912,16 +850,15 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   // the scalar solve itself (identical results), and block 0 alone writes the
   // record. sync64[0] counts arrivals monotonically, so it never needs a
   // reset: this launch's target is the next multiple of the grid.
-  SolvePre<R> pre;
+  SolvePre pre;
   if (threadIdx.x == 0) {
-    typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
-    ps[blockIdx.x] = t3[0];
-    ps[gridDim.x + blockIdx.x] = t3[1];
-    ps[2 * gridDim.x + blockIdx.x] = t3[2];
+    partG[blockIdx.x] = RD::to_double(t3[0]);
+    partG[gridDim.x + blockIdx.x] = RD::to_double(t3[1]);
+    partG[2 * gridDim.x + blockIdx.x] = RD::to_double(t3[2]);
     __threadfence();
     const unsigned long long prev = atomicAdd(sync64, 1ull);
     const unsigned long long target = (prev / gridDim.x + 1ull) * gridDim.x;
-    pre = sav_solve_pre(P, qres);  // E_1, S, 1/S: overlaps the wait
+    pre = sav_solve_pre(P, qres, BDF1, rin);  // E_1, S, 1/S and the rest: overlaps the wait
     const bool ok = wait_counter(sync64, target, kSpinLimit);
     if (!ok) atomicExch(&sc->status, (int)DEV_TIMEOUT);
     __threadfence();
@@ -930,16 +867,14 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   __syncthreads();
   if (!bar_ok) return;
   {
-    using ST = typename RD::store;
-    const ST* pg = reinterpret_cast<const ST*>(partG);
-    const ST* arr[3] = {pg, pg + gridDim.x, pg + 2 * gridDim.x};
+    const double* arr[3] = {partG, partG + gridDim.x, partG + 2 * gridDim.x};
     const int cnt[3] = {(int)gridDim.x, (int)gridDim.x, (int)gridDim.x};
-    block_red_arrays<R, 3>(arr, cnt, qres + 2, red5);
+    block_sum_arrays<3>(arr, cnt, qres + 2, red5);
   }
   __shared__ R alpha_s;
   __shared__ int solve_ok;
   if (threadIdx.x == 0) {
-    const SolveOut<R> o = sav_solve_post(P, pre, qres + 2, BDF1, rin);
+    const SolveOut o = sav_solve_post(P, pre, qres + 2);
     alpha_s = (R)o.alpha;
     solve_ok = o.ok;
     if (blockIdx.x == 0) sav_commit(sc, o, 1 - p, PEND_NONE);
@@ -1114,24 +1049,8 @@ enum ScalarOp : int {
 };
 
 // One-warp scalar operations on the record.
-// r of the newest / previous level in the record's working representation
-template <typename R> __device__ __forceinline__ void set_r1(SavScal* sc, double v) {
-  sc->r1 = v;
-  if (sizeof(R) == 4) { sc->r1f[0] = (float)v; sc->r1f[1] = (float)(v - (double)sc->r1f[0]); }
-}
-template <typename R> __device__ __forceinline__ void set_r0(SavScal* sc, double v) {
-  sc->r0 = v;
-  if (sizeof(R) == 4) { sc->r0f[0] = (float)v; sc->r0f[1] = (float)(v - (double)sc->r0f[0]); }
-}
-template <typename R> __device__ __forceinline__ double get_r1(const SavScal* sc) {
-  return sizeof(R) == 4 ? (double)sc->r1f[0] + (double)sc->r1f[1] : sc->r1;
-}
-template <typename R> __device__ __forceinline__ double get_r0(const SavScal* sc) {
-  return sizeof(R) == 4 ? (double)sc->r0f[0] + (double)sc->r0f[1] : sc->r0;
-}
-
-// `a` holds E_1 partial sums (accumulators of precision R) for the ops that
-// need them, or float64 sums for SO_ZM_SLOT; `b` holds float64 norm partials.
+// `a` holds float64 partial sums (E_1 for the ops that need them, the field
+// for SO_ZM_SLOT); `b` holds float64 norm partials.
 template <typename R>
 __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a, int na, const double* b,
                             int nb, int arg, double x0, double x1) {
@@ -1144,7 +1063,7 @@ __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a
     return;
   }
   if (op == SO_SET_R) {
-    if (lane == 0) { set_r1<R>(sc, x0); set_r0<R>(sc, x1); }
+    if (lane == 0) { sc->r1 = x0; sc->r0 = x1; }
     return;
   }
   if (op == SO_ZM_SLOT) {
@@ -1152,14 +1071,13 @@ __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a
     if (lane == 0) sc->zm[arg == 0 ? sc->p : 1 - sc->p] = s / P.P;
     return;
   }
-  using ST = typename Red<R>::store;
-  const double s2 = warp_red_array<R>(reinterpret_cast<const ST*>(a), na, lane);
-  const double s1 = warp_red_array<R>(reinterpret_cast<const ST*>(a) + na, na, lane);
+  const double s2 = warp_sum_array(a, na, lane);
+  const double s1 = warp_sum_array(a + na, na, lane);
   if (op == SO_R_NEWEST || op == SO_R_PREV) {
     if (lane == 0) {
       const double E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
       if (!(isfinite(E1) && E1 > 0.0)) { sc->status = DEV_NONFINITE; return; }
-      if (op == SO_R_NEWEST) set_r1<R>(sc, sqrt(E1)); else set_r0<R>(sc, sqrt(E1));
+      if (op == SO_R_NEWEST) sc->r1 = sqrt(E1); else sc->r0 = sqrt(E1);
     }
     return;
   }
@@ -1176,7 +1094,7 @@ __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a
       const double Lpsi = P.vol * (n2 + P.a * zp * zp);     // ||L^{1/2} psi||^2
       const double Lphi = P.a * phi2 + lap2;
       const double grad4 = P.hd * s2, grad2 = P.hd * s1;
-      const double r1 = get_r1<R>(sc), r0 = get_r0<R>(sc);
+      const double r1 = sc->r1, r0 = sc->r0;
       sc->E_orig = 0.25 * P.beta * grad4 + 0.5 * P.a * phi2 - grad2 + 0.5 * lap2;
       sc->E_mod = 0.25 * (Lphi + Lpsi) + 0.5 * (r1 * r1 + (2.0 * r1 - r0) * (2.0 * r1 - r0));
       sc->E_breve = 0.5 * P.a * phi2 + 0.5 * lap2 + r1 * r1;

@@ -226,10 +226,9 @@ __device__ __forceinline__ void k3d_zfwd_body(const Params& P, Slots<R> S, const
       block_red_multi<R, 3>(acc, red3);
       if (threadIdx.x == 0) {
         const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-        typename RD::store* ps = reinterpret_cast<typename RD::store*>(partG);
-        ps[b] = acc[0];
-        ps[nb + b] = acc[1];
-        ps[2 * nb + b] = acc[2];
+        partG[b] = RD::to_double(acc[0]);
+        partG[nb + b] = RD::to_double(acc[1]);
+        partG[2 * nb + b] = RD::to_double(acc[2]);
       }
     }
   }
@@ -259,18 +258,14 @@ template <typename R>
 __global__ void __launch_bounds__(1024)
 k3d_scalar(const Params P, SavScal* __restrict__ sc, const double* __restrict__ partE, int nE,
            const double* __restrict__ partG, int nG, int bdf1) {
-  using RD = Red<R>;
-  using ST = typename RD::store;
-  __shared__ typename RD::acc red5[5][32];
-  __shared__ typename RD::acc qres[5];
+  __shared__ double red5[5][32];
+  __shared__ double qres[5];
   if (sc->status != DEV_OK) return;
-  const ST* pe = reinterpret_cast<const ST*>(partE);
-  const ST* pg = reinterpret_cast<const ST*>(partG);
-  const ST* arr[5] = {pe, pe + nE, pg, pg + nG, pg + 2 * nG};
+  const double* arr[5] = {partE, partE + nE, partG, partG + nG, partG + 2 * nG};
   const int cnt[5] = {nE, nE, nG, nG, nG};
-  block_red_arrays<R, 5>(arr, cnt, qres, red5);
+  block_sum_arrays<5>(arr, cnt, qres, red5);
   if (threadIdx.x == 0) {
-    const SolveOut<R> o = sav_solve(P, qres, bdf1 != 0, RIn<R>(sc));
+    const SolveOut o = sav_solve(P, qres, bdf1 != 0, RIn(sc));
     sav_commit(sc, o, 1 - sc->p, PEND_NONE);
   }
 }
@@ -554,9 +549,8 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
     }
     block_red_multi<R, 2>(acc, red2);
     if (threadIdx.x == 0) {
-      typename RD::store* ps = reinterpret_cast<typename RD::store*>(part);
-      ps[blockIdx.x] = acc[0];
-      ps[gridDim.x + blockIdx.x] = acc[1];
+      part[blockIdx.x] = RD::to_double(acc[0]);
+      part[gridDim.x + blockIdx.x] = RD::to_double(acc[1]);
     }
   }
 }

@@ -42,3 +42,62 @@ extern "C" int spfc_wait_selftest(unsigned long long target, long long polls, vo
   if (host == (int)spfc::DEV_TIMEOUT) return SPFC_ETIMEOUT;
   return host == (int)spfc::DEV_OK ? SPFC_OK : SPFC_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Measured float64 FMA rate of the device (the arithmetic roofline of the
+// float64 step): every thread runs kChains independent chains of `iters`
+// float64 fused multiply-adds (no dependence between chains, so the FP64
+// pipe, not latency, sets the time), on an SM-count multiple of blocks.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kChains = 8;
+
+__global__ void __launch_bounds__(256) k_dfma_rate(double* out, int iters, double a, double b) {
+  double x[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) x[j] = 1e-3 * threadIdx.x + j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) x[j] = fma(x[j], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+}  // namespace
+
+extern "C" int spfc_fp64_fma_rate(double* gflops, void* cuda_stream) {
+  if (!gflops) return SPFC_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SPFC_ECUDA;
+  const int threads = 256, blocks = 4 * nsm, iters = 4096;
+  double* out = nullptr;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) return SPFC_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+      k_dfma_rate<<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess || !(best > 0.f)) return SPFC_ECUDA;
+  const double flops = 2.0 * kChains * (double)iters * (double)blocks * threads;
+  *gflops = flops / (best * 1e-3) / 1e9;
+  return SPFC_OK;
+}

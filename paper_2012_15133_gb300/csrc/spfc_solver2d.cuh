@@ -11,6 +11,7 @@
 
 #include "spfc_internal.h"
 #include "spfc_kernels2d.cuh"
+#include "spfc_step2d_persist.cuh"
 
 namespace spfc {
 
@@ -40,8 +41,6 @@ template <int N, int SCHED = 0> struct Shape2D {
   static constexpr int CT = (SCHED == 1 || SCHED == 5) ? CT1 : ((SCHED == 3 || SCHED == 4) ? 4 : CT0);
   static constexpr int RPC0 = (128 / T > 1) ? 128 / T : 1;
   static constexpr int RPC = (RPC0 < N) ? RPC0 : N;
-  static_assert(sizeof(Red<float>::store) == sizeof(double) && sizeof(Red<double>::store) == sizeof(double),
-                "partial-sum buffers hold 8-byte entries");
   static_assert(N % RPC == 0 && (RPC * T) % 32 == 0 && (2 * CT * T) % 32 == 0 && (CT * T) % 32 == 0,
                 "tiles must divide N and fill warps");
 };
@@ -86,10 +85,19 @@ template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
   }
 }
 
+// The schedule whose steps run as one persistent cooperative kernel
+// (k2d_step_persist): the last index of every grid; its start-up and
+// diagnostics passes use schedule 0's tiles.
+constexpr int persist_schedule(int N) { return (N >= 128) ? 6 : 1; }
+// Steps per launch of the persistent kernel (a long run is a few launches).
+constexpr long long kPersistMaxSteps = 4096;
+
 template <typename R, int N, int SCHED = 0>
 class Solver2D final : public SolverBase {
   using C = C_t<R>;
-  using SH = Shape2D<N, SCHED>;
+  static constexpr bool PERSIST = (SCHED == persist_schedule(N));
+  using SH = Shape2D<N, PERSIST ? 0 : SCHED>;
+  using PS = PShape<R, N>;
   static constexpr int NH = N / 2 + 1;
   static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T, E = SH::E;
   static constexpr int GCOL = (NH + CT - 1) / CT;
@@ -131,6 +139,8 @@ class Solver2D final : public SolverBase {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc_, sizeof(SavScal));  // pinned: small fast reads
     if (e == cudaSuccess) e = al((void**)&counter_, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = al((void**)&sync64_, sizeof(unsigned long long));
+    if (e == cudaSuccess && PERSIST) e = al((void**)&sync64p_, sizeof(unsigned long long));
+    if (e == cudaSuccess && PERSIST) e = al((void**)&partP_, 5 * (size_t)PS::G * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
@@ -141,6 +151,7 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(counter_, 0, 4 * sizeof(unsigned)));
     SPFC_CK(cudaMemset(sync64_, 0, sizeof(unsigned long long)));
+    if (PERSIST) SPFC_CK(cudaMemset(sync64p_, 0, sizeof(unsigned long long)));
     SavScal z{};
     SPFC_CK(cudaMemcpy(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(S_.s[0], 0, sb));
@@ -171,6 +182,15 @@ class Solver2D final : public SolverBase {
         err = "the fused column pass does not fit co-resident on this GPU";
         return 3;
       }
+      if (PERSIST) {
+        SPFC_CK(set_smem(k2d_step_persist<R, N>, PS::smem_bytes()));
+        SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_step_persist<R, N>, PS::NT,
+                                                               PS::smem_bytes()));
+        if (per * nsm < PS::G) {
+          err = "the persistent step does not fit co-resident on this GPU";
+          return 3;
+        }
+      }
     }
     SPFC_CK(cudaStreamCreateWithFlags(&cap_st_, cudaStreamNonBlocking));
     return 0;
@@ -182,7 +202,7 @@ class Solver2D final : public SolverBase {
     for (auto ev : evpool_) cudaEventDestroy(ev);
     if (cap_st_) cudaStreamDestroy(cap_st_);
     void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W2_, real_, partE_, partG_, partN_, partS_, sc_,
-                    counter_, sync64_, tw_};
+                    counter_, sync64_, sync64p_, partP_, tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     if (hsc_) cudaFreeHost(hsc_);
@@ -315,6 +335,15 @@ class Solver2D final : public SolverBase {
       }
       return 0;
     }
+    if (PERSIST && !g3_on()) {  // one cooperative launch per chunk of steps
+      while (n > 0) {
+        const long long k = n < kPersistMaxSteps ? n : kPersistMaxSteps;
+        int rc = launch_persist((int)k);
+        if (rc) return rc;
+        n -= k;
+      }
+      return 0;
+    }
     int rc = ensure_graphs();
     if (rc) return rc;
     long long chunks = n / 16, rest = n % 16;
@@ -369,7 +398,6 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
     SavScal h = *hsc_;
-    if (sizeof(R) == 4) scal_from_ff(&h);
     if (h.status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
       return h.status;
@@ -403,6 +431,7 @@ class Solver2D final : public SolverBase {
     h.zm[1] = z1;
     drop_graphs();
     SPFC_CK(cudaStreamSynchronize(st_));
+    if (int rc = reset_barriers()) return rc;
     SPFC_CK(cudaMemcpy(S_.s[0], blob.data() + sizeof(SavScal), spec_bytes_, cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemcpy(S_.s[1], blob.data() + sizeof(SavScal) + spec_bytes_, spec_bytes_, cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemcpy(sc_, &h, sizeof(SavScal), cudaMemcpyHostToDevice));
@@ -425,9 +454,15 @@ class Solver2D final : public SolverBase {
     }
     trecs_.clear();
     evnext_ = 0;
-    kt->names = {"row", g3_on() ? "col_inv+col_fwd" : "col_fused"};
-    kt->launches.assign(tcount_, tcount_ + 2);
-    kt->ms.assign(tms_, tms_ + 2);
+    if (PERSIST && !g3_on()) {
+      kt->names = {"step"};
+      kt->launches.assign(tcount_, tcount_ + 1);
+      kt->ms.assign(tms_, tms_ + 1);
+    } else {
+      kt->names = {"row", g3_on() ? "col_inv+col_fwd" : "col_fused"};
+      kt->launches.assign(tcount_, tcount_ + 2);
+      kt->ms.assign(tms_, tms_ + 2);
+    }
     for (int i = 0; i < 3; ++i) { tcount_[i] = 0; tms_[i] = 0.0; }
     return 0;
   }
@@ -529,7 +564,6 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
     *h = *hsc_;
-    if (sizeof(R) == 4) scal_from_ff(h);
     if (h->status != DEV_OK) {
       err = "device status: non-finite value or infeasible SAV scalar system";
       return h->status;
@@ -567,6 +601,7 @@ class Solver2D final : public SolverBase {
     if (reset) {
       SavScal z{};
       SPFC_CK(cudaMemcpyAsync(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
+      reset_barriers();
       drop_graphs();
     }
     SPFC_CK(cudaMemcpyAsync(real_, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
@@ -602,6 +637,25 @@ class Solver2D final : public SolverBase {
     else
       SPFC_CK(launch_k(k2d_col_fused<R, N, E, CT, false>, GCOL, CT * T, smem_col(2), st_, false, true, P, S_,
                        W_[0], W_[1], partG_, partE_, nE_, sc_, sync64_, tw_));
+    return 0;
+  }
+
+  // The grid barriers count arrivals on monotone counters whose rounds are
+  // whole multiples of the grid; a launch that stopped inside a round (a
+  // latched failure) leaves a remainder, so a new start clears them.
+  int reset_barriers() {
+    SPFC_CK(cudaMemsetAsync(sync64_, 0, sizeof(unsigned long long), st_));
+    if (PERSIST) SPFC_CK(cudaMemsetAsync(sync64p_, 0, sizeof(unsigned long long), st_));
+    bar_rounds_ = 0;
+    return 0;
+  }
+
+  // nsteps BDF2 steps in one cooperative launch (W prepared, nothing pending)
+  int launch_persist(int nsteps) {
+    const unsigned long long base = bar_rounds_ * (unsigned long long)PS::G;
+    SPFC_CK(launch_k(k2d_step_persist<R, N>, PS::G, PS::NT, PS::smem_bytes(), st_, false, true, P, S_, W_[0],
+                     W_[1], partP_, partP_ + 2 * PS::G, sc_, sync64p_, base, tw_, nsteps));
+    bar_rounds_ += 3ull * (unsigned long long)nsteps - 1ull;  // the launch's barrier rounds
     return 0;
   }
 
@@ -662,6 +716,14 @@ class Solver2D final : public SolverBase {
       trecs_.push_back({1, e2, e3});
       return 0;
     }
+    if (PERSIST) {
+      if ((rc = ev(&e0)) || (rc = ev(&e1))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e0], st_));
+      if ((rc = launch_persist(1))) return rc;
+      SPFC_CK(cudaEventRecord(evpool_[e1], st_));
+      trecs_.push_back({0, e0, e1});
+      return 0;
+    }
     if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2))) return rc;
     SPFC_CK(cudaEventRecord(evpool_[e0], st_));
     if ((rc = launch_row(RW_NONLIN))) return rc;
@@ -686,6 +748,9 @@ class Solver2D final : public SolverBase {
   SavScal* hsc_ = nullptr;  // pinned host copy of the record
   unsigned* counter_ = nullptr;
   unsigned long long* sync64_ = nullptr;  // arrival counter of the fused pass's grid barrier
+  unsigned long long* sync64p_ = nullptr; // arrival counter of the persistent step's grid barriers
+  double* partP_ = nullptr;               // the persistent step's partial sums: E_1 [2][G], gamma/eta/theta [3][G]
+  unsigned long long bar_rounds_ = 0;     // barrier rounds the persistent launches issued since the last reset
   C* tw_ = nullptr;
   int gpw_ = 0, nE_ = 0, nG_ = 0;
   size_t spec_bytes_ = 0, total_ = 0;
@@ -702,8 +767,9 @@ class Solver2D final : public SolverBase {
   double tms_[3] = {0, 0, 0};
 };
 
-// Number of launch schedules compiled for a 2D grid size.
-inline int num_schedules_2d(int N) { return (N >= 128) ? 6 : 1; }
+// Number of launch schedules compiled for a 2D grid size: the tile shapes of
+// the two-kernel step (six from N = 128, one below) and the persistent step.
+inline int num_schedules_2d(int N) { return persist_schedule(N) + 1; }
 
 template <typename R, int N, int SCHED>
 SolverBase* new_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
@@ -729,6 +795,7 @@ SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int
     case 3: return new_solver_2d<R, N, 3>(P, st, status, err);
     case 4: return new_solver_2d<R, N, 4>(P, st, status, err);
     case 5: return new_solver_2d<R, N, 5>(P, st, status, err);
+    case 6: return new_solver_2d<R, N, 6>(P, st, status, err);
     default: return new_solver_2d<R, N, 0>(P, st, status, err);
   }
 }
@@ -753,9 +820,9 @@ SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int schedule, int* 
   }
   constexpr bool F64 = sizeof(R) == 8;
   switch (P.N) {
-    case 16: return new_solver_2d<R, 16, 0>(P, st, status, err);
-    case 32: return new_solver_2d<R, 32, 0>(P, st, status, err);
-    case 64: return new_solver_2d<R, 64, 0>(P, st, status, err);
+    case 16: return schedule ? new_solver_2d<R, 16, 1>(P, st, status, err) : new_solver_2d<R, 16, 0>(P, st, status, err);
+    case 32: return schedule ? new_solver_2d<R, 32, 1>(P, st, status, err) : new_solver_2d<R, 32, 0>(P, st, status, err);
+    case 64: return schedule ? new_solver_2d<R, 64, 1>(P, st, status, err) : new_solver_2d<R, 64, 0>(P, st, status, err);
     case 128:
       return make_solver_2d_n<R, 128>(P, st, schedule, status, err);
     case 256:

@@ -426,7 +426,6 @@ class Solver3D final : public SolverBase {
     SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
     SPFC_CK(cudaStreamSynchronize(st_));
     *h = *hsc_;
-    if (sizeof(R) == 4) scal_from_ff(h);
     if (h->status != DEV_OK) {
       err = "device status: non-finite value, infeasible SAV scalar system or timeout";
       return h->status;

@@ -23,8 +23,6 @@ struct Params {
   // float32 copies for the float32-bulk kernels (no float64 work per thread)
   float kf_f[3];
   float dt_f, a_f, beta_f, invP_f;
-  // float-float (hi, lo) copies for the float32-bulk scalar algebra
-  float hd_ff[2], vol_ff[2], Cvol_ff[2], qbeta_ff[2], dt_ff[2];
   // stabiliser of Sec. 5.2 (- A dt Delta_N (phi^{n+1} - phi^n)); A = 0: the scheme of Sec. 2
   double stab;    // A
   double sdt;     // A dt
@@ -50,7 +48,7 @@ enum DevStatus : int { DEV_OK = 0, DEV_NONFINITE = 4, DEV_TIMEOUT = 5 };
 // stored N_hat and is materialised by the next step's first kernel (or by an
 // explicit finalize), which also flips p.
 struct SavScal {
-  double r1, r0;        // r of the newest level and of the one before
+  double r1, r0;        // r of the newest level and of the one before (float64 on both paths)
   double alpha;         // dt r^{n+1} / sqrt(E1) of the pending update
   float alpha_f;        // the same, rounded to float32 (read by float32-bulk kernels)
   int pad0_;
@@ -61,11 +59,6 @@ struct SavScal {
   double E_orig, E_mod, E_breve;
   int p, pending, status, pad_;
   long long nsteps;
-  // float32-bulk path: the scalar algebra runs in float-float (hi, lo); these
-  // are its state (r) and diagnostics, converted to the float64 fields above
-  // by the host when read.
-  float r1f[2], r0f[2];
-  float E1f[2], Sf[2], gammaf[2], etaf[2], thetaf[2], denomf[2], LHSf[2], xif[2];
 };
 
 }  // namespace spfc

@@ -51,6 +51,7 @@ _SIGS = {
     "spfc_kernel_times": (_I, [_P, _I, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_int64), _DP]),
     "spfc_device_bytes": (ct.c_int64, [_P]),
     "spfc_wait_selftest": (_I, [ct.c_ulonglong, ct.c_longlong, _P]),
+    "spfc_fp64_fma_rate": (_I, [_DP, _P]),
     "spfc_destroy": (None, [_P]),
     "spfc_last_error": (ct.c_char_p, [_P]),
     "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
@@ -141,6 +142,19 @@ def field_energy_noalloc(phi, L, eps, beta, stream=None):
     if rc != 0:
         raise SPFCError(rc, lib.spfc_noalloc_last_error().decode())
     return out[0], out[1], out[2]
+
+
+def fp64_fma_rate(stream=None):
+    """Measured float64 FMA throughput of the current GPU in GFLOP/s (the
+    arithmetic roofline of the float64 step)."""
+    lib = load_library()
+    out = ct.c_double()
+    sp = _current_stream_ptr() if stream is None else ct.c_void_p(
+        stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = lib.spfc_fp64_fma_rate(ct.byref(out), sp)
+    if rc != 0:
+        raise SPFCError(rc, "FP64 FMA rate measurement failed")
+    return out.value
 
 
 def num_schedules(d, n):
@@ -237,10 +251,13 @@ class Solver:
         self._check(self._lib.spfc_mass(self._h, ct.byref(a), ct.byref(b)))
         return a.value, b.value
 
-    def sav_scalars(self):
-        out = (ct.c_double * 6)()
-        self._check(self._lib.spfc_sav_scalars(self._h, out, 6))
-        keys = ("r", "r_prev", "xi", "gamma", "E1", "nsteps")
+    def sav_scalars(self, full=False):
+        """r^n, r^{n-1}, xi, gamma, E_1, steps; with full=True also eta, theta,
+        the denominator 1 - dt gamma/(2 E_1) and LHS of the last solve."""
+        k = 10 if full else 6
+        out = (ct.c_double * k)()
+        self._check(self._lib.spfc_sav_scalars(self._h, out, k))
+        keys = ("r", "r_prev", "xi", "gamma", "E1", "nsteps", "eta", "theta", "denom", "LHS")
         return dict(zip(keys, list(out)))
 
     def get_field(self, which=0, out=None):

@@ -632,3 +632,25 @@ def pin_energies_closed_form() -> float:
                 worst = max(worst, abs(m.L_norm_sq(phi) - (m.a * P2 + D2)) / (m.a * P2 + D2))
                 worst = max(worst, abs(g.mean_value(phi) - c0 * V) / (c0 * V))
     return worst
+
+
+def pin_scalar_form() -> float:
+    """The scalar form of the solve, r^{n+1} = rho + LHS / (2 sqrt(E1)) from
+    (E1, gamma, eta, theta, r^n, r^{n-1}) alone, against r^{n+1} of the full
+    elimination of Sec. 2.3 (eq. solver-2 evaluated with the new field), for
+    BDF2 steps and the first-order start, plain and stabilised."""
+    worst = 0.0
+    for stab in (0.0, 3.0):
+        o, phi0 = _case()
+        o.model.stab = stab
+        o.start(phi0, "bdf1")
+        i = o.last_info
+        worst = max(worst, abs(so.sav_r_update(i["E1"], i["gamma"], i["eta"], i["theta"], 0.0, 0.0, o.dt,
+                                               bdf1=True) - o.r) / abs(o.r))
+        for _ in range(3):
+            r_n, r_nm1 = o.r, o.r_prev
+            o.step()
+            i = o.last_info
+            worst = max(worst, abs(so.sav_r_update(i["E1"], i["gamma"], i["eta"], i["theta"], r_n, r_nm1,
+                                                   o.dt) - o.r) / abs(o.r))
+    return worst

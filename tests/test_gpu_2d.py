@@ -197,15 +197,20 @@ def test_device_pointer_io_matches_host_io():
     assert np.array_equal(out.cpu().numpy(), s1.get_field(0))
 
 
-def test_timing_mode_matches_graph_mode():
+@pytest.mark.parametrize("schedule,classes", [(0, {"row", "col_fused"}), (6, {"step"})])
+def test_timing_mode_matches_production_mode(schedule, classes):
+    """Per-kernel timed launches (one step per launch, events around each)
+    give the same steps as production launches: the graph-replayed two-kernel
+    step (schedule 0) and the persistent step, whose production launch runs
+    all seven steps in one kernel (schedule 6)."""
     c = crystal_2d_case(128)
-    a = _solver(c, "fp32").init(c["phi0"], "bdf1")
-    b = _solver(c, "fp32").init(c["phi0"], "bdf1")
+    a = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
+    b = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
     a.step(7)
     b.set_timing(True)
     b.step(7)
     kt = b.kernel_times()
-    assert set(kt) == {"row", "col_fused"}
+    assert set(kt) == classes
     assert all(v[0] == 7 and v[1] > 0 for v in kt.values())
     assert np.array_equal(a.get_field(0), b.get_field(0))
 

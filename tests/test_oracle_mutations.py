@@ -27,6 +27,7 @@ PINS = [
     (P.pin_gamma3_cosine, lambda v: v < 1e-12),
     (P.pin_gamma3_variational, lambda v: v < 1e-9),
     (P.pin_energies_closed_form, lambda v: v < 1e-12),
+    (P.pin_scalar_form, lambda v: v < 1e-13),
 ]
 
 
@@ -229,6 +230,16 @@ def _m_mass_without_cell_volume(mp):
     mp.setattr(so.Grid, "mean_value", lambda self, f: float(np.sum(f)))
 
 
+def _m_scalar_form_rho_half(mp):
+    orig = so.sav_r_update
+
+    def upd(E1, gamma, eta, theta, r_n, r_nm1, dt, bdf1=False):
+        # theta / (2 sqrt E1) in rho where the BDF2 form has theta / (3 sqrt E1)
+        return orig(E1, gamma, eta, 1.5 * theta, r_n, r_nm1, dt, bdf1) if not bdf1 else \
+            orig(E1, gamma, eta, theta, r_n, r_nm1, dt, bdf1)
+    mp.setattr(so, "sav_r_update", upd)
+
+
 MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_axis,
              _m_wrong_bdf2_operator, _m_wrong_r_coefficient, _m_E1_constant_ignores_beta,
              _m_energy_quarter_dropped, _m_first_order_extrapolation,
@@ -236,7 +247,7 @@ MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_ax
              _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt,
              _m_gamma3_dropped_from_N, _m_gamma3_energy_factor, _m_gamma3_mean_kept,
              _m_original_energy_half_dropped, _m_original_energy_gamma3_dropped, _m_breve_energy_without_a,
-             _m_modified_energy_swapped_levels, _m_mass_without_cell_volume]
+             _m_modified_energy_swapped_levels, _m_mass_without_cell_volume, _m_scalar_form_rho_half]
 
 
 def test_pins_pass_unmutated():

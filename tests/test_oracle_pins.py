@@ -125,3 +125,7 @@ def test_energies_and_mass_closed_form():
     polynomials against their closed forms (single modes along each axis of a
     non-square 2D and a non-cubic 3D box, and a 2D product mode)."""
     assert P.pin_energies_closed_form() < 1e-12
+
+
+def test_scalar_form_of_the_solve():
+    assert P.pin_scalar_form() < 1e-13
