@@ -74,14 +74,18 @@ typedef enum {
 int spfc_create(int d, const int* n, const double* L, double eps, double beta, double dt,
                 int precision, void* cuda_stream, spfc_t* out);
 
-/* Kernel launch schedules (tile shapes) compiled for a grid: spfc_create uses
- * the grid's default (the fastest measured on GB300: 2D float32 N = 128, 256
- * -> 2; 2D float64 N = 128, 256 -> 5, N = 512 -> 1; otherwise 0), as does
- * spfc_create_scheduled with schedule = -1; a schedule in
- * [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
- * autotuner times the choices.
- * All schedules compute the same step; results agree to rounding.
- * spfc_schedule returns the handle's schedule. */
+/* Kernel launch schedules compiled for a grid: the tile shapes of the
+ * two-kernel step (row pass, then the column pass with its grid barrier;
+ * six for N >= 128, one below) and, as the last schedule (6 for N >= 128, 1
+ * below), the persistent step: every step of a spfc_step call in one
+ * cooperative launch (row pass, column forward pass, scalar solve, update
+ * and the next column inverse pass behind bounded grid barriers). spfc_create
+ * uses the grid's default, the fastest measured on GB300 (2D float32: 512 ->
+ * 6, 128 and 256 -> 2, 16..64 -> 1; 2D float64: 512 -> 1, 128 and 256 -> 5,
+ * otherwise 0), as does spfc_create_scheduled with schedule = -1; a schedule
+ * in [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
+ * autotuner times the choices. All schedules compute the same step; results
+ * agree to rounding. spfc_schedule returns the handle's schedule. */
 int spfc_num_schedules(int d, int n);
 int spfc_create_scheduled(int d, const int* n, const double* L, double eps, double beta, double dt,
                           int precision, void* cuda_stream, int schedule, spfc_t* out);
