@@ -207,7 +207,22 @@ def measure_ensemble(steps, warmup, precision, peak, rank=0, world=1, dist=None)
     bytes_step = sum(15 * r["n"] * (r["n"] // 2 + 1) * csize for r in all_runs)
     points = sum(r["n"] * r["n"] for r in all_runs)
     ok = all(b.scalars(i)["status"] == 0 for i in range(len(runs)))
+    # error against plain FP64 single runs from the same start, one run of each
+    # grid class (the batch's steps: the BDF1 start and every step since)
+    import numpy as np
+    from paper_2012_15133_gb300 import Solver
+    errs = {}
+    for i in range(min(4, len(runs))):
+        r = runs[i]
+        done = int(b.scalars(i)["nsteps"]) - 1
+        ref = Solver(2, r["n"], r["L"], r["eps"], r["beta"], r["dt"], "fp64").init(r["phi0"], "bdf1")
+        ref.step(done)
+        fr = ref.get_field(0)
+        errs[str(r["n"])] = float(np.linalg.norm(b.get_field(i) - fr) / np.linalg.norm(fr))
+        ref.close()
     return {"workload": "256-run 2D ensemble (64 each of 64^2..512^2), dt 0.02", "runs": 256,
+            "rel_l2_vs_fp64": max(errs.values()) if errs else None,
+            "rel_l2_vs_fp64_per_class": errs,
             "points": points, "value": points / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
             "ranks": world,
             "steps": steps, "l2": "working set 1.3 GB > L2, no flush",
@@ -470,6 +485,74 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
                     "the surrogate workload at full scale"}
 
 
+# DRAM bytes per launch (read + write) of the 512^2 FP32 persistent step from
+# the committed ncu capture; None until one is taken of the current kernel
+TRAFFIC_STEP_512_FP32 = None
+
+
+def measure_precision_split(steps=1000, n=N_GRID):
+    """Error of the FP32-bulk path (float32 transforms and pointwise work,
+    float64 E_1, inner products and scalar solve) against the plain FP64 GPU
+    path on the headline's workload, from one BDF1 start over `steps` steps:
+    rel-L2 of the field, relative errors of r and of the modified energy, and
+    the mass difference (both keep the zero mode in float64)."""
+    import numpy as np
+    from paper_2012_15133_gb300 import Solver
+    from seeded_inputs import crystal_2d_case
+    c = crystal_2d_case(n)
+    a = Solver(2, n, c["L"], c["eps"], c["beta"], c["dt"], "fp64").init(c["phi0"], "bdf1")
+    b = Solver(2, n, c["L"], c["eps"], c["beta"], c["dt"], "fp32").init(c["phi0"], "bdf1")
+    out = {}
+    done = 0
+    for k in (1, 10, 100, steps):
+        a.step(k - done)
+        b.step(k - done)
+        done = k
+        fa, fb = a.get_field(0), b.get_field(0)
+        ra, rb = a.sav_scalars()["r"], b.sav_scalars()["r"]
+        Ea, Eb = a.energy()[1], b.energy()[1]
+        out[str(k)] = {"rel_l2_phi": float(np.linalg.norm(fb - fa) / np.linalg.norm(fa)),
+                       "rel_r": abs(rb - ra) / abs(ra), "rel_E_mod": abs(Eb - Ea) / abs(Ea),
+                       "mass_diff": abs(b.mass()[0] - a.mass()[0])}
+    return {"workload": f"2D SPFC {n}^2 crystallisation, FP32 bulk vs FP64 GPU from one BDF1 start",
+            "after_steps": out}
+
+
+def _summary(line):
+    """The headline's and each extra's main figures in a few hundred bytes, so
+    that they appear in the last lines of the output."""
+    def r4(x):
+        return None if x is None else float(f"{x:.4g}")
+    out = {"value": r4(line["value"]), "ms_per_step": r4(line["ms_per_step"]),
+           "frac": r4(line["roofline"]["frac"]), "e2e": r4(line["e2e"]["value"]),
+           "l2_resident": r4(line.get("l2_resident_value"))}
+    for k, v in line.items():
+        if not isinstance(v, dict) or "workload" not in v:
+            continue
+        d = {}
+        if "value" in v:
+            d["v"] = r4(v["value"])
+        if "ms_per_step" in v:
+            d["ms"] = r4(v["ms_per_step"])
+        if isinstance(v.get("roofline"), dict):
+            d["frac"] = r4(v["roofline"]["frac"])
+        for key in ("speedup_vs_plain", "speedup_vs_plain_batched"):
+            if key in v:
+                d[key.replace("speedup_vs_", "x_")] = r4(v[key])
+        if "final_rel_l2_vs_plain" in v:
+            d["rel_l2"] = r4(v["final_rel_l2_vs_plain"]["mean"])
+        if "rel_l2_vs_fp64" in v:
+            d["rel_l2"] = r4(v["rel_l2_vs_fp64"])
+        if "jumps" in v and isinstance(v["jumps"], dict):
+            d["fallback"] = r4(v["jumps"].get("fallback_rate"))
+        if "after_steps" in v:
+            last = v["after_steps"][max(v["after_steps"], key=int)]
+            d["rel_l2"] = r4(last["rel_l2_phi"])
+            d["rel_r"] = r4(last["rel_r"])
+        out[k] = d
+    return out
+
+
 def run_ours(args):
     rank, local, world, dist = _dist_init(args.gpus)
     import numpy as np
@@ -529,24 +612,28 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * P * args.steps / (total_ms * 1e-3) / 1e6
 
-    # --- roofline of the dominant kernel (algorithmic bytes: spectrum passes)
+    # --- roofline of the dominant kernel. Algorithmic bytes: SURVEY's 15
+    # half-spectrum passes per 2D step (read 8, write 7) at the bulk precision;
+    # the persistent step does a whole step per launch, the two-kernel step
+    # splits them 4 (row pass) + 11 (the rest, in the fused column pass)
     csize = 8 if args.precision == "fp32" else 16
     SB = N_GRID * (N_GRID // 2 + 1) * csize
-    passes = {"row": 4, "col_fused": 7}
+    passes = {"step": 15, "row": 4, "col_fused": 11}
     dom = max(kt, key=lambda k: kt[k][1])
     nl, ms = kt[dom]
     avg_s = ms / nl * 1e-3
     achieved = passes[dom] * SB / avg_s / 1e9
     peak, peak_kind = _peaks()
-    # DRAM bytes (read + write) per launch of each kernel from the committed ncu
-    # capture of the 512^2 step kernels (ncu --set full, cold caches); set to None whenever the
-    # kernel changes after the capture
-    traffic_ncu = {("fp32", "col_fused"): 4294400, ("fp32", "row"): 2132224}
+    # DRAM bytes (read + write) per launch from the committed ncu capture of the
+    # 512^2 FP32 persistent step (profiles/step2d_512_fp32_persist_ncu.md);
+    # None whenever the kernel changed after the capture
+    traffic_ncu = {("fp32", "step"): TRAFFIC_STEP_512_FP32}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,
             "traffic": traffic_ncu.get((args.precision, dom)),
-            "note": "per-kernel CUDA-event times include each kernel's launch latency (launched one by one)",
+            "note": "CUDA events around each launch on the solver's stream (launched one by one, L2 flushed "
+                    "before each step)",
             "kernels": {k: {"launches": v[0], "avg_us": v[1] / v[0] * 1e3,
                             "share": v[1] / sum(x[1] for x in kt.values())} for k, v in kt.items()}}
 
@@ -561,22 +648,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     resident = P * nres / (e0.elapsed_time(e1) * 1e-3) / 1e6
 
-    # --- end to end through the public API with host buffers
+    # --- end to end through the public API with host buffers: the field from
+    # pinned host memory (init), K steps whose scalar records the device writes
+    # into a pinned host ring every step (read by the host after the run), the
+    # final field back to pinned host memory
     pinned = torch.empty(P, dtype=torch.float64).pin_memory()
     pinned.copy_(torch.from_numpy(np.ascontiguousarray(c["phi0"]).ravel()))
     out = torch.empty(P, dtype=torch.float64).pin_memory()
+    ring = torch.zeros((args.steps + 2, 8), dtype=torch.float64).pin_memory()
     s2 = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+    s2.set_scalar_ring(ring)
     s2.init(pinned.numpy(), "bdf1")
     s2.step(3)
-    s2.sav_scalars()
+    s2.get_field(0, out=out.numpy())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s2.init(pinned.numpy(), "bdf1")
-    for i in range(args.steps):
-        s2.step(1)
-        s2.sav_scalars()           # device -> host read of the step's scalars (6 doubles)
-    s2.get_field(0, out=out.numpy())
+    s2.step(args.steps)
+    s2.get_field(0, out=out.numpy())   # synchronises: the ring holds every step's record
+    recs = ring.numpy()[1:args.steps + 2].copy()
     e2e_s = time.perf_counter() - t0
+    e2e_ok = bool(np.all(recs[:, 0] == np.arange(1, args.steps + 2)) and np.all(recs[:, 7] == 0.0)
+                  and np.all(np.isfinite(recs[:, 1])))
     e2e_val = P * (args.steps + 1) / e2e_s / 1e6
     if dist is not None:
         t = torch.tensor([e2e_s], dtype=torch.float64)
@@ -589,6 +682,7 @@ def run_ours(args):
                                               dist)
         extras["cube3d"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush)
         extras["fp64"] = measure_fp64(min(args.steps, 100), args.warmup, peak, flush)
+        extras["precision_split"] = measure_precision_split()
         extras["gamma3"] = measure_gamma3(min(args.steps, 200), args.warmup, args.precision, peak, flush)
         extras["cube3d_gamma3"] = measure_cube(min(args.steps, 100), args.warmup, args.precision, peak, flush,
                                                gamma3=1.0)
@@ -621,13 +715,18 @@ def run_ours(args):
                            "parallelism": f"{world} independent runs (one per GPU)" if world > 1 else "1 run"},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT,
-                        "h2d_bytes_per_step": P * 8 / args.steps,
-                        "d2h_bytes_per_step": 48 + P * 8 / args.steps,
-                        "note": "init from pinned host field, per step spfc_step(1) + scalar read-back, final field read-back"},
-                "gpu_launches": 2 * args.steps,
+                        "h2d_bytes_per_step": P * 8 / (args.steps + 1),
+                        "d2h_bytes_per_step": 64 + P * 8 / (args.steps + 1),
+                        "records_ok": e2e_ok,
+                        "note": "init (BDF1 start) from a pinned host field, K steps in one spfc_step call "
+                                "whose device writes each step's 8-double scalar record into a pinned host ring, "
+                                "final field back to pinned host memory; per step: the field's bytes amortised "
+                                "over the run plus the 64-byte record"},
+                "gpu_launches": sum(v[0] for v in kt.values()),
                 "l2_resident_value": resident,
                 "clocks": clk.summary(),
                 **extras}
+        line["summary"] = _summary(line)
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()

@@ -175,6 +175,22 @@ int spfc_set_gamma3(spfc_t h, double gamma3);
 int spfc_save(spfc_t h, const char* path);
 int spfc_load(spfc_t h, const char* path);
 
+/* Per-step scalar records without host synchronisation (the paper has no
+ * counterpart; it serves callers that follow r, xi, gamma and E_1 every step
+ * without stalling the stream): host_ring is page-locked host memory that the
+ * device can address (cudaHostAlloc / cudaMallocHost, or pinned torch
+ * tensors, under unified addressing) holding `capacity` records of 8 float64
+ * values. Every committed step of this handle (every solve of eqs. solver-2 to
+ * solver-6, the start-up included) writes, from the device, record
+ * steps % capacity = {steps since init, r^{n+1}, r^n, xi, gamma, E_1,
+ * alpha = dt r^{n+1}/sqrt(E_1), device status}. Records are complete once the
+ * stream has been synchronised (spfc_sync or any synchronising call); the
+ * caller owns the memory and must keep it alive until the ring is removed
+ * (host_ring = NULL) or the handle destroyed. The setting survives
+ * spfc_init, spfc_set_state and spfc_load. SPFC_EINVAL for a capacity < 1
+ * or memory the device cannot address. Synchronises the stream. */
+int spfc_set_scalar_ring(spfc_t h, double* host_ring, int64_t capacity);
+
 /* Wait for the handle's stream and report any latched device status. */
 int spfc_sync(spfc_t h);
 

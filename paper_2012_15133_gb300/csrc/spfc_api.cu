@@ -256,6 +256,19 @@ int spfc_load(spfc_t h, const char* path) {
   return wrap(h, h->s->restore(blob));
 }
 
+int spfc_set_scalar_ring(spfc_t h, double* host_ring, int64_t capacity) {
+  if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
+  if (!host_ring) return wrap(h, h->s->set_ring(nullptr, 0));
+  if (capacity < 1) return fail(h, SPFC_EINVAL, "capacity must be >= 1 when a ring is given");
+  void* dev = nullptr;
+  cudaError_t e = cudaHostGetDevicePointer(&dev, host_ring, 0);
+  if (e != cudaSuccess || !dev) {
+    cudaGetLastError();  // clear the sticky-free error of the failed lookup
+    return fail(h, SPFC_EINVAL, "the ring must be page-locked host memory mapped into the device address space");
+  }
+  return wrap(h, h->s->set_ring(static_cast<double*>(dev), (long long)capacity));
+}
+
 int spfc_sync(spfc_t h) {
   if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
   return wrap(h, h->s->sync());

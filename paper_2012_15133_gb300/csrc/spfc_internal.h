@@ -44,6 +44,15 @@ class SolverBase {
   virtual int dump(std::string* blob) = 0;
   virtual int restore(const std::string& blob) = 0;
 
+  // per-step record ring (device-visible pointer into pinned host memory)
+  virtual int set_ring(double* dev, long long cap) = 0;
+  void apply_ring(SavScal* h) const {
+    h->ring = ring_dev;
+    h->ring_cap = ring_cap;
+  }
+  double* ring_dev = nullptr;
+  long long ring_cap = 0;
+
   Params P{};
   int precision = 0;
   int schedule = 0;

@@ -547,6 +547,12 @@ __device__ inline void sav_commit(SavScal* sc, const SolveOut& o, int p_new, int
   sc->p = p_new;
   sc->pending = pending;
   sc->nsteps += 1;
+  if (sc->ring) {  // the step's record, written straight into pinned host memory
+    double* e = sc->ring + kRingFields * (sc->nsteps % sc->ring_cap);
+    e[1] = o.r_new; e[2] = o.r_prev_new; e[3] = o.xi; e[4] = o.gamma; e[5] = o.E1; e[6] = o.alpha;
+    e[7] = (double)sc->status;
+    e[0] = (double)sc->nsteps;
+  }
 }
 
 // Lazy-update form used by the separate forward column pass: newest holds

@@ -429,6 +429,7 @@ class Solver2D final : public SolverBase {
     const double z0 = h.zm[p], z1 = h.zm[1 - p];
     h.zm[0] = z0;
     h.zm[1] = z1;
+    apply_ring(&h);
     drop_graphs();
     SPFC_CK(cudaStreamSynchronize(st_));
     if (int rc = reset_barriers()) return rc;
@@ -436,6 +437,15 @@ class Solver2D final : public SolverBase {
     SPFC_CK(cudaMemcpy(S_.s[1], blob.data() + sizeof(SavScal) + spec_bytes_, spec_bytes_, cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemcpy(sc_, &h, sizeof(SavScal), cudaMemcpyHostToDevice));
     inited = true;
+    return 0;
+  }
+
+  int set_ring(double* dev, long long cap) override {
+    SPFC_CK(cudaStreamSynchronize(st_));
+    ring_dev = dev;
+    ring_cap = cap;
+    SPFC_CK(cudaMemcpy(&sc_->ring, &ring_dev, sizeof(double*), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(&sc_->ring_cap, &ring_cap, sizeof(long long), cudaMemcpyHostToDevice));
     return 0;
   }
 
@@ -600,7 +610,9 @@ class Solver2D final : public SolverBase {
     const size_t bytes = (size_t)N * N * sizeof(double);
     if (reset) {
       SavScal z{};
+      apply_ring(&z);
       SPFC_CK(cudaMemcpyAsync(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
+      SPFC_CK(cudaStreamSynchronize(st_));  // z is a stack object
       reset_barriers();
       drop_graphs();
     }

@@ -258,6 +258,15 @@ class Solver3D final : public SolverBase {
     return 0;
   }
 
+  int set_ring(double* dev, long long cap) override {
+    SPFC_CK(cudaStreamSynchronize(st_));
+    ring_dev = dev;
+    ring_cap = cap;
+    SPFC_CK(cudaMemcpy(&sc_->ring, &ring_dev, sizeof(double*), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(&sc_->ring_cap, &ring_cap, sizeof(long long), cudaMemcpyHostToDevice));
+    return 0;
+  }
+
   int set_timing(bool on) override {
     timing_ = on;
     return 0;
@@ -303,6 +312,7 @@ class Solver3D final : public SolverBase {
     h.status = DEV_OK;
     h.zm[0] = z0;
     h.zm[1] = z1;
+    apply_ring(&h);
     drop_graphs();
     w_ready_ = false;
     SPFC_CK(cudaStreamSynchronize(st_));
@@ -444,7 +454,9 @@ class Solver3D final : public SolverBase {
     const size_t bytes = (size_t)N * N * N * sizeof(double);
     if (reset) {
       SavScal z{};
+      apply_ring(&z);
       SPFC_CK(cudaMemcpyAsync(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
+      SPFC_CK(cudaStreamSynchronize(st_));  // z is a stack object
       drop_graphs();
     }
     SPFC_CK(cudaMemcpyAsync(real_, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));

@@ -59,6 +59,12 @@ struct SavScal {
   double E_orig, E_mod, E_breve;
   int p, pending, status, pad_;
   long long nsteps;
+  // optional per-step record ring in pinned host memory (device-visible
+  // pointer; NULL: none): every committed solve writes kRingFields doubles
+  // {steps, r^{n+1}, r^n, xi, gamma, E_1, alpha, status} at entry steps % cap.
+  double* ring;
+  long long ring_cap;
 };
+constexpr int kRingFields = 8;
 
 }  // namespace spfc

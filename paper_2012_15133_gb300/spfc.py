@@ -46,6 +46,7 @@ _SIGS = {
     "spfc_set_gamma3": (_I, [_P, _D]),
     "spfc_save": (_I, [_P, ct.c_char_p]),
     "spfc_load": (_I, [_P, ct.c_char_p]),
+    "spfc_set_scalar_ring": (_I, [_P, _P, ct.c_int64]),
     "spfc_sync": (_I, [_P]),
     "spfc_set_timing": (_I, [_P, _I]),
     "spfc_kernel_times": (_I, [_P, _I, ct.POINTER(ct.c_char_p), ct.POINTER(ct.c_int64), _DP]),
@@ -250,6 +251,24 @@ class Solver:
         a, b = ct.c_double(), ct.c_double()
         self._check(self._lib.spfc_mass(self._h, ct.byref(a), ct.byref(b)))
         return a.value, b.value
+
+    def set_scalar_ring(self, ring):
+        """Per-step records written by the device into page-locked host memory:
+        ring is a pinned torch float64 tensor of shape (capacity, 8) (None
+        removes it). Record steps % capacity of every committed step holds
+        (steps, r^{n+1}, r^n, xi, gamma, E_1, alpha, status); complete after
+        the stream is synchronised."""
+        if ring is None:
+            self._check(self._lib.spfc_set_scalar_ring(self._h, None, 0))
+            self._ring = None
+            return self
+        if ring.dtype.itemsize != 8 or ring.dim() != 2 or ring.shape[1] != 8 or not ring.is_contiguous():
+            raise ValueError("the ring is a contiguous float64 tensor of shape (capacity, 8)")
+        if not ring.is_pinned():
+            raise ValueError("the ring must be page-locked (pin_memory())")
+        self._check(self._lib.spfc_set_scalar_ring(self._h, ct.c_void_p(ring.data_ptr()), int(ring.shape[0])))
+        self._ring = ring  # kept alive with the handle
+        return self
 
     def sav_scalars(self, full=False):
         """r^n, r^{n-1}, xi, gamma, E_1, steps; with full=True also eta, theta,

@@ -277,3 +277,35 @@ def test_device_noise_start_equals_the_host_noise_field():
         a.step(5)
         b.step(5)
         assert np.array_equal(a.get_field(0), b.get_field(0))
+
+
+@pytest.mark.parametrize("schedule", [0, 6])
+def test_scalar_ring_records_every_step(schedule):
+    """The device writes every committed step's scalars into a pinned host
+    ring (no per-step synchronisation): after one sync the records equal the
+    synchronising reads of an identical run, for the two-kernel and the
+    persistent step, the BDF1 start included, with wrap-around."""
+    import torch
+    c = crystal_2d_case(128)
+    cap = 4
+    a = _solver(c, "fp32", schedule=schedule)
+    ring = torch.full((cap, 8), -1.0, dtype=torch.float64).pin_memory()
+    a.set_scalar_ring(ring)
+    a.init(c["phi0"], "bdf1")
+    a.step(6)
+    a.sync()
+    b = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
+    want = {}
+    for _ in range(6):
+        b.step(1)
+        sc = b.sav_scalars(full=True)
+        want[int(sc["nsteps"])] = sc
+    rec = ring.numpy()
+    for k in range(4, 8):  # the last `cap` steps (1 = the BDF1 start, 2..7 the steps)
+        e = rec[k % cap]
+        assert int(e[0]) == k
+        sc = want[k]
+        assert e[1] == sc["r"] and e[2] == sc["r_prev"] and e[3] == sc["xi"]
+        assert e[4] == sc["gamma"] and e[5] == sc["E1"] and e[7] == 0.0
+    assert np.array_equal(a.get_field(0), b.get_field(0))
+    a.set_scalar_ring(None)
