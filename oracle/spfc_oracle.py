@@ -38,6 +38,17 @@ design notes of the repository):
 * The manufactured-solution forcing of Sec. 5.1, which the paper adds
   without writing it, is ``f = d_t phi_e - Delta_N mu_N(phi_e)`` on the grid,
   added to the right-hand side of eq. scheme-SAV-1 (a).
+* The PFC model of Sec. 1 (eq. energy-PFC, phi^4 in place of |grad phi|^4),
+  which the paper states but does not discretise, with gamma3 the phi^4
+  coefficient (1 in the paper): the SPFC split cannot be reused (beta = 0
+  leaves -||grad phi||^2 without a lower bound), so the concave term goes to
+  the linear part as the Swift-Hohenberg operator: ``L = a + (1 + Delta)^2``
+  (symbol ``a + (1 - |k|^2)^2 > 0``), which counts ``1/2 ||phi||^2`` more
+  than the energy has, and ``E_1 = gamma3/4 ||phi||_4^4 - 1/2 ||phi||^2 +
+  C |Omega|`` takes it back; ``C = 1 + 1/(4 gamma3)`` makes the integrand
+  ``gamma3/4 (phi^2 - 1/gamma3)^2 + 1 >= 1``, so ``E_1 >= |Omega|`` as in
+  eq. energy-SPFC-split-2-2. ``N = gamma3 phi^3 - phi`` (mean removed), and
+  the SAV scheme of Sec. 2.2-2.3 is otherwise unchanged.
 """
 from __future__ import annotations
 
@@ -166,10 +177,31 @@ class Model:
         self.nonlinear = nonlinear            # test switch: False sets N_N := 0
         self.stab = 0.0                       # A of the stabilised scheme (Sec. 5.2); 0: Sec. 2
         self.gamma3 = 0.0                     # optional gamma3/4 phi^4 in E_1 (the PFC term); 0: SPFC
+        self.pfc = False                      # the PFC model of Sec. 1 with its own split
+
+    def use_pfc(self, gamma3: float = 1.0):
+        """Switch to the PFC model (eq. energy-PFC) with phi^4 coefficient gamma3 > 0:
+        no |grad phi|^4 term (beta = 0), L = a + (1 + Delta)^2, E_1 = gamma3/4 ||phi||_4^4
+        - 1/2 ||phi||^2 + (1 + 1/(4 gamma3)) |Omega|, N = gamma3 phi^3 - phi."""
+        if not gamma3 > 0.0:
+            raise ValueError("the PFC model needs gamma3 > 0")
+        self.pfc = True
+        self.gamma3 = float(gamma3)
+        self.beta = 0.0
+        self.C = 1.0 + 1.0 / (4.0 * self.gamma3)
+        return self
+
+    def L_symbol(self, K2):
+        """Fourier symbol of L_N: a + |k|^4 (SPFC, Sec. 2.2) or a + (1 - |k|^2)^2 (PFC)."""
+        return self.a + (1.0 - K2) ** 2 if self.pfc else self.a + K2 ** 2
 
     def L_op(self, f):
-        """L_N f = a f + Delta_N^2 f (Sec. 2.1, before eq. spectral-coll-6)."""
+        """L_N f = a f + Delta_N^2 f (Sec. 2.1, before eq. spectral-coll-6); for the PFC
+        model a f + (1 + Delta_N)^2 f = (a + 1) f + 2 Delta_N f + Delta_N^2 f."""
         g = self.g
+        if self.pfc:
+            lf = g.lap(f)
+            return (self.a + 1.0) * f + 2.0 * lf + g.lap(lf)
         return self.a * f + g.lap(g.lap(f))
 
     def grad_sq(self, phi):
@@ -180,6 +212,9 @@ class Model:
         """E_{1,N}(phi) = beta/4 ||grad_N phi||_4^4 - ||grad_N phi||_2^2 + C |Omega| (Sec. 2.2),
         plus gamma3/4 ||phi||_4^4 when the optional phi^4 term is on (E_1 >= |Omega| still)."""
         g = self.g
+        if self.pfc:
+            return (self.gamma3 / 4.0) * g.hd * float(np.sum(phi ** 4)) - 0.5 * g.hd * float(np.sum(phi * phi)) \
+                + self.C * g.volume
         s = self.grad_sq(phi)
         e = (self.beta / 4.0) * g.hd * float(np.sum(s * s)) - g.hd * float(np.sum(s)) + self.C * g.volume
         if self.gamma3:
@@ -192,6 +227,10 @@ class Model:
         g = self.g
         if not self.nonlinear:
             return np.zeros(g.shape)
+        if self.pfc:
+            # the variational derivative of gamma3/4 ||phi||_4^4 - 1/2 ||phi||^2, mean removed
+            n = self.gamma3 * phi ** 3 - phi
+            return n - float(np.mean(n))
         gr = g.grad(phi)
         s = sum(gc * gc for gc in gr)
         n = -g.div([self.beta * s * gc for gc in gr]) + 2.0 * g.div(gr)
@@ -232,6 +271,8 @@ class Model:
     def E_breve(self, phi, r) -> float:
         """a/2 ||phi||^2 + 1/2 ||Delta_N phi||^2 + |r|^2, the SAV energy plotted in Sec. 5.2."""
         g = self.g
+        if self.pfc:  # 1/2 <phi, L_N phi> + r^2 with the PFC operator
+            return 0.5 * self.L_norm_sq(phi) + r * r
         lp = g.lap(phi)
         return 0.5 * self.a * g.inner(phi, phi) + 0.5 * g.inner(lp, lp) + r * r
 
@@ -245,10 +286,11 @@ def A_inv(model: Model, f, dt: float, c0: float):
     Fourier space (A = model.stab, 0 for the scheme of Sec. 2).
 
     c0 = 3/2 gives A_N of eq. solver-1; c0 = 1 the first-order operator.
-    The symbol is c0 + dt |k|^2 (a + |k|^4) + A dt |k|^2 > 0.
+    The symbol is c0 + dt |k|^2 (a + |k|^4) + A dt |k|^2 > 0 (for the PFC model
+    a + (1 - |k|^2)^2 in place of a + |k|^4).
     """
     g = model.g
-    sym = c0 + dt * g.K2 * (model.a + g.K2 ** 2) + model.stab * dt * g.K2
+    sym = c0 + dt * g.K2 * model.L_symbol(g.K2) + model.stab * dt * g.K2
     return g.idft(g.dft(f) / sym)
 
 
@@ -361,11 +403,13 @@ def copy_start(model: Model, phi0):
 class Oracle:
     """State (phi^n, phi^{n-1}, r^n, r^{n-1}) advanced by bdf2_sav_step."""
 
-    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive", stab=0.0, gamma3=0.0):
+    def __init__(self, d, n, L, eps, beta, dt, nonlinear=True, dft="naive", stab=0.0, gamma3=0.0, pfc=False):
         self.grid = Grid(d, n, L, dft=dft)
-        self.model = Model(self.grid, eps, beta, nonlinear=nonlinear)
+        self.model = Model(self.grid, eps, beta if beta > 0 else 1.0, nonlinear=nonlinear)
         self.model.stab = float(stab)
         self.model.gamma3 = float(gamma3)
+        if pfc:
+            self.model.use_pfc(gamma3)
         self.dt = float(dt)
         self.phi = self.phi_prev = None
         self.r = self.r_prev = None

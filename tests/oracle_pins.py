@@ -204,8 +204,10 @@ def min_E1_margin() -> float:
 
 # --- the scheme -----------------------------------------------------------------
 
-def _case(n=16, L=8.0, dt=0.05, eps=0.25, beta=1.0, amp=0.4, d=2, smooth=0.2):
+def _case(n=16, L=8.0, dt=0.05, eps=0.25, beta=1.0, amp=0.4, d=2, smooth=0.2, pfc=False):
     o = so.Oracle(d, n, L, eps, beta, dt)
+    if pfc:
+        o.model.use_pfc(pfc if isinstance(pfc, float) else 1.0)
     phi0 = noisy_field(o.grid.shape, 0.2, amp, 21)
     # smooth the random data a little so that the gradients stay moderate
     g = o.grid
@@ -213,10 +215,11 @@ def _case(n=16, L=8.0, dt=0.05, eps=0.25, beta=1.0, amp=0.4, d=2, smooth=0.2):
     return o, phi0
 
 
-def pin_residual(d=2, gamma3=0.0) -> float:
+def pin_residual(d=2, gamma3=0.0, pfc=False) -> float:
     """Plug (phi^{n+1}, r^{n+1}) into eq. scheme-SAV-1 (a) and (b) directly."""
-    o, phi0 = _case(d=d, n=16 if d == 2 else 8, L=8.0 if d == 2 else 5.0)
-    o.model.gamma3 = gamma3
+    o, phi0 = _case(d=d, n=16 if d == 2 else 8, L=8.0 if d == 2 else 5.0, pfc=pfc)
+    if not pfc:
+        o.model.gamma3 = gamma3
     o.start(phi0, "ghost")
     worst = 0.0
     m, g, dt = o.model, o.grid, o.dt
@@ -255,10 +258,10 @@ def pin_bdf1_residual() -> float:
     return max(w, abs(resb) / ((abs(o.r) + abs(o.r_prev)) / dt), abs(o.r_prev - sq) / sq)
 
 
-def pin_dissipation() -> float:
+def pin_dissipation(pfc=False) -> float:
     """Exact identity eq. eng stab-5, with ||grad_N mu||^2 written as <-Delta_N mu, mu>.
     Returns the worst |identity residual| / |E^{n+1} - E^n|."""
-    o, phi0 = _case(dt=0.1)
+    o, phi0 = _case(dt=0.1, pfc=pfc)
     o.start(phi0, "bdf1")
     m, g, dt = o.model, o.grid, o.dt
     worst = 0.0
@@ -279,11 +282,13 @@ def pin_dissipation() -> float:
     return worst
 
 
-def pin_linear_closed_form() -> float:
+def pin_linear_closed_form(pfc=False) -> float:
     """N_N switched off: each Fourier mode follows (3/2 + lam) x_{n+1} = 2 x_n - x_{n-1}/2,
-    lam = dt |k|^2 (a + |k|^4), i.e. x_n = c1 z1^n + c2 z2^n with z the roots of
-    (3/2 + lam) z^2 - 2 z + 1/2 = 0; r stays constant."""
+    lam = dt |k|^2 (a + |k|^4) (PFC: dt |k|^2 (a + (1 - |k|^2)^2)), i.e. x_n = c1 z1^n +
+    c2 z2^n with z the roots of (3/2 + lam) z^2 - 2 z + 1/2 = 0; r stays constant."""
     o = so.Oracle(2, 12, 6.0, 0.3, 1.0, 0.02, nonlinear=False)
+    if pfc:
+        o.model.use_pfc(1.0)
     g = o.grid
     phi0 = noisy_field(g.shape, 0.1, 0.5, 9)
     phim1 = noisy_field(g.shape, 0.1, 0.5, 10)
@@ -291,7 +296,7 @@ def pin_linear_closed_form() -> float:
     nsteps = 25
     o.step(nsteps)
     x0, xm1 = g.dft(phi0), g.dft(phim1)
-    lam = o.dt * g.K2 * (o.model.a + g.K2 ** 2)
+    lam = o.dt * g.K2 * ((o.model.a + (1.0 - g.K2) ** 2) if pfc else (o.model.a + g.K2 ** 2))
     worst = 0.0
     out = g.dft(o.phi)
     for idx in np.ndindex(*g.shape):
@@ -653,4 +658,80 @@ def pin_scalar_form() -> float:
             i = o.last_info
             worst = max(worst, abs(so.sav_r_update(i["E1"], i["gamma"], i["eta"], i["theta"], r_n, r_nm1,
                                                    o.dt) - o.r) / abs(o.r))
+    return worst
+
+
+# --- the PFC model of Sec. 1 (eq. energy-PFC) with its own split -------------
+
+def pin_pfc_closed_form() -> float:
+    """phi = c0 + A cos(k x_c) under the PFC model (gamma3 phi^4 / 4, beta = 0):
+    N = gamma3 (3 c0^2 A cos kx + 3/2 c0 A^2 cos 2kx + A^3/4 (3 cos kx + cos 3kx)) - A cos kx
+    (gamma3 phi^3 - phi with its mean removed);
+    E_1 = |Omega| (gamma3/4 (c0^4 + 3 c0^2 A^2 + 3/8 A^4) - 1/2 (c0^2 + A^2/2) + 1 + 1/(4 gamma3));
+    L phi = (a + 1) c0 + (a + (1 - k^2)^2) A cos kx (the Swift-Hohenberg operator a + (1 + Delta)^2);
+    E_N = the PFC energy of eq. energy-PFC, |Omega| (gamma3/4 (c0^4 + 3 c0^2 A^2 + 3/8 A^4)
+    + a/2 (c0^2 + A^2/2) - A^2 k^2 / 2 + A^2 k^4 / 4), and E_N = 1/2 <phi, L phi> + E_1 - C |Omega|."""
+    worst = 0.0
+    for d, n, L in ((2, (32, 24), (16.0, 12.0)), (3, 16, (8.0, 6.0, 5.0))):
+        g = so.Grid(d, n, L)
+        X = _coords(g)
+        V = g.volume
+        for c in range(d):
+            for eps, g3 in ((0.25, 1.0), (0.6, 0.7)):
+                m = so.Model(g, eps=eps).use_pfc(g3)
+                a = m.a
+                A, c0 = 0.8, 0.3
+                ell = 3 if 3 * 3 < g.n[c] // 2 else 2
+                k = 2 * math.pi * ell / g.L[c]
+                x = X[c]
+                phi = c0 + A * np.cos(k * x)
+                Nref = g3 * (3 * c0 * c0 * A * np.cos(k * x) + 1.5 * c0 * A * A * np.cos(2 * k * x)
+                             + 0.25 * A ** 3 * (3 * np.cos(k * x) + np.cos(3 * k * x))) - A * np.cos(k * x)
+                worst = max(worst, _rel(m.N_op(phi), Nref))
+                Q4 = c0 ** 4 + 3 * c0 * c0 * A * A + 3 / 8 * A ** 4
+                P2 = c0 ** 2 + A ** 2 / 2
+                E1ref = V * (g3 / 4 * Q4 - 0.5 * P2 + 1.0 + 1.0 / (4 * g3))
+                worst = max(worst, abs(m.E1(phi) - E1ref) / E1ref)
+                Lref = (a + 1.0) * c0 + (a + (1 - k * k) ** 2) * A * np.cos(k * x)
+                worst = max(worst, _rel(m.L_op(phi), Lref))
+                EN = V * (g3 / 4 * Q4 + a / 2 * P2 - A * A * k * k / 2 + A * A * k ** 4 / 4)
+                worst = max(worst, abs(m.E_orig(phi) - EN) / abs(EN))
+                split = 0.5 * m.L_norm_sq(phi) + m.E1(phi) - m.C * V
+                worst = max(worst, abs(split - EN) / abs(EN))
+    return worst
+
+
+def pfc_lower_bound_margin() -> float:
+    """E_1 >= |Omega| for the PFC split: equality at the constant states
+    phi = +-1/sqrt(gamma3) (the minimum of gamma3/4 phi^4 - 1/2 phi^2), and
+    above it on noisy fields. Returns the smallest (E_1 - |Omega|)/|Omega|
+    seen, with the constant states' |E_1 - |Omega|| / |Omega| subtracted."""
+    g = so.Grid(2, 16, 7.0)
+    lo, eq = np.inf, 0.0
+    for g3 in (1.0, 0.3, 2.5):
+        m = so.Model(g, eps=0.2).use_pfc(g3)
+        for sgn in (1.0, -1.0):
+            v = np.full(g.shape, sgn / math.sqrt(g3))
+            eq = max(eq, abs(m.E1(v) - g.volume) / g.volume)
+        for seed in range(4):
+            phi = noisy_field(g.shape, 0.0, 2.0 / math.sqrt(g3), 40 + seed)
+            lo = min(lo, (m.E1(phi) - g.volume) / g.volume)
+    return lo - eq
+
+
+def pin_pfc_variational() -> float:
+    """N_N of the PFC split is the gradient of E_{1,N} along mass-preserving
+    directions (central differences with one Richardson step)."""
+    worst = 0.0
+    for d, n, L in ((2, 16, 8.0), (3, 8, 5.0)):
+        g = so.Grid(d, n, L)
+        phi = noisy_field(g.shape, 0.25, 0.6, 33)
+        psi = noisy_field(g.shape, 0.0, 1.0, 34)
+        psi = psi - psi.mean()
+        for g3 in (1.0, 0.45):
+            m = so.Model(g, eps=0.25).use_pfc(g3)
+            cd = lambda e: (m.E1(phi + e * psi) - m.E1(phi - e * psi)) / (2 * e)
+            fd = (4.0 * cd(5e-4) - cd(1e-3)) / 3.0
+            an = g.inner(m.N_op(phi), psi)
+            worst = max(worst, abs(fd - an) / abs(an))
     return worst

@@ -28,6 +28,12 @@ PINS = [
     (P.pin_gamma3_variational, lambda v: v < 1e-9),
     (P.pin_energies_closed_form, lambda v: v < 1e-12),
     (P.pin_scalar_form, lambda v: v < 1e-13),
+    (P.pin_pfc_closed_form, lambda v: v < 1e-12),
+    (P.pfc_lower_bound_margin, lambda v: v >= -1e-14),
+    (P.pin_pfc_variational, lambda v: v < 1e-9),
+    (lambda: P.pin_residual(2, pfc=True), lambda v: v < 1e-10),
+    (lambda: P.pin_dissipation(pfc=True), lambda v: v < 1e-9),
+    (lambda: P.pin_linear_closed_form(pfc=True), lambda v: v < 1e-12),
 ]
 
 
@@ -240,6 +246,41 @@ def _m_scalar_form_rho_half(mp):
     mp.setattr(so, "sav_r_update", upd)
 
 
+def _m_pfc_symbol_sign(mp):
+    orig = so.Model.L_symbol
+    mp.setattr(so.Model, "L_symbol", lambda self, K2: self.a + (1.0 + K2) ** 2 if self.pfc else orig(self, K2))
+
+
+def _m_pfc_operator_drops_laplacian(mp):
+    orig = so.Model.L_op
+
+    def L_op(self, f):
+        if self.pfc:
+            lf = self.g.lap(f)
+            return (self.a + 1.0) * f + self.g.lap(lf)
+        return orig(self, f)
+    mp.setattr(so.Model, "L_op", L_op)
+
+
+def _m_pfc_potential_keeps_linear_term_out(mp):
+    orig = so.Model.N_op
+
+    def N_op(self, phi):
+        n = orig(self, phi)
+        return n + (phi - float(np.mean(phi))) if self.pfc else n
+    mp.setattr(so.Model, "N_op", N_op)
+
+
+def _m_pfc_energy_constant(mp):
+    orig = so.Model.use_pfc
+
+    def use_pfc(self, gamma3=1.0):
+        orig(self, gamma3)
+        self.C = 1.0 + 1.0 / (2.0 * self.gamma3)
+        return self
+    mp.setattr(so.Model, "use_pfc", use_pfc)
+
+
 MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_axis,
              _m_wrong_bdf2_operator, _m_wrong_r_coefficient, _m_E1_constant_ignores_beta,
              _m_energy_quarter_dropped, _m_first_order_extrapolation,
@@ -247,7 +288,9 @@ MUTATIONS = [_m_drop_laplacian_term, _m_flip_quartic_sign, _m_swap_derivative_ax
              _m_stab_rhs_sign, _m_stab_rhs_dropped, _m_stab_symbol_dropped, _m_stab_symbol_without_dt,
              _m_gamma3_dropped_from_N, _m_gamma3_energy_factor, _m_gamma3_mean_kept,
              _m_original_energy_half_dropped, _m_original_energy_gamma3_dropped, _m_breve_energy_without_a,
-             _m_modified_energy_swapped_levels, _m_mass_without_cell_volume, _m_scalar_form_rho_half]
+             _m_modified_energy_swapped_levels, _m_mass_without_cell_volume, _m_scalar_form_rho_half,
+             _m_pfc_symbol_sign, _m_pfc_operator_drops_laplacian, _m_pfc_potential_keeps_linear_term_out,
+             _m_pfc_energy_constant]
 
 
 def test_pins_pass_unmutated():

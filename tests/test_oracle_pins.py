@@ -129,3 +129,33 @@ def test_energies_and_mass_closed_form():
 
 def test_scalar_form_of_the_solve():
     assert P.pin_scalar_form() < 1e-13
+
+
+def test_pfc_split_closed_form():
+    """The PFC model of Sec. 1: N, E_1, the operator and the energy of
+    eq. energy-PFC in closed form, and the split identity E_N = 1/2 <phi, L phi>
+    + E_1 - C |Omega|."""
+    assert P.pin_pfc_closed_form() < 1e-12
+
+
+def test_pfc_split_lower_bound():
+    assert P.pfc_lower_bound_margin() >= -1e-14
+
+
+def test_pfc_potential_is_the_variational_derivative():
+    assert P.pin_pfc_variational() < 1e-9
+
+
+def test_pfc_scheme_residual():
+    # relative to the largest term of (a); the Swift-Hohenberg symbol's |k|^2 (1 - |k|^2)^2
+    # amplifies the transforms' roundoff about as much as the stabilised scheme's does
+    assert P.pin_residual(2, pfc=True) < 1e-10
+    assert P.pin_residual(3, pfc=True) < 1e-10
+
+
+def test_pfc_dissipation_identity():
+    assert P.pin_dissipation(pfc=True) < 1e-9
+
+
+def test_pfc_linear_part_closed_form():
+    assert P.pin_linear_closed_form(pfc=True) < 1e-12
