@@ -505,8 +505,9 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
 
 
 # DRAM bytes per launch (read + write) of the 512^2 FP32 persistent step from
-# the committed ncu capture; None until one is taken of the current kernel
-TRAFFIC_STEP_512_FP32 = None
+# the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,321,024
+# read, 0 written); None whenever the kernel changes after the capture
+TRAFFIC_STEP_512_FP32 = 4321024
 
 
 def measure_precision_split(steps=1000, n=N_GRID):
@@ -546,7 +547,7 @@ def _summary(line):
            "frac": r4(line["roofline"]["frac"]), "e2e": r4(line["e2e"]["value"]),
            "l2_resident": r4(line.get("l2_resident_value"))}
     for k, v in line.items():
-        if not isinstance(v, dict) or "workload" not in v:
+        if k == "config" or not isinstance(v, dict) or "workload" not in v:
             continue
         d = {}
         if "value" in v:

@@ -167,6 +167,22 @@ int spfc_set_stabilization(spfc_t h, double A);
  * non-finite gamma3. */
 int spfc_set_gamma3(spfc_t h, double gamma3);
 
+/* The PFC model of Sec. 1 (eq. energy-PFC: gamma3/4 phi^4 in place of
+ * beta/4 |grad phi|^4; gamma3 = 1 is the paper's) on the same scheme, with a
+ * split of its own, since without the |grad phi|^4 term the SPFC split has no
+ * lower bound: L_N = a + (1 + Delta_N)^2 (symbol a + (1 - |k|^2)^2 > 0, so
+ * A_N = 3/2 + dt |k|^2 (a + (1 - |k|^2)^2)), E_1 = gamma3/4 ||phi||_4^4 -
+ * 1/2 ||phi||^2 + (1 + 1/(4 gamma3)) |Omega| >= |Omega|, N_N = gamma3 phi^3 -
+ * phi (mean removed). gamma3 > 0 switches it on, 0 switches back to SPFC (the
+ * beta given at creation). 2D single runs; a step is the lazy three-pass form.
+ * spfc_energy then returns E_N = the PFC energy, the modified energy with
+ * this L_N, and E_breve = 1/2 ||L_N^{1/2} phi||^2 + r^2. Set before spfc_init
+ * it also applies to the start-up step; set later it applies to the steps
+ * that follow (a pending update is completed first). Checkpoints record the
+ * model. spfc_set_gamma3 is refused while it is on. SPFC_EINVAL for a
+ * negative or non-finite gamma3, or a 3D handle with gamma3 > 0. */
+int spfc_set_pfc(spfc_t h, double gamma3);
+
 /* Write / read a checkpoint: the exact device state (both spectral levels in the
  * handle's precision, r^n, r^{n-1}, the step count) plus the grid and parameters.
  * A resumed run continues bit-identically. spfc_load rejects a file whose grid,

@@ -205,7 +205,7 @@ int spfc_dt_change(spfc_t h, double dt_new) {
 }
 
 // Checkpoint file: magic, then int32 {d, N, precision, blob bytes}, then
-// float64 {kf0, kf1, kf2, dt, a, beta, A, gamma3}, then the raw state blob
+// float64 {kf0, kf1, kf2, dt, a, beta, A, gamma3, model (1 = PFC)}, then the raw state blob
 // (scalar record and both spectral levels), so that a resumed run is
 // bit-identical.
 static const char kMagic[8] = {'S', 'P', 'F', 'C', 'C', 'K', 'P', '5'};
@@ -220,7 +220,7 @@ int spfc_save(spfc_t h, const char* path) {
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(h, SPFC_EINVAL, std::string("cannot open ") + path);
   const int32_t hdr[4] = {P.d, P.N, h->s->precision, (int32_t)blob.size()};
-  const double sv[8] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab, P.g3};
+  const double sv[9] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab, P.g3, (double)P.pfc};
   bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
             std::fwrite(sv, sizeof(sv), 1, fp) == 1 && std::fwrite(blob.data(), 1, blob.size(), fp) == blob.size();
   ok = (std::fclose(fp) == 0) && ok;
@@ -235,25 +235,31 @@ int spfc_load(spfc_t h, const char* path) {
   if (!fp) return fail(h, SPFC_EINVAL, std::string("cannot open ") + path);
   char magic[8];
   int32_t hdr[4];
-  double sv[8];
+  double sv[9];
   bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
             std::fread(hdr, sizeof(hdr), 1, fp) == 1 && std::fread(sv, sizeof(sv), 1, fp) == 1;
   if (!ok || hdr[0] != P.d || hdr[1] != P.N || hdr[2] != h->s->precision || hdr[3] <= 0) {
     std::fclose(fp);
     return fail(h, SPFC_EINVAL, "checkpoint does not match this handle (grid or precision)");
   }
-  const double want[8] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab, P.g3};
-  for (int i = 0; i < 8; ++i)
+  const double want[9] = {P.kf[0], P.kf[1], P.kf[2], P.dt, P.a, P.beta, P.stab, P.g3, (double)P.pfc};
+  for (int i = 0; i < 9; ++i)
     if (std::fabs(sv[i] - want[i]) > 1e-12 * std::fabs(want[i])) {
       std::fclose(fp);
       return fail(h, SPFC_EINVAL,
-                  "checkpoint parameters (L, dt, eps, beta, stabiliser or gamma3) differ from this handle's");
+                  "checkpoint parameters (L, dt, eps, beta, stabiliser, gamma3 or model) differ from this handle's");
     }
   std::string blob((size_t)hdr[3], '\0');
   ok = std::fread(&blob[0], 1, blob.size(), fp) == blob.size();
   std::fclose(fp);
   if (!ok) return fail(h, SPFC_EINVAL, "truncated checkpoint");
   return wrap(h, h->s->restore(blob));
+}
+
+int spfc_set_pfc(spfc_t h, double gamma3) {
+  if (!h) return fail(h, SPFC_EINVAL, "NULL handle");
+  if (!(gamma3 >= 0.0) || !std::isfinite(gamma3)) return fail(h, SPFC_EINVAL, "gamma3 must be finite and >= 0");
+  return wrap(h, h->s->set_pfc(gamma3));
 }
 
 int spfc_set_scalar_ring(spfc_t h, double* host_ring, int64_t capacity) {

@@ -36,6 +36,13 @@ class SolverBase {
     err = "this solver has no kernels for the phi^4 term";
     return 1;
   }
+  // the PFC model of Sec. 1 (phi^4 coefficient g3 > 0) or the SPFC model (0);
+  // a solver without its kernels accepts 0 only
+  virtual int set_pfc(double g3) {
+    if (g3 == 0.0) return 0;
+    err = "this solver has no kernels for the PFC model (2D single runs only)";
+    return 1;
+  }
   virtual int sync() = 0;
   virtual int set_timing(bool on) = 0;
   virtual int kernel_times(KernelTimes* kt) = 0;
@@ -73,6 +80,8 @@ inline void fill_float_params(Params* P) {
   P->g3b = (P->beta > 0.0) ? P->g3 / P->beta : 0.0;
   P->g3_f = (float)P->g3;
   P->g3b_f = (float)P->g3b;
+  P->e1c4 = P->pfc ? 0.25 * P->g3 : 0.25 * P->beta;
+  P->e1c2 = P->pfc ? -0.5 : -1.0;
 }
 
 // Factories (one translation unit per precision); return nullptr and set err on failure.

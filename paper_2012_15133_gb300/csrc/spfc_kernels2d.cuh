@@ -44,15 +44,17 @@ template <typename R> __device__ __forceinline__ R kderiv(int i, int N, R kf) {
 template <typename R> struct PC;
 template <> struct PC<double> {
   double kfx, kfy, kfz, dt, a, beta, invP, sdt, g3, g3b;
+  int pfc;
   __device__ __forceinline__ explicit PC(const Params& P)
       : kfx(P.kf[0]), kfy(P.kf[1]), kfz(P.kf[2]), dt(P.dt), a(P.a), beta(P.beta), invP(P.invP), sdt(P.sdt),
-        g3(P.g3), g3b(P.g3b) {}
+        g3(P.g3), g3b(P.g3b), pfc(P.pfc) {}
 };
 template <> struct PC<float> {
   float kfx, kfy, kfz, dt, a, beta, invP, sdt, g3, g3b;
+  int pfc;
   __device__ __forceinline__ explicit PC(const Params& P)
       : kfx(P.kf_f[0]), kfy(P.kf_f[1]), kfz(P.kf_f[2]), dt(P.dt_f), a(P.a_f), beta(P.beta_f), invP(P.invP_f),
-        sdt(P.sdt_f), g3(P.g3_f), g3b(P.g3b_f) {}
+        sdt(P.sdt_f), g3(P.g3_f), g3b(P.g3b_f), pfc(P.pfc) {}
 };
 template <typename R> __device__ __forceinline__ R read_alpha(const SavScal* sc);
 template <> __device__ __forceinline__ double read_alpha<double>(const SavScal* sc) { return sc->alpha; }
@@ -85,12 +87,23 @@ __device__ __forceinline__ R sym_K2(int kx, int ky, int N, const PC<R>& c) {
   return rn_fma(kxx, kxx, rn_mul(kyy, kyy));
 }
 
-// 1 / (c0 + dt |k|^2 (a + |k|^4) + A dt |k|^2): inverse symbol of A_N (c0 = 3/2,
+// Symbol of the linear operator L_N: a + |k|^4 (SPFC, Sec. 2.2), or the
+// Swift-Hohenberg a + (1 - |k|^2)^2 of the PFC split.
+template <typename R>
+__device__ __forceinline__ R sym_L(R K2, const PC<R>& c) {
+  if (c.pfc) {
+    const R u = K2 - (R)1;
+    return rn_fma(u, u, c.a);
+  }
+  return rn_fma(K2, K2, c.a);
+}
+
+// 1 / (c0 + dt |k|^2 L(k) + A dt |k|^2): inverse symbol of A_N (c0 = 3/2,
 // eq. solver-1) or of the first-order operator (c0 = 1); the last term is the
 // stabiliser of Sec. 5.2 (exactly zero when A = 0).
 template <typename R>
 __device__ __forceinline__ R sym_invA(R K2, R c0, const PC<R>& c) {
-  const R A = rn_fma(c.sdt, K2, rn_fma(c.dt, rn_mul(K2, rn_fma(K2, K2, c.a)), c0));
+  const R A = rn_fma(c.sdt, K2, rn_fma(c.dt, rn_mul(K2, sym_L<R>(K2, c)), c0));
   return (R)1 / A;
 }
 
@@ -134,16 +147,18 @@ __device__ __forceinline__ C bdf1_update(C cur, C nh, R K2, R invA, R alpha, R s
 // transforms both, so that -i (Y W0 + k~_y Y W1) is N_hat with the transform of
 // gamma3 phi*^3 added.
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false, bool PF = false>
 __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ Nhat,
                                                  C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
                                                  SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which,
                                                  C_t<R>* __restrict__ W2 = nullptr) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CI_FIELD) ? 1 : 2;
+  // PF (the PFC model): the row pass needs phi* itself, not its gradients
+  constexpr int NF = (MODE == CI_FIELD || PF) ? 1 : 2;
   static_assert(!G3 || MODE == CI_STEP || MODE == CI_GRAD || MODE == CI_STEP_COMMITTED,
                 "the phi^4 channel is carried by the step and gradient modes");
+  static_assert(!(G3 && PF), "the PFC model has its own passes");
   constexpr int NTH = CT * T;
   constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
   constexpr int NH = N / 2 + 1;
@@ -221,7 +236,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
         }
         ph = mk<C>((R)2 * nw.x - old.x, (R)2 * nw.y - old.y);  // phi* = 2 phi^{n+1} - phi^n
       }
-      if (MODE == CI_FIELD) {
+      if (MODE == CI_FIELD || PF) {
         g0 = ph;
       } else {
         const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
@@ -251,6 +266,14 @@ k2d_col_inv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>*
   k2d_col_inv_body<R, N, E, CT, MODE>(P, S, Nhat, W0, W1, sc, tw, which);
 }
 
+// the PFC model: W0 receives the y-inverse of phi*
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k2d_col_inv_pfc(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __restrict__ W0,
+                SavScal* __restrict__ sc, const C_t<R>* __restrict__ tw, int which) {
+  k2d_col_inv_body<R, N, E, CT, MODE, false, true>(P, S, Nhat, W0, nullptr, sc, tw, which);
+}
+
 // with the phi^4 channel (W2 receives the y-inverse of phi*)
 template <typename R, int N, int E, int CT, int MODE>
 __global__ void __launch_bounds__(CT * (N / E))
@@ -269,7 +292,7 @@ k2d_col_inv_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<
 // gamma3 phi*^3 and writes W0 = k~_x W_x + i F_x(gamma3 phi*^3), W1 = W_y;
 // shared memory holds two sequences per row.
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int RPC, int MODE, bool G3 = false>
+template <typename R, int N, int E, int RPC, int MODE, bool G3 = false, bool PF = false>
 __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
                                              double* __restrict__ part, const SavScal* __restrict__ sc,
                                              const C_t<R>* __restrict__ tw, double* __restrict__ real_io,
@@ -326,6 +349,45 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
     fft_smem<C, N, E, true>(z, 1, lane, tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
+  } else if constexpr (PF) {
+    // the PFC model: the row's x-spectrum of phi* (Hermitian extension loaded
+    // straight into registers), inverse DFT to phi*(x), the E_1 sums
+    // sum phi*^4 and sum phi*^2, w = gamma3 phi*^3 - phi*, forward DFT into W0
+    const PC<R> pc(P);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = lane + i * T;
+      const bool direct = k <= N / 2;
+      const C f = W0[roff + (direct ? k : N - k)];
+      v[i] = direct ? f : cconj(f);
+    }
+    if (sc->status != DEV_OK) return;
+    fft_regs<C, N, E, true>(v, z, 1, lane, tw);
+    typename RD::acc acc4 = RD::zero(), acc2 = RD::zero();
+    const R g3 = pc.g3;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const R ph = v[i].x, p2 = ph * ph;
+      acc4 = RD::add(acc4, p2 * p2);
+      acc2 = RD::add(acc2, p2);
+      if (MODE == RW_NONLIN) v[i] = mk<C>(ph * (g3 * p2 - (R)1), (R)0);
+    }
+    if constexpr (MODE == RW_NONLIN) {
+      fft_regs<C, N, E, false>(v, z, 1, lane, tw);
+      const R sc1 = pc.invP;
+#pragma unroll
+      for (int i = 0; i < KH + 1; ++i) {
+        if (i == KH && lane != 0) break;
+        W0[roff + lane + i * T] = cscale(v[i], sc1);  // i == KH: the Nyquist entry N/2 (lane 0)
+      }
+    }
+    typename RD::acc t21[2] = {acc4, acc2};
+    block_red_multi<R, 2>(t21, red2);
+    if (threadIdx.x == 0) {
+      part[blockIdx.x] = RD::to_double(t21[0]);
+      part[gridDim.x + blockIdx.x] = RD::to_double(t21[1]);
+    }
   } else if constexpr (G3) {
     // sequence 0: Z = G_x + i G_y as below, G_x = i k~_x Y^-1 phi*; sequence 1:
     // the x-spectrum of phi* (Hermitian, so its inverse is real)
@@ -452,6 +514,14 @@ k2d_row(const Params P, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1, double
   k2d_row_body<R, N, E, RPC, MODE>(P, W0, W1, part, sc, tw, real_io);
 }
 
+// the PFC model (W0: y-inverse of phi* in, x-spectrum of gamma3 phi*^3 - phi* out)
+template <typename R, int N, int E, int RPC, int MODE>
+__global__ void __launch_bounds__(RPC * (N / E))
+k2d_row_pfc(const Params P, C_t<R>* __restrict__ W0, double* __restrict__ part, const SavScal* __restrict__ sc,
+            const C_t<R>* __restrict__ tw) {
+  k2d_row_body<R, N, E, RPC, MODE, false, true>(P, W0, nullptr, part, sc, tw, nullptr);
+}
+
 // with the phi^4 channel (W2: y-inverse of phi* in; W0 out: k~_x W_x + i F_x(gamma3 phi*^3))
 template <typename R, int N, int E, int RPC, int MODE>
 __global__ void __launch_bounds__(RPC * (N / E))
@@ -496,7 +566,7 @@ struct SolvePre {
 // float64 scalar algebra (both paths).
 __device__ inline SolvePre sav_solve_pre(const Params& P, const double* q, bool bdf1, const RIn& rin) {
   SolvePre o;
-  o.E1 = P.hd * (0.25 * P.beta * q[0] - q[1]) + P.C * P.vol;
+  o.E1 = P.hd * (P.e1c4 * q[0] + P.e1c2 * q[1]) + P.C * P.vol;
   o.S = sqrt(o.E1);
   o.iS = 1.0 / o.S;
   o.dt_iS = P.dt * o.iS;
@@ -566,7 +636,7 @@ __device__ inline void sav_scalar_solve(const Params& P, SavScal* sc, const doub
 // Column forward pass (thread layout as the inverse pass).
 // partG: 3 x gridDim.x doubles (gamma, eta, theta partial sums, without |Omega|).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int E, int CT, int MODE, bool G3 = false>
+template <typename R, int N, int E, int CT, int MODE, bool G3 = false, bool PF = false>
 __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, const C_t<R>* __restrict__ W0,
                                                  const C_t<R>* __restrict__ W1, C_t<R>* __restrict__ Nhat,
                                                  double* __restrict__ partG, const double* __restrict__ partE,
@@ -574,7 +644,8 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
                                                  const C_t<R>* __restrict__ tw, int target) {
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
-  constexpr int NF = (MODE == CF_TO_STATE) ? 1 : 2;
+  // PF (the PFC model): W0 holds the x-spectrum of N itself, one field
+  constexpr int NF = (MODE == CF_TO_STATE || PF) ? 1 : 2;
   static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT || MODE == CF_PART,
                 "the phi^4 channel is carried by the modes that form N_hat");
   constexpr int NTH = CT * T;
@@ -643,11 +714,13 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
       const int ky = lane + i * T;
       if (!col) continue;
       const size_t off = (size_t)ky * NH + kx;
-      const C wx = v[0][i], wy = v[1][i];
+      const C wx = v[0][i], wy = v[NF - 1][i];
       const R ktx = kderiv<R>(kx, N, pc.kfx), kty = kderiv<R>(ky, N, pc.kfy);
       // N_hat = -i (k~_x W_x + k~_y W_y)
       C nh;
-      if constexpr (G3) {
+      if constexpr (PF) {
+        nh = (off == 0) ? mk<C>(0, 0) : wx;  // gamma3 phi*^3 - phi*, its mean removed
+      } else if constexpr (G3) {
         // -i (Y(k~_x W_x + i W2) + k~_y W_y): the transform of gamma3 phi*^3 joins
         // N_hat, whose zero mode (the mean of gamma3 phi*^3) is removed
         const R ux = wx.x + kty * wy.x, uy = wx.y + kty * wy.y;
@@ -714,6 +787,15 @@ k2d_col_fwd(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
             SavScal* __restrict__ sc, unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw,
             int target) {
   k2d_col_fwd_body<R, N, E, CT, MODE>(P, S, W0, W1, Nhat, partG, partE, nE, sc, counter, tw, target);
+}
+
+// the PFC model (W0 holds the x-spectrum of gamma3 phi*^3 - phi*)
+template <typename R, int N, int E, int CT, int MODE>
+__global__ void __launch_bounds__(CT * (N / E))
+k2d_col_fwd_pfc(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, C_t<R>* __restrict__ Nhat,
+                double* __restrict__ partG, const double* __restrict__ partE, int nE, SavScal* __restrict__ sc,
+                unsigned* __restrict__ counter, const C_t<R>* __restrict__ tw) {
+  k2d_col_fwd_body<R, N, E, CT, MODE, false, true>(P, S, W0, nullptr, Nhat, partG, partE, nE, sc, counter, tw, 0);
 }
 
 // with the phi^4 channel (W0 holds k~_x W_x + i F_x(gamma3 phi*^3))
@@ -981,7 +1063,7 @@ __global__ void k2d_ghost(const Params P, Slots<R> S, const C_t<R>* __restrict__
     const int ky = (int)(off / NH), kx = (int)(off % NH);
     const R K2 = sym_K2<R>(kx, ky, N, pc);
     const C cu = cur[off], nh = Nhat[off];
-    const R L = pc.a + K2 * K2;
+    const R L = sym_L<R>(K2, pc);
     const R f = pc.dt * K2;
     dst[off] = mk<C>(cu.x + f * (nh.x + L * cu.x), cu.y + f * (nh.y + L * cu.y));
     if (off == 0) sc->zm[1 - p] = sc->zm[p];
@@ -991,7 +1073,8 @@ __global__ void k2d_ghost(const Params P, Slots<R> S, const C_t<R>* __restrict__
 // Spectral norms of the newest level phi = slot p and psi = 2 phi - slot (1-p),
 // without the zero mode (added in FP64 from zm):
 // part[0..G)   = sum w |phi_k|^2, part[G..2G) = sum w |k|^4 |phi_k|^2,
-// part[2G..3G) = sum w (a + |k|^4) |psi_k|^2.
+// part[2G..3G) = sum w L(k) |psi_k|^2 (L the symbol of L_N), part[3G..4G) =
+// sum w |k|^2 |phi_k|^2.
 template <typename R>
 __global__ void k2d_norms(const Params P, Slots<R> S, const SavScal* sc, double* part) {
   using C = C_t<R>;
@@ -1001,7 +1084,7 @@ __global__ void k2d_norms(const Params P, Slots<R> S, const SavScal* sc, double*
   const C* nw = S.at(p);
   const C* ol = S.at(1 - p);
   const size_t total = (size_t)N * NH;
-  double a0 = 0, a1 = 0, a2 = 0;
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   for (size_t off = blockIdx.x * (size_t)blockDim.x + threadIdx.x; off < total;
        off += (size_t)gridDim.x * blockDim.x) {
     if (off == 0) continue;
@@ -1012,17 +1095,21 @@ __global__ void k2d_norms(const Params P, Slots<R> S, const SavScal* sc, double*
     const C u = nw[off], v = ol[off];
     const double n2 = (double)u.x * u.x + (double)u.y * u.y;
     const double px = 2.0 * u.x - v.x, py = 2.0 * u.y - v.y;
+    const double Ls = P.pfc ? P.a + (1.0 - K2) * (1.0 - K2) : P.a + K2 * K2;
     a0 += w * n2;
     a1 += w * K2 * K2 * n2;
-    a2 += w * (P.a + K2 * K2) * (px * px + py * py);
+    a2 += w * Ls * (px * px + py * py);
+    a3 += w * K2 * n2;
   }
   const double t0 = block_sum(a0, red);
   const double t1 = block_sum(a1, red);
   const double t2 = block_sum(a2, red);
+  const double t3 = block_sum(a3, red);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = t0;
     part[gridDim.x + blockIdx.x] = t1;
     part[2 * gridDim.x + blockIdx.x] = t2;
+    part[3 * gridDim.x + blockIdx.x] = t3;
   }
 }
 
@@ -1081,9 +1168,33 @@ __global__ void k_scalar_op(const Params P, SavScal* sc, int op, const double* a
   const double s1 = warp_sum_array(a + na, na, lane);
   if (op == SO_R_NEWEST || op == SO_R_PREV) {
     if (lane == 0) {
-      const double E1 = P.hd * (0.25 * P.beta * s2 - s1) + P.C * P.vol;
+      const double E1 = P.hd * (P.e1c4 * s2 + P.e1c2 * s1) + P.C * P.vol;
       if (!(isfinite(E1) && E1 > 0.0)) { sc->status = DEV_NONFINITE; return; }
       if (op == SO_R_NEWEST) sc->r1 = sqrt(E1); else sc->r0 = sqrt(E1);
+    }
+    return;
+  }
+  if (op == SO_ENERGY && P.pfc) {
+    // the PFC model: E_N = gamma3/4 ||phi||_4^4 + a/2 ||phi||^2 - ||grad phi||^2 + 1/2 ||Delta_N phi||^2
+    // (eq. energy-PFC; s2 = sum phi^4 from the row pass), L = a + (1 + Delta)^2, whose zero-mode
+    // symbol is a + 1, and E_breve = 1/2 ||L^{1/2} phi||^2 + r^2
+    const double n0 = warp_sum_array(b, nb, lane);
+    const double n1 = warp_sum_array(b + nb, nb, lane);
+    const double n2 = warp_sum_array(b + 2 * nb, nb, lane);
+    const double n3 = warp_sum_array(b + 3 * nb, nb, lane);
+    if (lane == 0) {
+      const int p = sc->p;
+      const double z = sc->zm[p], zo = sc->zm[1 - p];
+      const double phi2 = P.vol * (n0 + z * z);
+      const double lap2 = P.vol * n1;
+      const double grad2 = P.vol * n3;
+      const double zp = 2.0 * z - zo;
+      const double Lpsi = P.vol * (n2 + (P.a + 1.0) * zp * zp);
+      const double Lphi = (P.a + 1.0) * phi2 - 2.0 * grad2 + lap2;
+      const double r1 = sc->r1, r0 = sc->r0;
+      sc->E_orig = 0.25 * P.g3 * P.hd * s2 + 0.5 * P.a * phi2 - grad2 + 0.5 * lap2;
+      sc->E_mod = 0.25 * (Lphi + Lpsi) + 0.5 * (r1 * r1 + (2.0 * r1 - r0) * (2.0 * r1 - r0));
+      sc->E_breve = 0.5 * Lphi + r1 * r1;
     }
     return;
   }

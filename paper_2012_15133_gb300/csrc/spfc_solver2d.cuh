@@ -133,7 +133,7 @@ class Solver2D final : public SolverBase {
     nG_ = GCOL;
     if (e == cudaSuccess) e = al((void**)&partE_, 2 * (size_t)nE_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partG_, 3 * (size_t)nG_ * sizeof(double));
-    if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&partN_, 4 * (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc_, sizeof(SavScal));  // pinned: small fast reads
@@ -214,7 +214,7 @@ class Solver2D final : public SolverBase {
   int init(const double* phi0, bool on_device, int mode) override {
     int rc = load_field(phi0, on_device, /*slot_rel=*/0, /*reset=*/true);
     if (rc) return rc;
-    if (mode == 0 && g3_on()) {  // BDF1 with the phi^4 term: the lazy form, completed at once
+    if (mode == 0 && lazy()) {  // BDF1 with the phi^4 term or the PFC model: the lazy form, completed at once
       rc = launch_col_inv(CI_GRAD, 0); if (rc) return rc;
       rc = launch_row(RW_NONLIN); if (rc) return rc;
       rc = launch_col_fwd(CF_BDF1, 0); if (rc) return rc;
@@ -280,6 +280,10 @@ class Solver2D final : public SolverBase {
   // (column inverse with the pending update, row pass, column forward with
   // the scalar solve) rather than row pass + fused column pass.
   int set_gamma3(double g3) override {
+    if (pfc_on()) {
+      err = "the PFC model takes its phi^4 coefficient from spfc_set_pfc";
+      return 1;
+    }
     if (inited) { int rc = finalize(); if (rc) return rc; }
     if (g3 != 0.0 && !W2_) {
       cudaError_t e = cudaMalloc((void**)&W2_, spec_bytes_);
@@ -304,6 +308,32 @@ class Solver2D final : public SolverBase {
     return 0;
   }
 
+  // The PFC model of Sec. 1 (eq. energy-PFC) with phi^4 coefficient g3 > 0,
+  // or back to the SPFC model with g3 = 0 (the optional phi^4 term then off).
+  int set_pfc(double g3) override {
+    if (inited) { int rc = finalize(); if (rc) return rc; }
+    if (g3 > 0.0) {
+      SPFC_CK(set_smem(k2d_col_inv_pfc<R, N, E, CT, CI_STEP>, smem_col(1)));
+      SPFC_CK(set_smem(k2d_col_inv_pfc<R, N, E, CT, CI_GRAD>, smem_col(1)));
+      SPFC_CK(set_smem(k2d_row_pfc<R, N, E, RPC, RW_NONLIN>, smem_row()));
+      SPFC_CK(set_smem(k2d_row_pfc<R, N, E, RPC, RW_ENERGY>, smem_row()));
+      SPFC_CK(set_smem(k2d_col_fwd_pfc<R, N, E, CT, CF_BDF2>, smem_col(1)));
+      SPFC_CK(set_smem(k2d_col_fwd_pfc<R, N, E, CT, CF_BDF1>, smem_col(1)));
+      SPFC_CK(set_smem(k2d_col_fwd_pfc<R, N, E, CT, CF_NHAT>, smem_col(1)));
+      P.pfc = 1;
+      P.g3 = g3;
+      P.C = 1.0 + 1.0 / (4.0 * g3);
+    } else {
+      P.pfc = 0;
+      P.g3 = 0.0;
+      P.C = 1.0 + 1.0 / P.beta;
+    }
+    fill_float_params(&P);
+    drop_graphs();
+    w_ready_ = false;
+    return 0;
+  }
+
   int dt_change(double dt) override {
     int rc = finalize(); if (rc) return rc;
     P.dt = dt;
@@ -321,8 +351,8 @@ class Solver2D final : public SolverBase {
   // ---- stepping ------------------------------------------------------------
   int step(long long n) override {
     if (n <= 0) return 0;
-    if (g3_on()) pend_ = true;  // the lazy three-pass steps leave their update pending
-    if (!w_ready_ && !g3_on()) {
+    if (lazy()) pend_ = true;  // the lazy three-pass steps leave their update pending
+    if (!w_ready_ && !lazy()) {
       // W <- inverse DFT in y of i k~ (2 phi^n - phi^{n-1}): the first half of a step
       int rc = finalize(); if (rc) return rc;
       rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
@@ -335,7 +365,7 @@ class Solver2D final : public SolverBase {
       }
       return 0;
     }
-    if (PERSIST && !g3_on()) {  // one cooperative launch per chunk of steps
+    if (PERSIST && !lazy()) {  // one cooperative launch per chunk of steps
       while (n > 0) {
         const long long k = n < kPersistMaxSteps ? n : kPersistMaxSteps;
         int rc = launch_persist((int)k);
@@ -464,12 +494,12 @@ class Solver2D final : public SolverBase {
     }
     trecs_.clear();
     evnext_ = 0;
-    if (PERSIST && !g3_on()) {
+    if (PERSIST && !lazy()) {
       kt->names = {"step"};
       kt->launches.assign(tcount_, tcount_ + 1);
       kt->ms.assign(tms_, tms_ + 1);
     } else {
-      kt->names = {"row", g3_on() ? "col_inv+col_fwd" : "col_fused"};
+      kt->names = {"row", lazy() ? "col_inv+col_fwd" : "col_fused"};
       kt->launches.assign(tcount_, tcount_ + 2);
       kt->ms.assign(tms_, tms_ + 2);
     }
@@ -485,9 +515,19 @@ class Solver2D final : public SolverBase {
   static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * CTP * sizeof(C); }
   static constexpr size_t smem_row() { return (size_t)RPC * (sp_len(N) + 1) * sizeof(C); }
 
-  bool g3_on() const { return P.g3 != 0.0; }
+  bool pfc_on() const { return P.pfc != 0; }
+  bool g3_on() const { return P.g3 != 0.0 && !pfc_on(); }  // the optional phi^4 term of the SPFC model
+  bool lazy() const { return g3_on() || pfc_on(); }        // steps in the lazy three-pass form
 
   int launch_col_inv(int mode, int which) {
+    if (pfc_on() && (mode == CI_STEP || mode == CI_GRAD)) {
+      if (mode == CI_STEP)
+        k2d_col_inv_pfc<R, N, E, CT, CI_STEP><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], sc_, tw_, which);
+      else
+        k2d_col_inv_pfc<R, N, E, CT, CI_GRAD><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, Nhat_, W_[0], sc_, tw_, which);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     if (g3_on() && (mode == CI_STEP || mode == CI_GRAD)) {
       if (mode == CI_STEP)
         k2d_col_inv_g3<R, N, E, CT, CI_STEP><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, Nhat_, W_[0], W_[1], W2_, sc_, tw_, which);
@@ -511,6 +551,14 @@ class Solver2D final : public SolverBase {
     return 0;
   }
   int launch_row(int mode) {
+    if (pfc_on() && (mode == RW_NONLIN || mode == RW_ENERGY)) {
+      if (mode == RW_NONLIN)
+        k2d_row_pfc<R, N, E, RPC, RW_NONLIN><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], partE_, sc_, tw_);
+      else
+        k2d_row_pfc<R, N, E, RPC, RW_ENERGY><<<GROW, RPC * T, smem_row(), st_>>>(P, W_[0], partE_, sc_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     if (g3_on() && (mode == RW_NONLIN || mode == RW_ENERGY)) {
       if (mode == RW_NONLIN)
         k2d_row_g3<R, N, E, RPC, RW_NONLIN><<<GROW, RPC * T, 2 * smem_row(), st_>>>(P, W_[0], W_[1], W2_, partE_, sc_, tw_);
@@ -538,6 +586,16 @@ class Solver2D final : public SolverBase {
   }
   int launch_col_fwd(int mode, int target) {
     if (mode == CF_BDF2 || mode == CF_BDF1) pend_ = true;  // the scalar solve leaves the update pending
+    if (pfc_on() && mode != CF_TO_STATE) {
+      if (mode == CF_BDF2)
+        k2d_col_fwd_pfc<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      else if (mode == CF_BDF1)
+        k2d_col_fwd_pfc<R, N, E, CT, CF_BDF1><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      else
+        k2d_col_fwd_pfc<R, N, E, CT, CF_NHAT><<<GCOL, CT * T, smem_col(1), st_>>>(P, S_, W_[0], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
+      SPFC_CK(cudaGetLastError());
+      return 0;
+    }
     if (g3_on() && mode != CF_TO_STATE) {
       if (mode == CF_BDF2)
         k2d_col_fwd_g3<R, N, E, CT, CF_BDF2><<<GCOL, CT * T, smem_col(2), st_>>>(P, S_, W_[0], W_[1], Nhat_, partG_, partE_, nE_, sc_, counter_, tw_);
@@ -633,7 +691,7 @@ class Solver2D final : public SolverBase {
   // one step with W prepared: row pass, then the fused column pass (which
   // prepares W for the next step)
   int launch_step_kernels() {
-    if (g3_on()) {  // lazy three-pass form: the update stays pending between steps
+    if (lazy()) {  // lazy three-pass form: the update stays pending between steps
       int rc = launch_col_inv(CI_STEP, 0); if (rc) return rc;
       rc = launch_row(RW_NONLIN); if (rc) return rc;
       return launch_col_fwd(CF_BDF2, 0);
@@ -713,7 +771,7 @@ class Solver2D final : public SolverBase {
 
   int timed_step() {
     int e0, e1, e2, rc;
-    if (g3_on()) {  // row pass in class 0, the two column passes in class 1
+    if (lazy()) {  // row pass in class 0, the two column passes in class 1
       int e3;
       if ((rc = ev(&e0)) || (rc = ev(&e1)) || (rc = ev(&e2)) || (rc = ev(&e3))) return rc;
       SPFC_CK(cudaEventRecord(evpool_[e0], st_));

@@ -32,6 +32,14 @@ struct Params {
   double g3;      // gamma3
   double g3b;     // gamma3 / beta (folded into the sum of s^2 that E_1 takes with beta/4)
   float g3_f, g3b_f;
+  // model: 0 the SPFC equation (the paper's), 1 the PFC model of Sec. 1
+  // (eq. energy-PFC; g3 is its phi^4 coefficient, beta unused), with the
+  // split L = a + (1 + Delta)^2, E_1 = g3/4 ||phi||_4^4 - 1/2 ||phi||^2 + C |Omega|
+  int pfc;
+  // E_1 = hd (e1c4 q0 + e1c2 q1) + C |Omega| from the row pass's sums q0, q1
+  // (SPFC: sum s^2 and sum s with beta/4 and -1; PFC: sum phi^4 and sum phi^2
+  // with g3/4 and -1/2)
+  double e1c4, e1c2;
   // the box lengths and eps exactly as given at creation (kf and a derive from them)
   double Lbox[3];
   double eps;

@@ -44,6 +44,7 @@ _SIGS = {
     "spfc_dt_change": (_I, [_P, _D]),
     "spfc_set_stabilization": (_I, [_P, _D]),
     "spfc_set_gamma3": (_I, [_P, _D]),
+    "spfc_set_pfc": (_I, [_P, _D]),
     "spfc_save": (_I, [_P, ct.c_char_p]),
     "spfc_load": (_I, [_P, ct.c_char_p]),
     "spfc_set_scalar_ring": (_I, [_P, _P, ct.c_int64]),
@@ -295,6 +296,13 @@ class Solver:
         """The stabilised scheme of Sec. 5.2 with constant A >= 0 (0: plain)."""
         self._check(self._lib.spfc_set_stabilization(self._h, float(A)))
         self.stab = float(A)
+        return self
+
+    def set_pfc(self, gamma3=1.0):
+        """Switch to the PFC model of Sec. 1 with phi^4 coefficient gamma3 > 0
+        (its own split: L = a + (1 + Delta)^2, E_1 = gamma3/4 ||phi||_4^4 -
+        1/2 ||phi||^2 + C |Omega|); gamma3 = 0 switches back to SPFC."""
+        self._check(self._lib.spfc_set_pfc(self._h, float(gamma3)))
         return self
 
     def set_gamma3(self, gamma3):
