@@ -80,9 +80,9 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
  * below), the persistent step: every step of a spfc_step call in one
  * cooperative launch (row pass, column forward pass, scalar solve, update
  * and the next column inverse pass behind bounded grid barriers). spfc_create
- * uses the grid's default, the fastest measured on GB300 (2D float32: 512 ->
- * 6, 128 and 256 -> 2, 16..64 -> 1; 2D float64: 512 -> 1, 128 and 256 -> 5,
- * otherwise 0), as does spfc_create_scheduled with schedule = -1; a schedule
+ * uses the grid's default, the autotuner's choice on GB300 (2D float32: 512
+ * -> 0, 256 -> 2, 128 -> 5, 16..64 -> 1; 2D float64: 512 -> 6, 128 and 256
+ * -> 5, otherwise 0), as does spfc_create_scheduled with schedule = -1; a schedule
  * in [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
  * autotuner times the choices. All schedules compute the same step; results
  * agree to rounding. spfc_schedule returns the handle's schedule. */
@@ -329,10 +329,12 @@ int spfc_fno_load(spfc_fno_t f, const char* path);
  * scheme, which stays its fallback and its judge. Each round:
  *  1. one call of the network predicts phi^{n+K} of every run from
  *     (phi^n, phi^{n-1}, eps, beta);
- *  2. energy test: a run whose prediction has the larger E_N (eq.
- *     energy-discrete-spectral) takes K plain SAV steps instead. After a copy
- *     restart with r = sqrt(E_1) the modified energy is E_N + C_beta |Omega|,
- *     so this is the modified-energy test;
+ *  2. energy test: the jump is rejected, and the run takes K plain SAV steps
+ *     instead, if the modified energy (eq. discrete energy) of the restarted
+ *     prediction exceeds that of the run's live two-level state (phi^n,
+ *     phi^{n-1}, r^n, r^{n-1}). After the copy restart with r = sqrt(E_1) the
+ *     former is E_N(prediction) + C_beta |Omega| (E_N of eq.
+ *     energy-discrete-spectral with the run's phi^4 term);
  *  3. every check_every rounds (round j with j % check_every == 0; 0: never)
  *     a surviving prediction is compared with K plain steps that run's twin
  *     takes from the same state (phi^n, phi^{n-1}, r^n, r^{n-1}); rel-L2 above
@@ -340,7 +342,7 @@ int spfc_fno_load(spfc_fno_t f, const char* path);
  *  4. an accepted prediction restarts the run with the copy start (Sec. 5.2:
  *     phi^{n+K-1} := phi^{n+K}, r = sqrt(E_1)).
  * net: a network of grid size n <= 256 (the energy test's limit), nruns <= its
- *    largest batch;
+ *    largest batch; runs of the PFC model (spfc_set_pfc) are refused;
  * runs: nruns initialised 2D handles on square n x n grids (their eps and
  *    beta feed the network), owned by the caller;
  * twins: nruns further 2D handles, distinct and none of them a run, each with
@@ -374,8 +376,10 @@ const char* spfc_surrogate_last_error(void);
  * out[3] (host): E_N(phi) (eq. energy-discrete-spectral), 1/2 ||L_N^{1/2} phi||^2,
  *    and the mass h^2 sum phi;
  * cuda_stream: the stream to run on (synchronised before returning).
- * The first call on a device, with that device current, looks up the
- * scratch array's device address and writes a twiddle table into it; make
+ * Every call looks up the scratch array's device address on the current
+ * device and reads an 8-byte marker from it (synchronously); the first call
+ * in a device context (the first on a device, or the first after
+ * cudaDeviceReset) also writes a twiddle table and the marker into it. Make
  * that first call before any stream capture. All calls share the one array
  * and leave their contents in it; calls that overlap on the GPU (other host
  * threads, other streams) race and must be serialised by the caller.

@@ -35,16 +35,16 @@ static int fail(spfc_t h, int code, const std::string& msg) {
   return code;
 }
 
-// Default launch schedule per grid, from flushed and L2-resident step times
-// measured on GB300: float32 bulk -- the persistent step (6) at N = 512 (equal
-// to schedule 0 on a flushed step, and a whole run in one launch), schedule 2
-// at 128 and 256, the persistent step (1) below; float64 -- bound by its
-// arithmetic, the shapes with the most threads (5 at 128 and 256, 1 at 512).
+// Default launch schedule per grid: the autotuner's choice on GB300 (the
+// smallest sum of flushed and L2-resident step time; autotune_cache.json):
+// float32 bulk -- 0 at 512, 2 at 256, 5 at 128, the persistent step (1) below;
+// float64 -- the persistent step (6) at 512, 5 at 128 and 256, 0 below.
 static int default_schedule(int d, int n, int precision) {
   if (d != 2) return 0;
-  if (precision == SPFC_FP64) return n == 512 ? 1 : ((n == 128 || n == 256) ? 5 : 0);
-  if (n == 512) return 6;
-  return (n == 128 || n == 256) ? 2 : 1;
+  if (precision == SPFC_FP64) return n == 512 ? 6 : ((n == 128 || n == 256) ? 5 : 0);
+  if (n == 512) return 0;
+  if (n == 256) return 2;
+  return n == 128 ? 5 : 1;
 }
 
 static int wrap(spfc_t h, int rc) {

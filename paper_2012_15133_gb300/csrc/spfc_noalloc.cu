@@ -37,25 +37,39 @@ struct DevSlot {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of g_scratch on this device
 };
+// A marker written into the array after the twiddle table: a new context on
+// the device (after cudaDeviceReset) reloads the module with the array
+// zeroed, possibly at another address, so each call checks both.
+constexpr unsigned long long kMagic = 0x5350464354574431ull;
+constexpr size_t kMagicOff = kBytes - sizeof(unsigned long long);
 constexpr int kMaxDev = 64;
 DevSlot g_dev[kMaxDev];
 std::mutex g_mu;
 thread_local std::string g_err;
 
-// Once per device, with that device current: look up the device address of
-// the scratch array (a host-side name of a __device__ array is only a
-// stand-in, never a device address) and write the twiddle table into it.
+// Every call, with the device current: look up the device address of the
+// scratch array (a host-side name of a __device__ array is only a stand-in,
+// never a device address); once per device context, write the twiddle table
+// and the marker into it.
 int setup_device(int dev, unsigned char** base) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (dev < 0 || dev >= kMaxDev) { g_err = "device index out of range"; return SPFC_EINVAL; }
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess) { g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return SPFC_ECUDA; }
+  if (g_dev[dev].ready) {
+    unsigned long long m = 0;
+    e = cudaMemcpy(&m, (unsigned char*)ptr + kMagicOff, sizeof(m), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { g_err = std::string("scratch check: ") + cudaGetErrorString(e); return SPFC_ECUDA; }
+    if (ptr != (void*)g_dev[dev].base || m != kMagic) g_dev[dev].ready = false;  // a new context
+  }
   if (!g_dev[dev].ready) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess) { g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e); return SPFC_ECUDA; }
     std::vector<double2> tw;
     host_twiddles<double>(tw);
     e = cudaMemcpy((unsigned char*)ptr + 3 * kSpec + kPart, tw.data(), kTw, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { g_err = std::string("twiddle upload: ") + cudaGetErrorString(e); return SPFC_ECUDA; }
+    e = cudaMemcpy((unsigned char*)ptr + kMagicOff, &kMagic, sizeof(kMagic), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { g_err = std::string("scratch marker: ") + cudaGetErrorString(e); return SPFC_ECUDA; }
     g_dev[dev].base = (unsigned char*)ptr;
     g_dev[dev].ready = true;
   }
@@ -79,7 +93,7 @@ int run(const Params& P, const double* phi, double* out, cudaStream_t st, unsign
   double* partS = partN + 3 * 1024;
   const C* tw = reinterpret_cast<const C*>(base + 3 * kSpec + kPart);
   SavScal* sc = reinterpret_cast<SavScal*>(base + 3 * kSpec + kPart + kTw);
-  static_assert(sizeof(SavScal) <= kScal, "scalar record must fit");
+  static_assert(sizeof(SavScal) + sizeof(unsigned long long) <= kScal, "scalar record and marker must fit");
   static_assert(GROW <= 1024 && 8 * (2 * 1024 + 3 * 1024 + 608) <= kPart, "partial sums must fit");
   Slots<double> S{{spec, spec}};
   const size_t scol = (size_t)sp_len(N) * (CT + 1) * sizeof(C);
@@ -105,7 +119,10 @@ int run(const Params& P, const double* phi, double* out, cudaStream_t st, unsign
   e = cudaMemcpyAsync(&h, sc, sizeof(SavScal), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return SPFC_ECUDA; }
-  if (h.status != DEV_OK) { g_err = "non-finite value in the field"; return SPFC_ENONFINITE; }
+  if (h.status != DEV_OK || !std::isfinite(h.E_orig) || !std::isfinite(h.E_mod) || !std::isfinite(h.zm[0])) {
+    g_err = "non-finite value in the field";
+    return SPFC_ENONFINITE;
+  }
   out[0] = h.E_orig;
   out[1] = h.E_mod;          // with phi^{n-1} = phi^n and r = 0: 1/2 ||L^{1/2} phi||^2
   out[2] = P.vol * h.zm[0];  // mass h^2 sum phi

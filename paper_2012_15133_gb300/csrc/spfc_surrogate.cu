@@ -1,6 +1,8 @@
 // Jump-with-fallback loop of the learned surrogate (declared in
 // include/spfc.h). One network call predicts phi^{n+K} for every run of a
-// round; each prediction is judged by the energy test and, every
+// round; each prediction is judged by the modified-energy test (eq.
+// discrete energy of the live two-level state against that of the
+// copy-restarted prediction) and, every
 // check_every rounds, against K plain SAV steps taken from the same state
 // by a twin solver; a rejected jump falls back to the plain steps. The loop
 // composes the library's own entry points (solver handles, the network, the
@@ -28,6 +30,18 @@ __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, size_
 __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
+}
+
+// One block: sum a^4 over n values in a fixed order (the phi^4 term of E_1).
+__global__ void __launch_bounds__(1024) k_sum_pow4(const double* __restrict__ a, size_t n, double* __restrict__ out) {
+  __shared__ double scratch[32];
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = a[i] * a[i];
+    s += v * v;
+  }
+  s = spfc::block_sum(s, scratch);
+  if (threadIdx.x == 0) out[0] = s;
 }
 
 // One block: sum (a - b)^2 and sum b^2 over n values in a fixed order.
@@ -88,6 +102,7 @@ int spfc_surrogate_advance(spfc_fno_t net, spfc_t* runs, spfc_t* twins, int nrun
     const spfc::Params& P = h->s->P;
     if (P.d != 2 || P.N != n || P.Lbox[0] != P.Lbox[1])
       return failx(SPFC_EINVAL, "runs must be square 2D grids of the network's size");
+    if (P.pfc) return failx(SPFC_EINVAL, "the surrogate serves SPFC runs (not the PFC model)");
     for (int k = 0; k < i; ++k)
       if (runs[k] == h) return failx(SPFC_EINVAL, "a run appears twice");
     if (check_every > 0) {
@@ -139,15 +154,27 @@ int spfc_surrogate_advance(spfc_fno_t net, spfc_t* runs, spfc_t* twins, int nrun
     for (int i = 0; i < nruns; ++i) {
       const spfc_t h = runs[i];
       const double L2[2] = {h->s->P.Lbox[0], h->s->P.Lbox[1]};
-      double e_now[3], e_new[3];
+      const spfc::Params& Pr = h->s->P;
+      double e_new[3], e_live = 0.0, s4 = 0.0;
       ++cnt[0];
       if (check_err) check_err[(size_t)j * nruns + i] = std::numeric_limits<double>::quiet_NaN();
-      rc = spfc_field_energy_noalloc(n, L2, eps[i], beta[i], cur + i * P, e_now, st);
-      if (!rc) rc = spfc_field_energy_noalloc(n, L2, eps[i], beta[i], pred + i * P, e_new, st);
+      // before: the modified energy of the live state (phi^n, phi^{n-1}, r^n, r^{n-1})
+      rc = spfc_energy(h, nullptr, &e_live, nullptr);
+      if (rc) return run_err(h, rc, "energy test");
+      // after the copy restart (phi^{n+K-1} = phi^{n+K}, r = sqrt(E_1)) the
+      // modified energy is E_N(prediction) + C_beta |Omega|, E_N with the
+      // run's phi^4 term
+      rc = spfc_field_energy_noalloc(n, L2, eps[i], beta[i], pred + i * P, e_new, st);
       if (rc) return failx(rc, std::string("energy test: ") + spfc_noalloc_last_error());
-      // with r = sqrt(E_1) after the copy restart, the modified energy of the
-      // restarted prediction is E_N + C_beta |Omega|: compare the E_N
-      if (e_new[0] > e_now[0]) {
+      if (Pr.g3 != 0.0) {
+        k_sum_pow4<<<1, 1024, 0, st>>>(pred + i * P, P, parts);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&s4, parts, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return failx(SPFC_ECUDA, std::string("energy test: ") + cudaGetErrorString(e));
+      }
+      const double e_after = e_new[0] + 0.25 * Pr.g3 * Pr.hd * s4 + Pr.C * Pr.vol;
+      if (e_after > e_live) {
         ++cnt[2];
         if (decisions) decisions[(size_t)j * nruns + i] = 1;
         if ((rc = spfc_step(h, K))) return run_err(h, rc, "fallback steps");

@@ -136,6 +136,8 @@ def field_energy_noalloc(phi, L, eps, beta, stream=None):
     if not (phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous() and phi.dim() == 2
             and phi.shape[0] == phi.shape[1]):
         raise ValueError("phi must be a square, contiguous float64 CUDA tensor")
+    if phi.device.index != torch.cuda.current_device():
+        raise ValueError("phi must live on the current CUDA device (the entry point runs there)")
     Ls = [float(L)] * 2 if np.isscalar(L) else [float(v) for v in L]
     out = (ct.c_double * 3)()
     sp = ct.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None else stream)

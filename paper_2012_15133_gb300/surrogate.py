@@ -12,10 +12,10 @@ training on trajectories of the batched solver. The loop:
   convention phi^{n+K-1} := phi^{n+K}, r = sqrt(E_1) (the paper's restart
   after a time-step change, Sec. 5);
 * the jump is rejected, and K plain SAV steps taken instead, if the modified
-  energy of the restarted state exceeds that of the current state. With
+  energy (the paper's discrete energy) of the restarted prediction exceeds
+  that of the live two-level state (phi^n, phi^{n-1}, r^n, r^{n-1}). With
   r = sqrt(E_1) the modified energy of a copy-restarted field is
-  E_N(phi) + C_beta |Omega|, so the test compares the original energies E_N
-  of phi^n and of the prediction;
+  E_N(phi) + C_beta |Omega|, E_N with the run's phi^4 term;
 * every ``check_every`` jumps, K plain steps from the same state judge the
   jump: rel-L2 above ``tol`` rejects it (and the plain result is kept).
 """

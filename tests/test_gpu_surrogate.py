@@ -62,15 +62,23 @@ def test_training_lowers_the_loss_on_training_and_held_out_trajectories(trained)
     assert hl < 0.2 * S.identity_loss(held), (hl, S.identity_loss(held))
 
 
+def _restarted_energy(pred, s, gamma3=0.0):
+    """The modified energy of a field after the copy restart, r = sqrt(E_1):
+    E_N(field) + C_beta |Omega|, E_N with the phi^4 term."""
+    from paper_2012_15133_gb300 import field_energy_noalloc
+    h2 = (s.L[0] / s.n[0]) * (s.L[1] / s.n[1])
+    e = field_energy_noalloc(pred, s.L[0], s.eps, s.beta)[0]
+    return e + 0.25 * gamma3 * h2 * float(torch.sum(pred ** 4)) + (1.0 + 1.0 / s.beta) * s.L[0] * s.L[1]
+
+
 def test_accepted_jumps_keep_energy_and_restart_from_the_prediction(trained):
-    from paper_2012_15133_gb300 import surrogate as S, field_energy_noalloc
+    from paper_2012_15133_gb300 import surrogate as S
     net = trained[0]
     sol = _solvers(4)
     accepted = 0
     for j in range(4):
         before = [s.get_field(0) for s in sol]
-        e_before = [field_energy_noalloc(torch.tensor(b, device="cuda"), s.L[0], s.eps, s.beta)[0]
-                    for b, s in zip(before, sol)]
+        e_before = [s.energy()[1] for s in sol]  # the modified energy of the live state
         cur = torch.tensor(np.stack(before), dtype=torch.float32, device="cuda")
         prev = torch.tensor(np.stack([s.get_field(1) for s in sol]), dtype=torch.float32, device="cuda")
         pred = net.predict(cur, prev, [s.eps for s in sol], [s.beta for s in sol]).double().cpu().numpy()
@@ -83,8 +91,9 @@ def test_accepted_jumps_keep_energy_and_restart_from_the_prediction(trained):
                 # the copy restart: both levels hold the prediction
                 assert np.max(np.abs(after - pred[i])) < 1e-6 * np.max(np.abs(pred[i]))
                 assert np.array_equal(s.get_field(1), after)
-                e_after = field_energy_noalloc(torch.tensor(after, device="cuda"), s.L[0], s.eps, s.beta)[0]
-                assert e_after <= e_before[i] + 1e-6 * abs(e_before[i])
+                e_after = s.energy()[1]  # the modified energy of the copy-restarted state
+                assert e_after <= e_before[i] * (1 + 1e-12)
+                assert abs(e_after - _restarted_energy(torch.tensor(after, device="cuda"), s)) < 1e-9 * e_after
             else:
                 assert what == "energy"
     assert accepted > 0
@@ -108,7 +117,7 @@ def test_rejected_jumps_are_exactly_the_plain_steps():
 def _reference_advance(solvers, net, K, jumps, check_every, tol):
     """The jump loop composed in Python from the binding's single calls: the
     decisions the library's native loop must reproduce."""
-    from paper_2012_15133_gb300 import Solver, field_energy_noalloc
+    from paper_2012_15133_gb300 import Solver
     R, n = len(solvers), solvers[0].n[0]
     cur = torch.empty((R, n, n), dtype=torch.float64, device="cuda")
     prev = torch.empty_like(cur)
@@ -121,8 +130,8 @@ def _reference_advance(solvers, net, K, jumps, check_every, tol):
         pred = net.predict(cur.float(), prev.float(), [s.eps for s in solvers], [s.beta for s in solvers]).double()
         check = check_every > 0 and j % check_every == 0
         for i, s in enumerate(solvers):
-            e_now = field_energy_noalloc(cur[i], s.L[0], s.eps, s.beta)[0]
-            e_new = field_energy_noalloc(pred[i], s.L[0], s.eps, s.beta)[0]
+            e_now = s.energy()[1]
+            e_new = _restarted_energy(pred[i], s, getattr(s, "gamma3", 0.0))
             if e_new > e_now:
                 decisions.append((j, i, "energy"))
                 s.step(K)
@@ -269,3 +278,19 @@ def test_what_the_trained_network_gains(trained):
           f"no change {err_none:.2e}; {log.as_dict()}; "
           f"Mpt-steps/s surrogate+fallback {pts / t_sur / 1e6:.0f}, plain {pts / t_plain / 1e6:.0f}")
     assert log.jumps == 8 * jumps
+
+
+def test_the_native_loop_judges_runs_with_the_phi4_term(trained):
+    """Runs with the phi^4 term (gamma3 = 0.5): the native loop's energy test
+    takes the term into the restarted prediction's modified energy, as the
+    loop composed from single calls does; the same decisions."""
+    from paper_2012_15133_gb300 import surrogate as S
+    net = trained[0]
+    a, b = _solvers(4), _solvers(4)
+    for s in a + b:
+        s.set_gamma3(0.5)
+    log = S.advance(a, net, K, 3, check_every=0)
+    dec, _ = _reference_advance(b, net, K, 3, 0, 1e-3)
+    assert log.decisions == dec
+    for sa, sb in zip(a, b):
+        assert np.array_equal(sa.get_field(0), sb.get_field(0))

@@ -25,12 +25,14 @@ def _built():
 
 
 def _reference(phi, n, L, eps, beta):
+    """The allocating path on the same field: E_N, and with both levels the
+    field and r = 0 the modified energy 1/2 ||L^{1/2} phi||^2; the mass."""
     from paper_2012_15133_gb300 import Solver
     s = Solver(2, n, L, eps, beta, 0.01, "fp64")
-    s.set_state(phi, phi, 1.0, 1.0)
-    E_orig, _, _ = s.energy()
+    s.set_state(phi, phi, 0.0, 0.0)
+    E_orig, E_half, _ = s.energy()
     mass, _ = s.mass()
-    return E_orig, mass
+    return E_orig, E_half, mass
 
 
 @pytest.mark.parametrize("n,L,eps,beta,seed", [(64, 32.0, 0.1, 1.0, 0), (256, 128.0, 0.25, 0.7, 3)])
@@ -40,14 +42,49 @@ def test_noalloc_matches_allocating_path_on_two_calls_in_a_row(n, L, eps, beta, 
     phi_a = noisy_field((n, n), 0.2, 0.05, seed)
     phi_b = noisy_field((n, n), 0.15, 0.08, seed + 1)
     for phi in (phi_a, phi_b):
-        E_ref, m_ref = _reference(phi, n, L, eps, beta)
+        E_ref, H_ref, m_ref = _reference(phi, n, L, eps, beta)
         dev = torch.tensor(phi, dtype=torch.float64, device="cuda")
         r1 = field_energy_noalloc(dev, L, eps, beta)
         r2 = field_energy_noalloc(dev, L, eps, beta)
         for r in (r1, r2):
             assert abs(r[0] - E_ref) <= TOL * abs(E_ref), (r[0], E_ref)
+            assert abs(r[1] - H_ref) <= TOL * abs(H_ref), (r[1], H_ref)
             assert abs(r[2] - m_ref) <= TOL * abs(m_ref), (r[2], m_ref)
         assert r1 == r2
+
+
+def test_noalloc_matches_the_oracle():
+    """Against the FP64 CPU oracle on a 64^2 field: E_N (eq.
+    energy-discrete-spectral), 1/2 ||L_N^{1/2} phi||^2 and the mass."""
+    import torch
+    from oracle import Oracle
+    from paper_2012_15133_gb300 import field_energy_noalloc
+    n, L, eps, beta = 64, (32.0, 32.0), 0.1, 1.3
+    phi = noisy_field((n, n), 0.2, 0.1, 5)
+    o = Oracle(2, n, L, eps, beta, 0.01)
+    r = field_energy_noalloc(torch.tensor(phi, dtype=torch.float64, device="cuda"), L, eps, beta)
+    E = o.model.E_orig(phi)
+    H = 0.5 * o.model.L_norm_sq(phi)
+    m = o.grid.mean_value(phi)
+    assert abs(r[0] - E) <= TOL * abs(E) and abs(r[1] - H) <= TOL * abs(H) and abs(r[2] - m) <= TOL * abs(m)
+
+
+def test_noalloc_reports_a_non_finite_field_and_recovers():
+    """A field with a NaN written in on the host comes back as SPFC_ENONFINITE
+    (4), with no state left behind: the next call on a clean field agrees with
+    the allocating path again."""
+    import torch
+    from paper_2012_15133_gb300 import SPFCError, field_energy_noalloc
+    n, L, eps, beta = 64, 32.0, 0.1, 1.0
+    bad = noisy_field((n, n), 0.2, 0.05, 7)
+    bad[3, 5] = np.nan
+    with pytest.raises(SPFCError) as ei:
+        field_energy_noalloc(torch.tensor(bad, dtype=torch.float64, device="cuda"), L, eps, beta)
+    assert ei.value.code == 4
+    good = noisy_field((n, n), 0.2, 0.05, 8)
+    E_ref, H_ref, m_ref = _reference(good, n, L, eps, beta)
+    r = field_energy_noalloc(torch.tensor(good, dtype=torch.float64, device="cuda"), L, eps, beta)
+    assert abs(r[0] - E_ref) <= TOL * abs(E_ref) and abs(r[1] - H_ref) <= TOL * abs(H_ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
