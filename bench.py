@@ -188,7 +188,7 @@ def measure_ensemble(steps, warmup, precision, peak, rank=0, world=1, dist=None)
     all_runs = [ensemble_run(i) for i in range(256)]
     mine = shard_runs([r["n"] for r in all_runs], world)[rank]
     runs = [all_runs[i] for i in mine]
-    b = Batch(runs, 0.02, precision)
+    b = Batch(runs, 0.02, precision, schedule="auto")
     for i, r in enumerate(runs):
         b.init(i, r["phi0"], "bdf1")
     b.step(max(3, warmup))
@@ -221,6 +221,7 @@ def measure_ensemble(steps, warmup, precision, peak, rank=0, world=1, dist=None)
         errs[str(r["n"])] = float(np.linalg.norm(b.get_field(i) - fr) / np.linalg.norm(fr))
         ref.close()
     return {"workload": "256-run 2D ensemble (64 each of 64^2..512^2), dt 0.02", "runs": 256,
+            "schedules": {str(n): b.schedule(n) for n in (64, 128, 256, 512)},
             "rel_l2_vs_fp64": max(errs.values()) if errs else None,
             "rel_l2_vs_fp64_per_class": errs,
             "points": points, "value": points / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
@@ -508,6 +509,10 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
 # the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,321,024
 # read, 0 written); None whenever the kernel changes after the capture
 TRAFFIC_STEP_512_FP32 = 4321024
+# the same for the two-kernel step (schedule 0) from the capture in
+# profiles/step2d_512_kernels_ncu_full.md (BDF2 instance of the fused column pass)
+TRAFFIC_COL_FUSED_512_FP32 = 4285184
+TRAFFIC_ROW_512_FP32 = 2132224
 
 
 def measure_precision_split(steps=1000, n=N_GRID):
@@ -647,7 +652,8 @@ def run_ours(args):
     # DRAM bytes (read + write) per launch from the committed ncu capture of the
     # 512^2 FP32 persistent step (profiles/step2d_512_fp32_persist_ncu.md);
     # None whenever the kernel changed after the capture
-    traffic_ncu = {("fp32", "step"): TRAFFIC_STEP_512_FP32}
+    traffic_ncu = {("fp32", "step"): TRAFFIC_STEP_512_FP32, ("fp32", "col_fused"): TRAFFIC_COL_FUSED_512_FP32,
+                   ("fp32", "row"): TRAFFIC_ROW_512_FP32}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,

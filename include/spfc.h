@@ -253,6 +253,22 @@ typedef struct spfc_batch_s* spfc_batch_t;
  * L[r], eps[r] (1 - eps > 0), beta[r] > 0; dt and precision shared. */
 int spfc_batch_create(int nruns, const int* n, const double* L, const double* eps, const double* beta, double dt,
                       int precision, void* cuda_stream, spfc_batch_t* out);
+/* As spfc_batch_create, with the tile shape of each grid-size class chosen:
+ * schedules[r] (nruns values, NULL for every default) is the Shape schedule
+ * of run r's class, -1 for the default of its size and precision (float32:
+ * 4 from N = 256, else 0; float64: 5 from N = 128, else 0); runs of one grid
+ * size must give the same value. The schedules a class can be built with
+ * (spfc_batch_schedule_valid): 0, 2, 4 and 5 from N = 128, 0 below. Every
+ * schedule computes the same steps (results agree to rounding); the
+ * autotuner times them. SPFC_EINVAL for a schedule not compiled for its
+ * size or runs of one size that disagree. */
+int spfc_batch_create_scheduled(int nruns, const int* n, const double* L, const double* eps, const double* beta,
+                                double dt, int precision, void* cuda_stream, const int* schedules,
+                                spfc_batch_t* out);
+/* 1 if a batch class of grid size n can be built with `schedule`, else 0. */
+int spfc_batch_schedule_valid(int n, int schedule);
+/* The schedule of the batch's class of grid size n (-1: no such class). */
+int spfc_batch_schedule(spfc_batch_t b, int n);
 /* Start run `run` from phi0 (host, n[run]^2 float64 values) with spfc_start `mode`. */
 int spfc_batch_init(spfc_batch_t b, int run, const double* phi0, int mode);
 /* Set both time levels and the auxiliary scalars of one run directly, as

@@ -48,6 +48,94 @@ def lookup(d, n, precision) -> int:
         return 0
 
 
+def _batch_key(n, precision) -> str:
+    return f"{_gpu_name()}|batch|n{int(n)}|{'fp64' if _PREC[precision] == 0 else 'fp32'}"
+
+
+def lookup_batch(n, precision) -> int:
+    """Tuned batch schedule of grid size n for this GPU (-1, the default, if untuned)."""
+    try:
+        with open(cache_path()) as f:
+            table = json.load(f)
+        return int(table.get(_batch_key(n, precision), {}).get("schedule", -1))
+    except (OSError, ValueError):
+        return -1
+
+
+def batch_schedules(n):
+    """The schedules a batch class of grid size n can be built with."""
+    from .spfc import load_library
+    lib = load_library()
+    return [s for s in range(6) if lib.spfc_batch_schedule_valid(int(n), s)]
+
+
+def _batch_runs(n, count):
+    """Ensemble runs of one grid size (the ensemble recipe at size n)."""
+    from seeded_inputs import ensemble_run
+    return [ensemble_run(i, sizes=(n,)) for i in range(count)]
+
+
+def time_batch(n, precision, schedule, runs=16, steps=64):
+    """us per batched step of `runs` runs at n^2 (graph replay; the class's
+    working set, 5 half spectra per run, exceeds the L2 from 512^2 x 16)."""
+    import torch
+    from .spfc import Batch
+    rs = _batch_runs(n, runs)
+    b = Batch(rs, 0.02, precision, schedule={n: schedule})
+    for i, r in enumerate(rs):
+        b.init(i, r["phi0"], "bdf1")
+    b.step(16)
+    b.sync()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / steps
+
+
+def check_batch(n, precision, schedule, runs=4, nsteps=3):
+    """Relative L2 difference of a batch schedule's fields from the default's."""
+    from .spfc import Batch
+    rs = _batch_runs(n, runs)
+    out = []
+    for sch in (-1, schedule):
+        b = Batch(rs, 0.02, precision, schedule={n: sch})
+        for i, r in enumerate(rs):
+            b.init(i, r["phi0"], "bdf1")
+        b.step(nsteps)
+        out.append(np.stack([b.get_field(i) for i in range(runs)]))
+    return float(np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]))
+
+
+def tune_batch(n, precision, write=True, verbose=True):
+    """Time every batch schedule of grid size n (after the parity check) and
+    store the fastest under the key (GPU, batch, n, precision)."""
+    tol = 1e-12 if _PREC[precision] == 0 else 1e-5
+    results = {}
+    for sch in batch_schedules(n):
+        err = check_batch(n, precision, sch)
+        if not err < tol:
+            raise RuntimeError(f"batch schedule {sch} disagrees with the default (rel-L2 {err:.2e})")
+        us = time_batch(n, precision, sch)
+        results[sch] = {"step_us": us, "rel_l2_vs_default": err}
+        if verbose:
+            print(f"batch n={n} {precision} schedule {sch}: {us:.1f} us per batched step, rel-L2 {err:.1e}")
+    best = min(results, key=lambda k: results[k]["step_us"])
+    if write:
+        path = cache_path()
+        try:
+            with open(path) as fh:
+                table = json.load(fh)
+        except (OSError, ValueError):
+            table = {}
+        table[_batch_key(n, precision)] = {"schedule": best, "timings": results}
+        with open(path, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+    return best, results
+
+
 def _field(n):
     """A fixed synthetic initial state (mean 0.2, noise 0.02): timing input only."""
     rng = np.random.default_rng(12345)
@@ -125,13 +213,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, nargs="+", default=[512, 256, 128])
     ap.add_argument("--precision", nargs="+", default=["fp32", "fp64"])
+    ap.add_argument("--batch", action="store_true", help="tune the batched ensemble's classes instead")
     args = ap.parse_args()
     from .build import build
     build()
     for prec in args.precision:
         for n in args.n:
-            best, _ = tune(n, prec)
-            print(f"best schedule for n={n} {prec}: {best}")
+            if args.batch:
+                best, _ = tune_batch(n, prec)
+                print(f"best batch schedule for n={n} {prec}: {best}")
+            else:
+                best, _ = tune(n, prec)
+                print(f"best schedule for n={n} {prec}: {best}")
 
 
 if __name__ == "__main__":

@@ -130,7 +130,7 @@ class BatchClassBase {
   virtual int run_energy(int local, double* e3) = 0;
   virtual int set_gamma3(int local, double g3) = 0;     // the phi^4 term of one run
   virtual int64_t device_bytes() const = 0;
-  int N = 0, nruns = 0;
+  int N = 0, nruns = 0, schedule = 0;
   std::vector<int> runs;  // global run indices
   std::string err;
 };
@@ -143,10 +143,18 @@ template <typename R, int N> constexpr int batch_sched() {
   return sizeof(R) == 8 ? (N >= 128 ? 5 : 0) : (N >= 256 ? 4 : 0);
 }
 
-template <typename R, int N_>
+// The tile shapes (Shape2D schedules) a batch class can be built with: from
+// N = 128 the four that fill whole sectors or give the most threads (0, 2,
+// 4, 5), one below. The autotuner times them per grid size and precision.
+inline bool batch_schedule_valid(int N, int sched) {
+  if (N < 128) return sched == 0;
+  return sched == 0 || sched == 2 || sched == 4 || sched == 5;
+}
+
+template <typename R, int N_, int SCHED>
 class BatchClass final : public BatchClassBase {
   using C = C_t<R>;
-  using SH = Shape2D<N_, batch_sched<R, N_>()>;
+  using SH = Shape2D<N_, SCHED>;
   static constexpr int NH = N_ / 2 + 1;
   static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RPC = SH::RPC, CTP = (CT == 1) ? 1 : CT + 1;
   static constexpr int GCOL = (NH + CT - 1) / CT, GROW = N_ / RPC;
@@ -376,38 +384,43 @@ class BatchClass final : public BatchClassBase {
   bool g3_ = false;  // some run of the class has the phi^4 term
 };
 
-template <typename R>
-BatchClassBase* make_batch_class(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
-                                 std::string* err) {
-  BatchClassBase* c = nullptr;
-  int rc = 0;
-  switch (N) {
-#define SPFC_BATCH_CASE(NN)                                   \
-  case NN: {                                                 \
-    auto* b = new BatchClass<R, NN>(params, st);             \
-    rc = b->setup();                                         \
-    c = b;                                                   \
-    break;                                                   \
-  }
-    SPFC_BATCH_CASE(16)
-    SPFC_BATCH_CASE(32)
-    SPFC_BATCH_CASE(64)
-    SPFC_BATCH_CASE(128)
-    SPFC_BATCH_CASE(256)
-    SPFC_BATCH_CASE(512)
-#undef SPFC_BATCH_CASE
-    default:
-      *status = 1;
-      *err = "batch grid sizes must be one of 16, 32, 64, 128, 256, 512";
-      return nullptr;
-  }
+template <typename R, int N, int SCHED>
+BatchClassBase* new_batch_class(const std::vector<Params>& params, cudaStream_t st, int* status,
+                                std::string* err) {
+  auto* b = new BatchClass<R, N, SCHED>(params, st);
+  const int rc = b->setup();
   if (rc) {
     *status = rc;
-    *err = c->err;
-    delete c;
+    *err = b->err;
+    delete b;
     return nullptr;
   }
-  return c;
+  b->schedule = SCHED;
+  return b;
+}
+
+// One grid size N >= 128, every batch schedule (one translation unit per
+// size and precision, compiled in parallel).
+template <typename R, int N>
+BatchClassBase* make_batch_class_n(int sched, const std::vector<Params>& params, cudaStream_t st, int* status,
+                                   std::string* err) {
+  switch (sched) {
+    case 2: return new_batch_class<R, N, 2>(params, st, status, err);
+    case 4: return new_batch_class<R, N, 4>(params, st, status, err);
+    case 5: return new_batch_class<R, N, 5>(params, st, status, err);
+    default: return new_batch_class<R, N, 0>(params, st, status, err);
+  }
+}
+
+// Grids below 128 (one schedule).
+template <typename R>
+BatchClassBase* make_batch_class_small(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
+                                       std::string* err) {
+  switch (N) {
+    case 16: return new_batch_class<R, 16, 0>(params, st, status, err);
+    case 32: return new_batch_class<R, 32, 0>(params, st, status, err);
+    default: return new_batch_class<R, 64, 0>(params, st, status, err);
+  }
 }
 
 }  // namespace spfc

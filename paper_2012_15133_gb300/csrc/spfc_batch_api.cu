@@ -9,15 +9,45 @@
 #include "../../include/spfc.h"
 #include "spfc_internal.h"
 
-namespace spfc {
-class BatchClassBase;
-BatchClassBase* make_batch_class_f32(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
-                                     std::string* err);
-BatchClassBase* make_batch_class_f64(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
-                                     std::string* err);
-}  // namespace spfc
-
 #include "spfc_batch.cuh"
+
+namespace spfc {
+#define SPFC_BATCH_DECL(P)                                                                                      \
+  BatchClassBase* make_batch_class_##P##_small(int, const std::vector<Params>&, cudaStream_t, int*, std::string*); \
+  BatchClassBase* make_batch_class_##P##_128(int, const std::vector<Params>&, cudaStream_t, int*, std::string*);   \
+  BatchClassBase* make_batch_class_##P##_256(int, const std::vector<Params>&, cudaStream_t, int*, std::string*);   \
+  BatchClassBase* make_batch_class_##P##_512(int, const std::vector<Params>&, cudaStream_t, int*, std::string*);
+SPFC_BATCH_DECL(f32)
+SPFC_BATCH_DECL(f64)
+#undef SPFC_BATCH_DECL
+
+// A class of grid size N with a batch schedule (-1: the default of the size
+// and precision).
+static BatchClassBase* make_class(int N, int precision, int sched, const std::vector<Params>& ps, cudaStream_t st,
+                                  int* status, std::string* err) {
+  const bool f64 = precision == SPFC_FP64;
+  if (sched < 0) {
+    if (N >= 128) sched = f64 ? 5 : (N >= 256 ? 4 : 0);
+    else sched = 0;
+  }
+  if (!batch_schedule_valid(N, sched)) {
+    *status = SPFC_EINVAL;
+    *err = "batch schedule " + std::to_string(sched) + " is not compiled for N = " + std::to_string(N);
+    return nullptr;
+  }
+  switch (N) {
+    case 16: case 32: case 64:
+      return f64 ? make_batch_class_f64_small(N, ps, st, status, err) : make_batch_class_f32_small(N, ps, st, status, err);
+    case 128: return f64 ? make_batch_class_f64_128(sched, ps, st, status, err) : make_batch_class_f32_128(sched, ps, st, status, err);
+    case 256: return f64 ? make_batch_class_f64_256(sched, ps, st, status, err) : make_batch_class_f32_256(sched, ps, st, status, err);
+    case 512: return f64 ? make_batch_class_f64_512(sched, ps, st, status, err) : make_batch_class_f32_512(sched, ps, st, status, err);
+    default:
+      *status = SPFC_EINVAL;
+      *err = "batch grid sizes must be one of 16, 32, 64, 128, 256, 512";
+      return nullptr;
+  }
+}
+}  // namespace spfc
 
 using spfc::BatchClassBase;
 using spfc::Params;
@@ -83,12 +113,37 @@ extern "C" {
 
 int spfc_batch_create(int nruns, const int* n, const double* L, const double* eps, const double* beta, double dt,
                       int precision, void* cuda_stream, spfc_batch_t* out) {
+  return spfc_batch_create_scheduled(nruns, n, L, eps, beta, dt, precision, cuda_stream, nullptr, out);
+}
+
+int spfc_batch_schedule_valid(int n, int schedule) { return spfc::batch_schedule_valid(n, schedule) ? 1 : 0; }
+
+int spfc_batch_schedule(spfc_batch_t b, int n) {
+  if (!b) return -1;
+  for (auto& c : b->classes)
+    if (c->N == n) return c->schedule;
+  return -1;
+}
+
+int spfc_batch_create_scheduled(int nruns, const int* n, const double* L, const double* eps, const double* beta,
+                                double dt, int precision, void* cuda_stream, const int* schedules,
+                                spfc_batch_t* out) {
   if (!out) { g_batch_create_err = "out is NULL"; return SPFC_EINVAL; }
   *out = nullptr;
   if (nruns <= 0 || !n || !L || !eps || !beta) { g_batch_create_err = "invalid run list"; return SPFC_EINVAL; }
   if (!(dt > 0.0) || !std::isfinite(dt)) { g_batch_create_err = "dt must be positive"; return SPFC_EINVAL; }
   if (precision != SPFC_FP64 && precision != SPFC_FP32_BULK) { g_batch_create_err = "unknown precision"; return SPFC_EINVAL; }
   std::map<int, std::vector<int>> by_n;
+  std::map<int, int> sched_of;
+  for (int r = 0; r < nruns; ++r) {
+    const int sr = schedules ? schedules[r] : -1;
+    auto it = sched_of.find(n[r]);
+    if (it == sched_of.end()) sched_of[n[r]] = sr;
+    else if (it->second != sr) {
+      g_batch_create_err = "runs of one grid size must share one schedule";
+      return SPFC_EINVAL;
+    }
+  }
   for (int r = 0; r < nruns; ++r) {
     if (!(L[r] > 0.0) || !(1.0 - eps[r] > 0.0) || !(beta[r] > 0.0)) {
       g_batch_create_err = "run " + std::to_string(r) + ": need L > 0, 1 - eps > 0, beta > 0";
@@ -123,8 +178,7 @@ int spfc_batch_create(int nruns, const int* n, const double* L, const double* ep
     }
     int status = 0;
     std::string err;
-    BatchClassBase* c = precision == SPFC_FP64 ? spfc::make_batch_class_f64(kv.first, ps, b->st, &status, &err)
-                                              : spfc::make_batch_class_f32(kv.first, ps, b->st, &status, &err);
+    BatchClassBase* c = spfc::make_class(kv.first, precision, sched_of[kv.first], ps, b->st, &status, &err);
     if (!c) { g_batch_create_err = err; return status ? status : SPFC_ECUDA; }
     c->runs = kv.second;
     for (size_t i = 0; i < kv.second.size(); ++i) b->where[kv.second[i]] = {(int)b->classes.size(), (int)i};

@@ -1,9 +1,9 @@
-// float64 batched ensemble classes.
+// float64 batched ensemble classes for grids below 128.
 #include "spfc_batch.cuh"
 
 namespace spfc {
-BatchClassBase* make_batch_class_f64(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
-                                      std::string* err) {
-  return make_batch_class<double>(N, params, st, status, err);
+BatchClassBase* make_batch_class_f64_small(int N, const std::vector<Params>& params, cudaStream_t st, int* status,
+                                           std::string* err) {
+  return make_batch_class_small<double>(N, params, st, status, err);
 }
 }  // namespace spfc

@@ -1,0 +1,9 @@
+// float64 batched ensemble classes for 128 x 128 grids (every batch schedule).
+#include "spfc_batch.cuh"
+
+namespace spfc {
+BatchClassBase* make_batch_class_f64_128(int sched, const std::vector<Params>& params, cudaStream_t st,
+                                         int* status, std::string* err) {
+  return make_batch_class_n<double, 128>(sched, params, st, status, err);
+}
+}  // namespace spfc

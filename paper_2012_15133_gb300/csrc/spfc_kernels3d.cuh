@@ -251,22 +251,50 @@ k3d_zfwd_g3(const Params P, Slots<R> S, const C_t<R>* __restrict__ W0, const C_t
   k3d_zfwd_body<R, N, E, CT, MODE, true>(P, S, W0, W1, Nhat, partG, sc, tw, 0);
 }
 
-// One block: reduce the E_1 and gamma/eta/theta partial sums and solve the
-// scalar system; the update is then applied by the z-inverse pass into slot
-// 1 - p_old, so p flips here.
+// Reduce the E_1 and gamma/eta/theta partial sums and solve the scalar
+// system; the update is then applied by the z-inverse pass into slot
+// 1 - p_old, so p flips here. The sums are float64 (several thousand
+// partials per array), spread over the grid: block b sums a fixed contiguous
+// chunk of each array, and the last block to arrive (an arrival counter that
+// it resets) sums the chunk sums and solves. Fixed order, so deterministic.
+constexpr int kScalarBlocks = 64;
+
 template <typename R>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k3d_scalar(const Params P, SavScal* __restrict__ sc, const double* __restrict__ partE, int nE,
-           const double* __restrict__ partG, int nG, int bdf1) {
+           const double* __restrict__ partG, int nG, int bdf1, double* __restrict__ chunk,
+           unsigned* __restrict__ counter) {
   __shared__ double red5[5][32];
   __shared__ double qres[5];
+  __shared__ bool am_last;
   if (sc->status != DEV_OK) return;
-  const double* arr[5] = {partE, partE + nE, partG, partG + nG, partG + 2 * nG};
-  const int cnt[5] = {nE, nE, nG, nG, nG};
-  block_sum_arrays<5>(arr, cnt, qres, red5);
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int cE = (nE + nb - 1) / nb, cG = (nG + nb - 1) / nb;
+  const int e0 = min(b * cE, nE), g0 = min(b * cG, nG);
+  const int ne = min(cE, nE - e0), ng = min(cG, nG - g0);
+  {
+    const double* arr[5] = {partE + e0, partE + nE + e0, partG + g0, partG + nG + g0, partG + 2 * nG + g0};
+    const int cnt[5] = {ne, ne, ng, ng, ng};
+    block_sum_arrays<5>(arr, cnt, qres, red5);
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) chunk[q * nb + b] = qres[q];
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  {
+    const double* arr[5] = {chunk, chunk + nb, chunk + 2 * nb, chunk + 3 * nb, chunk + 4 * nb};
+    const int cnt[5] = {nb, nb, nb, nb, nb};
+    block_sum_arrays<5>(arr, cnt, qres, red5);
+  }
   if (threadIdx.x == 0) {
     const SolveOut o = sav_solve(P, qres, bdf1 != 0, RIn(sc));
     sav_commit(sc, o, 1 - sc->p, PEND_NONE);
+    *counter = 0u;
   }
 }
 

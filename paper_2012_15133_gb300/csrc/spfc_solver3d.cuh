@@ -50,6 +50,8 @@ class Solver3D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&real_, (size_t)N * N * N * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partE_, 2 * (size_t)nE_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partG_, 3 * (size_t)nG_ * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&chunk_, 5 * (size_t)kScalarBlocks * sizeof(double));
+    if (e == cudaSuccess) e = al((void**)&counter_, sizeof(unsigned));
     if (e == cudaSuccess) e = al((void**)&partN_, 3 * (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
@@ -64,6 +66,7 @@ class Solver3D final : public SolverBase {
     SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
     SavScal z{};
     SPFC_CK(cudaMemcpy(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemset(counter_, 0, sizeof(unsigned)));
     SPFC_CK(cudaMemset(S_.s[0], 0, sb));
     SPFC_CK(cudaMemset(S_.s[1], 0, sb));
     SPFC_CK(cudaMemset(Nhat_, 0, sb));
@@ -93,7 +96,7 @@ class Solver3D final : public SolverBase {
     if (g8_) cudaGraphExecDestroy(g8_);
     for (auto ev : evpool_) cudaEventDestroy(ev);
     if (cap_st_) cudaStreamDestroy(cap_st_);
-    void* ptrs[] = {S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W_[2], W3_, real_, partE_, partG_, partN_, partS_, sc_,
+    void* ptrs[] = {chunk_, counter_, S_.s[0], S_.s[1], Nhat_, W_[0], W_[1], W_[2], W3_, real_, partE_, partG_, partN_, partS_, sc_,
                     tw_};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -418,7 +421,7 @@ class Solver3D final : public SolverBase {
     return 0;
   }
   int scalar(bool bdf1) {
-    k3d_scalar<R><<<1, 1024, 0, st_>>>(P, sc_, partE_, nE_, partG_, nG_, bdf1 ? 1 : 0);
+    k3d_scalar<R><<<kScalarBlocks, 256, 0, st_>>>(P, sc_, partE_, nE_, partG_, nG_, bdf1 ? 1 : 0, chunk_, counter_);
     SPFC_CK(cudaGetLastError());
     return 0;
   }
@@ -537,6 +540,8 @@ class Solver3D final : public SolverBase {
   C* W3_ = nullptr;  // fourth work array of the phi^4 term (allocated on demand)
   double* real_ = nullptr;
   double *partE_ = nullptr, *partG_ = nullptr, *partN_ = nullptr, *partS_ = nullptr;
+  double* chunk_ = nullptr;    // chunk sums of the spread scalar reduction
+  unsigned* counter_ = nullptr; // its arrival counter (reset by the last block)
   SavScal* sc_ = nullptr;
   SavScal* hsc_ = nullptr;  // pinned host copy of the record
   C* tw_ = nullptr;

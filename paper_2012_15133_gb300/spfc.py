@@ -57,6 +57,10 @@ _SIGS = {
     "spfc_destroy": (None, [_P]),
     "spfc_last_error": (ct.c_char_p, [_P]),
     "spfc_batch_create": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_P)]),
+    "spfc_batch_create_scheduled": (_I, [_I, ct.POINTER(_I), _DP, _DP, _DP, _D, _I, _P, ct.POINTER(_I),
+                                         ct.POINTER(_P)]),
+    "spfc_batch_schedule_valid": (_I, [_I, _I]),
+    "spfc_batch_schedule": (_I, [_P, _I]),
     "spfc_batch_init": (_I, [_P, _I, _P, _I]),
     "spfc_batch_set_state": (_I, [_P, _I, _P, _P, _D, _D]),
     "spfc_batch_set_gamma3": (_I, [_P, _I, _D]),
@@ -358,9 +362,12 @@ class Solver:
 class Batch:
     """Batched ensemble of independent 2D runs (see include/spfc.h).
 
-    runs: sequence of dicts with keys n, L, eps, beta (square boxes)."""
+    runs: sequence of dicts with keys n, L, eps, beta (square boxes).
+    schedule: None (each grid size's default), "auto" (the autotuner's table
+    for this GPU, the default where it has no entry), an int for every class
+    of N >= 128, or a dict {n: schedule}."""
 
-    def __init__(self, runs, dt, precision="fp32", stream=None):
+    def __init__(self, runs, dt, precision="fp32", stream=None, schedule=None):
         self._lib = load_library()
         self.runs = [dict(r) for r in runs]
         k = len(self.runs)
@@ -370,8 +377,19 @@ class Batch:
         bs = (ct.c_double * k)(*[float(r["beta"]) for r in self.runs])
         sp = _current_stream_ptr() if stream is None else ct.c_void_p(
             stream if isinstance(stream, int) else stream.cuda_stream)
+        scheds = None
+        if schedule is not None:
+            def pick(n):
+                if schedule == "auto":
+                    from .autotune import lookup_batch
+                    return lookup_batch(n, precision)
+                if isinstance(schedule, dict):
+                    return int(schedule.get(n, -1))
+                return int(schedule) if n >= 128 else -1
+            scheds = (ct.c_int * k)(*[pick(int(r["n"])) for r in self.runs])
         h = ct.c_void_p()
-        rc = self._lib.spfc_batch_create(k, ns, Ls, es, bs, float(dt), _PREC[precision], sp, ct.byref(h))
+        rc = self._lib.spfc_batch_create_scheduled(k, ns, Ls, es, bs, float(dt), _PREC[precision], sp, scheds,
+                                                   ct.byref(h))
         if rc != 0:
             raise SPFCError(rc, self._lib.spfc_batch_last_error(None).decode())
         self._h = h
@@ -434,6 +452,10 @@ class Batch:
     @property
     def points(self):
         return int(self._lib.spfc_batch_points(self._h))
+
+    def schedule(self, n):
+        """The tile schedule of the class of grid size n (-1: none)."""
+        return int(self._lib.spfc_batch_schedule(self._h, int(n)))
 
     def close(self):
         if getattr(self, "_h", None):

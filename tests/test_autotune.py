@@ -62,9 +62,33 @@ def test_the_committed_table_names_compiled_schedules():
     with open(A.DEFAULT_CACHE) as f:
         table = json.load(f)
     assert table
+    from paper_2012_15133_gb300.autotune import batch_schedules
     for key, entry in table.items():
         gpu, d, n, prec = key.split("|")
-        assert d == "d2" and prec in ("fp32", "fp64")
+        assert d in ("d2", "batch") and prec in ("fp32", "fp64")
+        if d == "batch":
+            assert entry["schedule"] in batch_schedules(int(n[1:])), key
+            times = {int(s): t["step_us"] for s, t in entry["timings"].items()}
+            assert set(times) == set(batch_schedules(int(n[1:]))), key
+            assert entry["schedule"] == min(times, key=times.get), key
+            continue
         assert 0 <= entry["schedule"] < num_schedules(2, int(n[1:])), key
         sums = {int(s): t["resident_us"] + t["flushed_us"] for s, t in entry["timings"].items()}
         assert entry["schedule"] == min(sums, key=sums.get), key
+
+
+def test_batch_tuner_picks_the_fastest_and_lookup_reads_it(tmp_path, monkeypatch):
+    """The batch tuner times every compiled batch schedule of a grid size (the
+    GPU parts faked), refuses one that disagrees, and Batch(schedule="auto")
+    reads the table."""
+    monkeypatch.setenv("SPFC_TUNE_CACHE", str(tmp_path / "t.json"))
+    monkeypatch.setattr(A, "_gpu_name", lambda: "FakeGPU")
+    monkeypatch.setattr(A, "batch_schedules", lambda n: [0, 2, 4, 5])
+    monkeypatch.setattr(A, "check_batch", lambda n, p, s: 0.0)
+    monkeypatch.setattr(A, "time_batch", lambda n, p, s: {0: 30.0, 2: 25.0, 4: 20.0, 5: 22.0}[s])
+    assert A.lookup_batch(512, "fp32") == -1
+    best, res = A.tune_batch(512, "fp32", verbose=False)
+    assert best == 4 and A.lookup_batch(512, "fp32") == 4 and A.lookup_batch(256, "fp32") == -1
+    monkeypatch.setattr(A, "check_batch", lambda n, p, s: 1e-3 if s == 5 else 0.0)
+    with pytest.raises(RuntimeError, match="batch schedule 5"):
+        A.tune_batch(256, "fp32", verbose=False)

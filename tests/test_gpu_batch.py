@@ -115,3 +115,30 @@ def test_one_failing_run_does_not_stop_the_others():
         sc = b.scalars(i)
         assert sc["status"] == 0 and sc["nsteps"] == 4
         assert np.all(np.isfinite(b.get_field(i)))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("n", [128, 256, 512])
+def test_every_batch_schedule_matches_the_oracle_per_step(precision, tol, n):
+    """Each tile schedule a batch class can be built with (the autotuner's
+    choices) takes the step of the oracle from an identical state."""
+    from paper_2012_15133_gb300 import Batch
+    from paper_2012_15133_gb300.autotune import batch_schedules
+    runs = [ensemble_run(i, sizes=(n,)) for i in range(2)]
+    states = []
+    for r in runs:
+        o = Oracle(2, r["n"], r["L"], r["eps"], r["beta"], r["dt"], dft="numpy").start(r["phi0"], "bdf1")
+        o.step(2)
+        states.append((o.phi.copy(), o.phi_prev.copy(), o.r, o.r_prev))
+        o.step(1)
+        states[-1] += (o.phi, o.r)
+    for sch in batch_schedules(n):
+        b = Batch(runs, 0.02, precision, schedule={n: sch})
+        assert b.schedule(n) == sch
+        for i, st in enumerate(states):
+            b.set_state(i, st[0], st[1], st[2], st[3])
+        b.step(1)
+        for i, st in enumerate(states):
+            assert rel_l2(b.get_field(i), st[4]) < tol, (sch, i)
+            assert abs(b.scalars(i)["r"] - st[5]) / st[5] < tol, (sch, i)
+        b.close()

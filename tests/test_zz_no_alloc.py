@@ -25,14 +25,15 @@ def _built():
 
 
 def _reference(phi, n, L, eps, beta):
-    """The allocating path on the same field: E_N, and with both levels the
-    field and r = 0 the modified energy 1/2 ||L^{1/2} phi||^2; the mass."""
+    """The allocating path on the same field: E_N; with both levels the field
+    and r^n = r^{n-1} = 1 the modified energy is 1/2 ||L^{1/2} phi||^2 + 1
+    (eq. discrete energy); the mass."""
     from paper_2012_15133_gb300 import Solver
     s = Solver(2, n, L, eps, beta, 0.01, "fp64")
-    s.set_state(phi, phi, 0.0, 0.0)
-    E_orig, E_half, _ = s.energy()
+    s.set_state(phi, phi, 1.0, 1.0)
+    E_orig, E_mod, _ = s.energy()
     mass, _ = s.mass()
-    return E_orig, E_half, mass
+    return E_orig, E_mod - 1.0, mass
 
 
 @pytest.mark.parametrize("n,L,eps,beta,seed", [(64, 32.0, 0.1, 1.0, 0), (256, 128.0, 0.25, 0.7, 3)])
