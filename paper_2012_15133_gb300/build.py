@@ -63,7 +63,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout, r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    # the solver instantiation units (the long compiles) first, on every core
+    srcs = sorted(srcs, key=lambda f: 0 if os.path.basename(f).startswith(("spfc_f", "spfc_batch_f")) else 1)
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

@@ -1,0 +1,8 @@
+// float64 solvers for 128 x 128 grids (all launch schedules).
+#include "spfc_solver2d.cuh"
+
+namespace spfc {
+SolverBase* make_solver_2d_f64_128(const Params& P, cudaStream_t st, int schedule, int* status, std::string* err) {
+  return make_solver_2d_n<double, 128>(P, st, schedule, status, err);
+}
+}  // namespace spfc

@@ -870,6 +870,8 @@ SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int
   }
 }
 
+SolverBase* make_solver_2d_f64_128(const Params&, cudaStream_t, int, int*, std::string*);
+SolverBase* make_solver_2d_f32_128(const Params&, cudaStream_t, int, int*, std::string*);
 SolverBase* make_solver_2d_f64_256(const Params&, cudaStream_t, int, int*, std::string*);
 SolverBase* make_solver_2d_f64_512(const Params&, cudaStream_t, int, int*, std::string*);
 SolverBase* make_solver_2d_f32_256(const Params&, cudaStream_t, int, int*, std::string*);
@@ -894,7 +896,7 @@ SolverBase* make_solver_2d(const Params& P, cudaStream_t st, int schedule, int* 
     case 32: return schedule ? new_solver_2d<R, 32, 1>(P, st, status, err) : new_solver_2d<R, 32, 0>(P, st, status, err);
     case 64: return schedule ? new_solver_2d<R, 64, 1>(P, st, status, err) : new_solver_2d<R, 64, 0>(P, st, status, err);
     case 128:
-      return make_solver_2d_n<R, 128>(P, st, schedule, status, err);
+      return F64 ? make_solver_2d_f64_128(P, st, schedule, status, err) : make_solver_2d_f32_128(P, st, schedule, status, err);
     case 256:
       return F64 ? make_solver_2d_f64_256(P, st, schedule, status, err) : make_solver_2d_f32_256(P, st, schedule, status, err);
     default:
