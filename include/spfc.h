@@ -80,9 +80,11 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
  * below), the persistent step: every step of a spfc_step call in one
  * cooperative launch (row pass, column forward pass, scalar solve, update
  * and the next column inverse pass behind bounded grid barriers). spfc_create
- * uses the grid's default, the autotuner's choice on GB300 (2D float32: 512
- * -> 0, 256 -> 2, 128 -> 5, 16..64 -> 1; 2D float64: 512 -> 6, 128 and 256
- * -> 5, otherwise 0), as does spfc_create_scheduled with schedule = -1; a schedule
+ * uses the grid's default, measured on GB300 (2D float32: 512 -> 6, 256 -> 2,
+ * 128 -> 5, 16..64 -> 1; 2D float64: 512 -> 6, 128 and 256 -> 5, otherwise
+ * 0: the autotuner's choices, except the persistent step at 512^2 float32,
+ * which ties on a flushed step and runs a spfc_step call in one launch), as
+ * does spfc_create_scheduled with schedule = -1; a schedule
  * in [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
  * autotuner times the choices. All schedules compute the same step; results
  * agree to rounding. spfc_schedule returns the handle's schedule. */
