@@ -61,8 +61,11 @@ typedef enum {
 
 typedef enum {
   SPFC_FP64 = 0,      /* all arithmetic in float64 */
-  SPFC_FP32_BULK = 1  /* FFTs and pointwise work in float32; E_1, inner products, r and the
-                         zero mode (mass) in float64 */
+  SPFC_FP32_BULK = 1  /* FFTs and pointwise work in float32; the sums of E_1 and of the inner
+                         products accumulated in float-float (two float32 words, about 2^-48
+                         relative) per thread and per block, then in float64 across blocks;
+                         E_1, S, gamma, eta, theta, the scalar solve, r and the zero mode
+                         (mass) in float64 */
 } spfc_precision;
 
 /* Create a solver for one run.
