@@ -214,7 +214,6 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
   __shared__ R alpha_s;
   __shared__ int flag_s, ok_s;
 
-  if (sc->status != DEV_OK) return;
   const int G = gridDim.x;
   const PC<R> pc(P);
   // column ownership (passes C and D)
@@ -225,6 +224,37 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
   const int rg = threadIdx.x / T, rlane = threadIdx.x % T;
   C* zrow = fft_s + rg * NSR * (SEQ + 1);
 
+  // Z = G_x + i G_y of the rows of round rr over the full x-spectrum
+  // (Hermitian mirror for k > N/2), from W_x, W_y
+  C v[NSR][E];
+  int row[NSR];
+  auto load_rows = [&](int rr) {
+#pragma unroll
+    for (int q = 0; q < NSR; ++q) {
+      row[q] = blockIdx.x * RPB + rr * RPR + rg * NSR + q;
+      const bool ok = row[q] < N;
+      const size_t roff = (size_t)(ok ? row[q] : 0) * NH;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int k = rlane + i * T;
+        const bool direct = k <= N / 2;
+        const size_t off = roff + (direct ? k : N - k);
+        C a = mk<C>(0, 0), b = mk<C>(0, 0);
+        if (ok) { a = __ldcg(W0 + off); b = __ldcg(W1 + off); }
+        v[q][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
+      }
+    }
+  };
+
+  // Entry: the twiddle copies and the first rows' loads need no field of the
+  // record, so they are in flight before the record is read.
+  for (int m = threadIdx.x; m < TW_N; m += blockDim.x) cp_async(tw_s + m, tw_g + m);
+  cp_async_commit();
+  load_rows(0);
+  if (sc->status != DEV_OK) {
+    cp_async_wait<0>();  // no copy may still be landing when the block leaves
+    return;
+  }
   int p = sc->p;
   unsigned long long bar = bar_base;     // arrival count of the last completed barrier round
   RIn rin(sc);                           // r^n, r^{n-1} (float64), carried by thread 0
@@ -234,9 +264,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
     zm_n = sc->zm[p];
     zm_o = sc->zm[1 - p];
   }
-  // twiddles, then this block's state columns, into shared memory
-  for (int m = threadIdx.x; m < TW_N; m += blockDim.x) cp_async(tw_s + m, tw_g + m);
-  cp_async_commit();
+  // this block's state columns into shared memory
   {
     const C* sn = S.at(p);
     const C* so = S.at(1 - p);
@@ -257,24 +285,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
     typename RD::acc acc2 = RD::zero(), acc1 = RD::zero();
 #pragma unroll 1
     for (int rr = 0; rr < NRR; ++rr) {
-      C v[NSR][E];
-      int row[NSR];
-#pragma unroll
-      for (int q = 0; q < NSR; ++q) {
-        row[q] = blockIdx.x * RPB + rr * RPR + rg * NSR + q;
-        const bool ok = row[q] < N;
-        const size_t roff = (size_t)(ok ? row[q] : 0) * NH;
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-          const int k = rlane + i * T;
-          const bool direct = k <= N / 2;
-          const size_t off = roff + (direct ? k : N - k);
-          C a = mk<C>(0, 0), b = mk<C>(0, 0);
-          if (ok) { a = __ldcg(W0 + off); b = __ldcg(W1 + off); }
-          // Z = G_x + i G_y over the full x-spectrum (Hermitian mirror for k > N/2)
-          v[q][i] = direct ? mk<C>(a.x - b.y, a.y + b.x) : mk<C>(a.x + b.y, b.x - a.y);
-        }
-      }
+      if (step > 0 || rr > 0) load_rows(rr);
       if (step == 0 && rr == 0) {
         cp_async_wait<1>();  // the twiddle group (the state may still be in flight)
         __syncthreads();
@@ -330,7 +341,10 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
       }
     }
     bar += G;
-    if (!grid_sync(sync64, bar, sc, &flag_s)) return;
+    if (!grid_sync(sync64, bar, sc, &flag_s)) {
+      cp_async_wait<0>();  // no copy may still be landing when the block leaves
+      return;
+    }
 
     // ---------------- C: forward column pass and partial sums ----------------
     C g[2][E];
