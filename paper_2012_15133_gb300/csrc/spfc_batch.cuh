@@ -156,7 +156,7 @@ class BatchClass final : public BatchClassBase {
   using C = C_t<R>;
   using SH = Shape2D<N_, SCHED>;
   static constexpr int NH = N_ / 2 + 1;
-  static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RPC = SH::RPC, CTP = (CT == 1) ? 1 : CT + 1;
+  static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RPC = SH::RPC, CTP = col_pitch(CT);
   static constexpr int GCOL = (NH + CT - 1) / CT, GROW = N_ / RPC;
 
  public:

@@ -101,6 +101,17 @@ struct TwShared {
 __device__ __forceinline__ constexpr int sp(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int sp_len(int n) { return n + n / 8; }
 
+// Pitch (in elements) between consecutive elements of one sequence when CT
+// sequences of a column tile are interleaved in shared memory (element j of
+// column c at c + sp(j) * pitch; thread lane * CT + c). Bank analysis of the
+// exchanges of fft_regs_multi with 8- and 16-byte elements (each group of
+// lanes covering 128 bytes is one shared-memory wavefront when its words fall
+// in distinct banks): the unpadded pitch CT reaches the minimum number of
+// wavefronts for every tile with CT >= 2 used here, whereas an odd pitch
+// CT + 1 needs up to twice as many (measured: 3.98 wavefronts per 8-byte
+// access against 1.99 ideal in the 128^3 y pass).
+__host__ __device__ constexpr int col_pitch(int ct) { return ct; }
+
 
 // A length-N FFT is done by T = N/E lanes, each owning E values per stage.
 // T <= 32: the lanes of a sequence sit in one warp (__syncwarp between

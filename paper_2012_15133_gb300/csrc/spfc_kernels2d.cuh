@@ -160,7 +160,7 @@ __device__ __forceinline__ void k2d_col_inv_body(const Params& P, Slots<R> S, co
                 "the phi^4 channel is carried by the step and gradient modes");
   static_assert(!(G3 && PF), "the PFC model has its own passes");
   constexpr int NTH = CT * T;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr bool COMMITTED = (MODE == CI_STEP_COMMITTED);
   constexpr int SEQ = sp_len(N);
@@ -649,7 +649,7 @@ __device__ __forceinline__ void k2d_col_fwd_body(const Params& P, Slots<R> S, co
   static_assert(!G3 || MODE == CF_BDF2 || MODE == CF_BDF1 || MODE == CF_NHAT || MODE == CF_PART,
                 "the phi^4 channel is carried by the modes that form N_hat");
   constexpr int NTH = CT * T;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr int SEQ = sp_len(N);
   static_assert(NTH % 32 == 0, "tile must fill whole warps");
@@ -845,7 +845,7 @@ k2d_col_fused(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __res
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NTH = CT * T;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;  // odd column pitch (bank spread)
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr int SEQ = sp_len(N);
   static_assert(NTH % 32 == 0, "tile must fill whole warps");

@@ -62,7 +62,7 @@ __device__ __forceinline__ void k3d_ypass_body(const Params& P, C_t<R>* __restri
   static_assert(!G3 || MODE == Y3_FWD || MODE == Y3_INV, "the phi^4 channel rides on the gradient passes");
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = y3_nf<MODE>::fft;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr int SEQ = sp_len(N);
   constexpr bool INV = (MODE == Y3_INV || MODE == Y3_INV_FIELD);
@@ -150,7 +150,7 @@ __device__ __forceinline__ void k3d_zfwd_body(const Params& P, Slots<R> S, const
   using RD = Red<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == Z3F_TO_STATE) ? 1 : 2;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr int SEQ = sp_len(N);
   constexpr size_t PS = (size_t)N * NH;
@@ -312,7 +312,7 @@ k3d_zinv(const Params P, Slots<R> S, const C_t<R>* __restrict__ Nhat, C_t<R>* __
   using C = C_t<R>;
   constexpr int T = fft_shape<N, E>::T;
   constexpr int NF = (MODE == Z3I_FIELD) ? 1 : 2;
-  constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  constexpr int CTP = col_pitch(CT);
   constexpr int NH = N / 2 + 1;
   constexpr int SEQ = sp_len(N);
   constexpr size_t PS = (size_t)N * NH;

@@ -96,7 +96,7 @@ int run(const Params& P, const double* phi, double* out, cudaStream_t st, unsign
   static_assert(sizeof(SavScal) + sizeof(unsigned long long) <= kScal, "scalar record and marker must fit");
   static_assert(GROW <= 1024 && 8 * (2 * 1024 + 3 * 1024 + 608) <= kPart, "partial sums must fit");
   Slots<double> S{{spec, spec}};
-  const size_t scol = (size_t)sp_len(N) * (CT + 1) * sizeof(C);
+  const size_t scol = (size_t)sp_len(N) * col_pitch(CT) * sizeof(C);
   const size_t srow = (size_t)RPC * (sp_len(N) + 1) * sizeof(C);
   cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(SavScal), st);  // p = 0, status OK
   if (e != cudaSuccess) { g_err = cudaGetErrorString(e); return SPFC_ECUDA; }

@@ -511,7 +511,7 @@ class Solver2D final : public SolverBase {
   template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
-  static constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  static constexpr int CTP = col_pitch(CT);
   static constexpr size_t smem_col(int nf) { return (size_t)nf * sp_len(N) * CTP * sizeof(C); }
   static constexpr size_t smem_row() { return (size_t)RPC * (sp_len(N) + 1) * sizeof(C); }
 

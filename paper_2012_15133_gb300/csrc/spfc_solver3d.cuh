@@ -24,7 +24,7 @@ class Solver3D final : public SolverBase {
   using SH = Shape3D<N, sizeof(R) == 8 ? 4 : 8>;
   static constexpr int NH = N / 2 + 1;
   static constexpr int E = SH::E, T = SH::T, CT = SH::CT, RP = SH::RP;
-  static constexpr int CTP = (CT == 1) ? 1 : CT + 1;
+  static constexpr int CTP = col_pitch(CT);
   static constexpr int GX = (NH + CT - 1) / CT;          // tiles per line set
   static constexpr int GROW = N * N / (2 * RP);           // row-pass blocks
   static constexpr int PW_THREADS = 256;

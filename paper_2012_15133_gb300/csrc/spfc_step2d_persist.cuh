@@ -52,7 +52,7 @@ template <typename R, int N> struct PShape {
   static constexpr int RPB = ((N + G - 1) / G + RPR - 1) / RPR * RPR;
   static constexpr int NRR = RPB / RPR;
   static constexpr int SEQ = sp_len(N);
-  static constexpr int CTP = CT + 1;  // odd column pitch of the column-pass scratch
+  static constexpr int CTP = col_pitch(CT);  // column pitch of the column-pass scratch
   // dynamic shared memory, in complex entries: twiddles, state staging
   // [2][N][CT], FFT scratch (the larger of the column and the row pass)
   static constexpr int SM_TW = TW_N;
