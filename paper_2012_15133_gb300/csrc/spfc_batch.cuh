@@ -186,7 +186,7 @@ class BatchClass final : public BatchClassBase {
     if (e == cudaSuccess) e = al((void**)&v_.partG, (size_t)nruns * 3 * GCOL * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&v_.sc, (size_t)nruns * sizeof(SavScal));
     if (e == cudaSuccess) e = al((void**)&Pdev_, (size_t)nruns * sizeof(Params));
-    if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
+    if (e == cudaSuccess) e = al((void**)&tw_, TW_LEN * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
       return e == cudaErrorMemoryAllocation ? 2 : 3;
@@ -194,7 +194,7 @@ class BatchClass final : public BatchClassBase {
     v_.P = Pdev_;
     std::vector<C> tw;
     host_twiddles<R>(tw);
-    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_LEN * sizeof(C), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemcpy(Pdev_, params_.data(), nruns * sizeof(Params), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(v_.sc, 0, nruns * sizeof(SavScal)));
     auto smc = (size_t)2 * sp_len(N_) * CTP * sizeof(C);

@@ -82,17 +82,63 @@ template <typename C, int RAD, bool INV> __device__ __forceinline__ void dft_r(C
   else dft2<C, INV>(v);
 }
 
-// Largest twiddle table length; table[m] = exp(-2 pi i m / TW_N).
+// Largest transform length.
 constexpr int TW_N = 512;
 
+// Staged twiddle table: one block per (span NS, radix RAD) of a Stockham
+// stage (NS RAD <= TW_N), in the order RAD = 2, 4, 8 and, within a radix, NS
+// ascending. Entry (r - 1) NS + k of block (NS, RAD) holds exp(-2 pi i r k /
+// (NS RAD)), r = 1 .. RAD-1, k < NS: the lanes of a warp, which differ in k,
+// read consecutive entries (a table indexed by r k TW_N / (NS RAD) puts them
+// 64 bytes or more apart, up to eight-way shared-memory bank conflicts).
+// tw_block(ns, rad) is the block's offset; with no such block, the table length.
+__host__ __device__ constexpr int tw_block(int ns, int rad) {
+  int off = 0;
+  for (int R = 2; R <= 8; R *= 2)
+    for (int st = 1; st * R <= TW_N; st *= 2) {
+      if (R == rad && st == ns) return off;
+      off += (R - 1) * st;
+    }
+  return off;
+}
+constexpr int TW_LEN = tw_block(0, 0);
+
+// Radix of the stage of a length-N transform that starts with span NS, E
+// values per lane (radix 8 while it divides the rest and E, then 4, then 2).
+__host__ __device__ constexpr int stage_radix(int N, int E, int ns) {
+  return ((N / ns) % 8 == 0 && E % 8 == 0) ? 8 : (((N / ns) % 4 == 0 && E % 4 == 0) ? 4 : 2);
+}
+// First and one-past-last table entry that the stages of a length-N
+// transform with E values per lane read (the first stage has no twiddles).
+__host__ __device__ constexpr int tw_lo(int N, int E) {
+  int lo = TW_LEN;
+  for (int ns = stage_radix(N, E, 1); ns < N; ns *= stage_radix(N, E, ns)) {
+    const int b = tw_block(ns, stage_radix(N, E, ns));
+    lo = b < lo ? b : lo;
+  }
+  return lo;
+}
+__host__ __device__ constexpr int tw_hi(int N, int E) {
+  int hi = 0;
+  for (int ns = stage_radix(N, E, 1); ns < N; ns *= stage_radix(N, E, ns)) {
+    const int rad = stage_radix(N, E, ns);
+    const int e = tw_block(ns, rad) + (rad - 1) * ns;
+    hi = e > hi ? e : hi;
+  }
+  return hi;
+}
+
 // Where the FFT stages read the twiddle table from: global memory through the
-// read-only path (TwGlobal, the default), or a copy in shared memory
-// (TwShared; a generic load, valid for a shared-memory pointer).
+// read-only path (TwGlobal, the default; the whole table), or a copy in
+// shared memory of entries [LO, ...) of it (TwSharedFrom<LO>; a generic load,
+// valid for a shared-memory pointer).
 struct TwGlobal {
   template <typename C> __device__ __forceinline__ static C ld(const C* p) { return __ldg(p); }
+  template <int NS, int RAD> __device__ __forceinline__ static constexpr int off() { return tw_block(NS, RAD); }
 };
-struct TwShared {
+template <int LO> struct TwSharedFrom {
   template <typename C> __device__ __forceinline__ static C ld(const C* p) { return *p; }
+  template <int NS, int RAD> __device__ __forceinline__ static constexpr int off() { return tw_block(NS, RAD) - LO; }
 };
 
 // Shared-memory position of element i of an FFT sequence: one pad slot every
@@ -164,14 +210,15 @@ __device__ __forceinline__ void stage_load(C* v, const C* s, int es, int lane) {
 
 template <typename C, int N, int E, bool INV, int NS, int RAD, class TWL = TwGlobal>
 __device__ __forceinline__ void stage_compute(C* v, int lane, const C* __restrict__ tw) {
-  constexpr int T = fft_shape<N, E>::T, NB = E / RAD, TWS = TW_N / (NS * RAD);
+  constexpr int T = fft_shape<N, E>::T, NB = E / RAD;
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
     const int k = (lane + m * T) & (NS - 1);
     if constexpr (NS > 1) {
+      constexpr int TB = TWL::template off<NS, RAD>();
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = TWL::template ld<C>(tw + r * k * TWS);
+        C w = TWL::template ld<C>(tw + TB + (r - 1) * NS + k);
         if (INV) w.y = -w.y;
         v[m * RAD + r] = cmul(v[m * RAD + r], w);
       }

@@ -26,7 +26,7 @@ namespace {
 constexpr int NOALLOC_MAX_N = 256;
 constexpr size_t kSpec = (size_t)NOALLOC_MAX_N * (NOALLOC_MAX_N / 2 + 1) * sizeof(double2);
 constexpr size_t kPart = 64 * 1024;
-constexpr size_t kTw = TW_N * sizeof(double2);
+constexpr size_t kTw = TW_LEN * sizeof(double2);
 constexpr size_t kScal = 1024;
 constexpr size_t kBytes = 3 * kSpec + kPart + kTw + kScal;
 

@@ -75,14 +75,22 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// The staged twiddle table (tw_block): entry (r - 1) NS + k of block (NS, RAD)
+// is exp(-2 pi i m / TW_N) with m = r k TW_N / (NS RAD), from libm in double
+// precision.
 template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
-  tw.resize(TW_N);
-  for (int m = 0; m < TW_N; ++m) {
-    // exp(-2 pi i m / TW_N) from libm in double precision
-    const double ang = 2.0 * M_PI * (double)m / (double)TW_N;
-    tw[m].x = (R)std::cos(ang);
-    tw[m].y = (R)(-std::sin(ang));
-  }
+  tw.assign(TW_LEN, C_t<R>{});
+  for (int rad = 2; rad <= 8; rad *= 2)
+    for (int ns = 1; ns * rad <= TW_N; ns *= 2) {
+      const int b = tw_block(ns, rad);
+      for (int r = 1; r < rad; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const int m = r * k * (TW_N / (ns * rad));
+          const double ang = 2.0 * M_PI * (double)m / (double)TW_N;
+          tw[b + (r - 1) * ns + k].x = (R)std::cos(ang);
+          tw[b + (r - 1) * ns + k].y = (R)(-std::sin(ang));
+        }
+    }
 }
 
 // The schedule whose steps run as one persistent cooperative kernel
@@ -141,14 +149,14 @@ class Solver2D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&sync64_, sizeof(unsigned long long));
     if (e == cudaSuccess && PERSIST) e = al((void**)&sync64p_, sizeof(unsigned long long));
     if (e == cudaSuccess && PERSIST) e = al((void**)&partP_, 5 * (size_t)PS::G * sizeof(double));
-    if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
+    if (e == cudaSuccess) e = al((void**)&tw_, TW_LEN * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
       return (e == cudaErrorMemoryAllocation) ? 2 : 3;
     }
     std::vector<C> tw;
     host_twiddles<R>(tw);
-    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_LEN * sizeof(C), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(counter_, 0, 4 * sizeof(unsigned)));
     SPFC_CK(cudaMemset(sync64_, 0, sizeof(unsigned long long)));
     if (PERSIST) SPFC_CK(cudaMemset(sync64p_, 0, sizeof(unsigned long long)));

@@ -56,14 +56,14 @@ class Solver3D final : public SolverBase {
     if (e == cudaSuccess) e = al((void**)&partS_, (size_t)gpw_ * sizeof(double));
     if (e == cudaSuccess) e = al((void**)&sc_, sizeof(SavScal));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc_, sizeof(SavScal));  // pinned: small fast reads
-    if (e == cudaSuccess) e = al((void**)&tw_, TW_N * sizeof(C));
+    if (e == cudaSuccess) e = al((void**)&tw_, TW_LEN * sizeof(C));
     if (e != cudaSuccess) {
       err = std::string("device allocation failed: ") + cudaGetErrorString(e);
       return (e == cudaErrorMemoryAllocation) ? 2 : 3;
     }
     std::vector<C> tw;
     host_twiddles<R>(tw);
-    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_N * sizeof(C), cudaMemcpyHostToDevice));
+    SPFC_CK(cudaMemcpy(tw_, tw.data(), TW_LEN * sizeof(C), cudaMemcpyHostToDevice));
     SavScal z{};
     SPFC_CK(cudaMemcpy(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice));
     SPFC_CK(cudaMemset(counter_, 0, sizeof(unsigned)));

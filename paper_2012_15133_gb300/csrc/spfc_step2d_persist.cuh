@@ -55,7 +55,9 @@ template <typename R, int N> struct PShape {
   static constexpr int CTP = col_pitch(CT);  // column pitch of the column-pass scratch
   // dynamic shared memory, in complex entries: twiddles, state staging
   // [2][N][CT], FFT scratch (the larger of the column and the row pass)
-  static constexpr int SM_TW = TW_N;
+  // the twiddle entries its transforms read (rows and columns: one length)
+  static constexpr int TW_LO = tw_lo(N, E), TW_HI = tw_hi(N, E);
+  static constexpr int SM_TW = TW_HI - TW_LO;
   static constexpr int SM_ST = 2 * N * CT;
   static constexpr int SM_COL = 2 * SEQ * CTP;
   static constexpr int SM_ROW = CT * NSR * (SEQ + 1);
@@ -248,7 +250,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
 
   // Entry: the twiddle copies and the first rows' loads need no field of the
   // record, so they are in flight before the record is read.
-  for (int m = threadIdx.x; m < TW_N; m += blockDim.x) cp_async(tw_s + m, tw_g + m);
+  for (int m = threadIdx.x; m < SH::SM_TW; m += blockDim.x) cp_async(tw_s + m, tw_g + SH::TW_LO + m);
   cp_async_commit();
   load_rows(0);
   if (sc->status != DEV_OK) {
@@ -290,7 +292,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
         cp_async_wait<1>();  // the twiddle group (the state may still be in flight)
         __syncthreads();
       }
-      fft_regs_multi<C, N, E, true, NSR, false, TwShared>(v, zrow, SEQ + 1, 1, rlane, tw_s);
+      fft_regs_multi<C, N, E, true, NSR, false, TwSharedFrom<SH::TW_LO>>(v, zrow, SEQ + 1, 1, rlane, tw_s);
       const R beta = pc.beta;
 #pragma unroll
       for (int q = 0; q < NSR; ++q) {
@@ -307,7 +309,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
           v[q][i] = mk<C>(fac * g.x, fac * g.y);
         }
       }
-      fft_regs_multi<C, N, E, false, NSR, false, TwShared>(v, zrow, SEQ + 1, 1, rlane, tw_s);
+      fft_regs_multi<C, N, E, false, NSR, false, TwSharedFrom<SH::TW_LO>>(v, zrow, SEQ + 1, 1, rlane, tw_s);
       // the split into W_x, W_y pairs k with N - k: one exchange
       fft_sync<N, E>();
 #pragma unroll
@@ -359,7 +361,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
     }
     double pe[2][2];  // the E_1 partial sums of all blocks: loaded now, summed after the transform
     load_partials<2>(partE, G, pe);
-    fft_regs_multi<C, N, E, false, 2, true, TwShared>(g, fft_s + c, SEQ * CTP, CTP, clane, tw_s);
+    fft_regs_multi<C, N, E, false, 2, true, TwSharedFrom<SH::TW_LO>>(g, fft_s + c, SEQ * CTP, CTP, clane, tw_s);
     if (step == 0) cp_async_wait<0>();  // this thread's state copies have landed
     C nh[E];
     R ia[E];
@@ -454,7 +456,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
       g[0][i] = g0;
       g[1][i] = g1;
     }
-    fft_regs_multi<C, N, E, true, 2, true, TwShared>(g, fft_s + c, SEQ * CTP, CTP, clane, tw_s);
+    fft_regs_multi<C, N, E, true, 2, true, TwSharedFrom<SH::TW_LO>>(g, fft_s + c, SEQ * CTP, CTP, clane, tw_s);
     if (col) {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
