@@ -506,13 +506,9 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
 
 
 # DRAM bytes per launch (read + write) of the 512^2 FP32 persistent step from
-# the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,321,024
+# the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,325,376
 # read, 0 written); None whenever the kernel changes after the capture
-TRAFFIC_STEP_512_FP32 = 4321024
-# the same for the two-kernel step (schedule 0) from the capture in
-# profiles/step2d_512_kernels_ncu_full.md (BDF2 instance of the fused column pass)
-TRAFFIC_COL_FUSED_512_FP32 = 4285184
-TRAFFIC_ROW_512_FP32 = 2132224
+TRAFFIC_STEP_512_FP32 = 4325376
 
 
 def measure_precision_split(steps=1000, n=N_GRID):
@@ -550,7 +546,8 @@ def _summary(line):
         return None if x is None else float(f"{x:.4g}")
     out = {"value": r4(line["value"]), "ms_per_step": r4(line["ms_per_step"]),
            "frac": r4(line["roofline"]["frac"]), "e2e": r4(line["e2e"]["value"]),
-           "l2_resident": r4(line.get("l2_resident_value"))}
+           "l2_resident": r4(line.get("l2_resident_value")),
+           "unflushed_us": r4((line.get("unflushed_step_us") or {}).get("median"))}
     for k, v in line.items():
         if k == "config" or not isinstance(v, dict) or "workload" not in v:
             continue
@@ -652,8 +649,7 @@ def run_ours(args):
     # DRAM bytes (read + write) per launch from the committed ncu capture of the
     # 512^2 FP32 persistent step (profiles/step2d_512_fp32_persist_ncu.md);
     # None whenever the kernel changed after the capture
-    traffic_ncu = {("fp32", "step"): TRAFFIC_STEP_512_FP32, ("fp32", "col_fused"): TRAFFIC_COL_FUSED_512_FP32,
-                   ("fp32", "row"): TRAFFIC_ROW_512_FP32}
+    traffic_ncu = {("fp32", "step"): TRAFFIC_STEP_512_FP32}
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": passes[dom] * SB, "avg_launch_us": avg_s * 1e6,
@@ -673,6 +669,17 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     resident = P * nres / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    # --- the same single-step calls as the timed region, back to back with no
+    # flush between them (what the flush costs a step)
+    evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        evb[i][0].record(stream)
+        s.step(1)
+        evb[i][1].record(stream)
+    torch.cuda.synchronize()
+    unflushed = sorted(a.elapsed_time(b) * 1e3 for a, b in evb)
+    unflushed_us = unflushed[len(unflushed) // 2]
 
     # --- end to end through the public API with host buffers: the field from
     # pinned host memory (init), K steps whose scalar records the device writes
@@ -750,6 +757,8 @@ def run_ours(args):
                                 "over the run plus the 64-byte record"},
                 "gpu_launches": sum(v[0] for v in kt.values()),
                 "l2_resident_value": resident,
+                "unflushed_step_us": {"median": unflushed_us, "note": "spfc_step(1) calls back to back, no flush "
+                                      "between them (the timed region flushes the L2 before each)"},
                 "clocks": clk.summary(),
                 **extras}
         line["summary"] = _summary(line)
