@@ -146,6 +146,15 @@ template <int LO> struct TwSharedFrom {
 // banks. A sequence of length N occupies sp_len(N) slots.
 __device__ __forceinline__ constexpr int sp(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int sp_len(int n) { return n + n / 8; }
+// Position in a contiguous sequence (element stride 1: rows, one-column
+// tiles): one pad slot every 16 elements. The strided writes of a radix-8
+// stage stay spread, and 16 lanes reading consecutive elements (one 128-byte
+// wavefront of 8-byte elements) no longer wrap onto the same banks as they do
+// with a pad every 8 (bank model: 2.5 against 3 wavefronts per access of the
+// row exchanges). Fits in sp_len(N) slots.
+__device__ __forceinline__ constexpr int spr(int i) { return i + (i >> 4); }
+// Slot of element i of a sequence with element stride es.
+__device__ __forceinline__ int sps(int i, int es) { return es == 1 ? spr(i) : sp(i) * es; }
 
 // Pitch (in elements) between consecutive elements of one sequence when CT
 // sequences of a column tile are interleaved in shared memory (element j of
@@ -205,7 +214,7 @@ __device__ __forceinline__ void stage_load(C* v, const C* s, int es, int lane) {
 #pragma unroll
   for (int m = 0; m < NB; ++m)
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sp(lane + m * T + r * STRIDE) * es];
+    for (int r = 0; r < RAD; ++r) v[m * RAD + r] = s[sps(lane + m * T + r * STRIDE, es)];
 }
 
 template <typename C, int N, int E, bool INV, int NS, int RAD, class TWL = TwGlobal>
@@ -235,7 +244,7 @@ __device__ __forceinline__ void stage_store(const C* v, C* s, int es, int lane) 
     const int j = lane + m * T, k = j & (NS - 1);
     const int base = (j - k) * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) s[sp(base + r * NS) * es] = v[m * RAD + r];
+    for (int r = 0; r < RAD; ++r) s[sps(base + r * NS, es)] = v[m * RAD + r];
   }
 }
 
@@ -356,7 +365,7 @@ __device__ __forceinline__ void fft_regs_multi(C (*v)[E], C* s, int qs, int es, 
 }
 
 // Unnormalised complex DFT of the length-N sequence whose element i is at
-// s[sp(i) * es] in shared memory, in place, by the T = N/E lanes (lane = 0..T-1) of one
+// s[sps(i, es)] in shared memory, in place, by the T = N/E lanes (lane = 0..T-1) of one
 // sequence. Forward: exp(-2 pi i k j / N); INV: exp(+2 pi i k j / N).
 // The caller has made the input visible (block or warp barrier as fft_sync);
 // on return the output is visible to the sequence's lanes.

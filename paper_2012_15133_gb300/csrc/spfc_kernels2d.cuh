@@ -326,13 +326,13 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = real_io[(size_t)row * N + lane + i * T];
 #pragma unroll
-    for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = mk<C>((R)v[i], (R)0);
+    for (int i = 0; i < E; ++i) z[spr(lane + i * T)] = mk<C>((R)v[i], (R)0);
     __syncthreads();
     fft_smem<C, N, E, false>(z, 1, lane, tw);
     const R sc1 = PC<R>(P).invP;
 #pragma unroll
-    for (int i = 0; i < KH; ++i) W0[roff + lane + i * T] = cscale(z[sp(lane + i * T)], sc1);
-    if (lane == 0) W0[roff + N / 2] = cscale(z[sp(N / 2)], sc1);
+    for (int i = 0; i < KH; ++i) W0[roff + lane + i * T] = cscale(z[spr(lane + i * T)], sc1);
+    if (lane == 0) W0[roff + N / 2] = cscale(z[spr(N / 2)], sc1);
   } else if constexpr (MODE == RW_OUT_REAL) {
     C a[KH];
 #pragma unroll
@@ -341,14 +341,14 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < KH; ++i) {
       const int k = lane + i * T;
-      z[sp(k)] = a[i];
-      if (k > 0) z[sp(N - k)] = cconj(a[i]);
+      z[spr(k)] = a[i];
+      if (k > 0) z[spr(N - k)] = cconj(a[i]);
     }
-    if (lane == 0) z[sp(N / 2)] = ny;
+    if (lane == 0) z[spr(N / 2)] = ny;
     __syncthreads();
     fft_smem<C, N, E, true>(z, 1, lane, tw);
 #pragma unroll
-    for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[sp(lane + i * T)].x;
+    for (int i = 0; i < E; ++i) real_io[(size_t)row * N + lane + i * T] = (double)z[spr(lane + i * T)].x;
   } else if constexpr (PF) {
     // the PFC model: the row's x-spectrum of phi* (Hermitian extension loaded
     // straight into registers), inverse DFT to phi*(x), the E_1 sums
@@ -425,14 +425,14 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
       fft_regs_multi<C, N, E, false, 2, false>(v, z, SEQ + 1, 1, lane, tw);
       fft_sync<N, E>();
 #pragma unroll
-      for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = v[0][i];
+      for (int i = 0; i < E; ++i) z[spr(lane + i * T)] = v[0][i];
       fft_sync<N, E>();
       const R half = (R)0.5 * pc.invP;
 #pragma unroll
       for (int i = 0; i < KH + 1; ++i) {
         if (i == KH && lane != 0) break;
         const int kk = lane + i * T;
-        const C zk = v[0][i], zm = cconj(z[sp((N - kk) & (N - 1))]);
+        const C zk = v[0][i], zm = cconj(z[spr((N - kk) & (N - 1))]);
         const C sx = cadd(zk, zm), dy = csub(zk, zm);
         const C f3 = cscale(v[1][i], pc.invP);  // x-spectrum of gamma3 phi*^3, k <= N/2
         const R ktk = kderiv<R>(kk, N, pc.kfx);
@@ -481,14 +481,14 @@ __device__ __forceinline__ void k2d_row_body(const Params& P, C_t<R>* __restrict
       // the split into W_x, W_y pairs k with N - k: one exchange
       fft_sync<N, E>();
 #pragma unroll
-      for (int i = 0; i < E; ++i) z[sp(lane + i * T)] = v[i];
+      for (int i = 0; i < E; ++i) z[spr(lane + i * T)] = v[i];
       fft_sync<N, E>();
       const R half = (R)0.5 * pc.invP;
 #pragma unroll
       for (int i = 0; i < KH + 1; ++i) {
         if (i == KH && lane != 0) break;
         const int kk = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
-        const C zk = v[i], zm = cconj(z[sp((N - kk) & (N - 1))]);
+        const C zk = v[i], zm = cconj(z[spr((N - kk) & (N - 1))]);
         const C sx = cadd(zk, zm), dy = csub(zk, zm);
         W0[roff + kk] = cscale(sx, half);                      // W_x = (Z_k + conj Z_{N-k}) / 2
         W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);      // W_y = (Z_k - conj Z_{N-k}) / (2i)

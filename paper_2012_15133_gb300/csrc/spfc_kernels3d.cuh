@@ -427,7 +427,7 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = lane + i * T;
-      z[sp(x)] = mk<C>((R)real_io[row0 * N + x], (R)real_io[(row0 + 1) * N + x]);
+      z[spr(x)] = mk<C>((R)real_io[row0 * N + x], (R)real_io[(row0 + 1) * N + x]);
     }
     __syncthreads();
     fft_smem<C, N, E, false>(z, 1, lane, tw);
@@ -436,7 +436,7 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
     for (int i = 0; i < KH + 1; ++i) {
       if (i == KH && lane != 0) break;
       const int k = (i == KH) ? N / 2 : lane + i * T;
-      const C zk = z[sp(k)], zm = cconj(z[sp((N - k) & (N - 1))]);
+      const C zk = z[spr(k)], zm = cconj(z[spr((N - k) & (N - 1))]);
       const C a = cadd(zk, zm), b = csub(zk, zm);
       W0[row0 * NH + k] = cscale(a, h);
       W0[(row0 + 1) * NH + k] = mk<C>(b.y * h, -b.x * h);
@@ -452,17 +452,17 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
     for (int i = 0; i < KH; ++i) {
       const int k = lane + i * T;
-      z[sp(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
-      if (k > 0) z[sp(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
+      z[spr(k)] = mk<C>(a[i].x - b[i].y, a[i].y + b[i].x);
+      if (k > 0) z[spr(N - k)] = mk<C>(a[i].x + b[i].y, b[i].x - a[i].y);
     }
-    if (lane == 0) z[sp(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
+    if (lane == 0) z[spr(N / 2)] = mk<C>(an.x - bn.y, an.y + bn.x);
     __syncthreads();
     fft_smem<C, N, E, true>(z, 1, lane, tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = lane + i * T;
-      real_io[row0 * N + x] = (double)z[sp(x)].x;
-      real_io[(row0 + 1) * N + x] = (double)z[sp(x)].y;
+      real_io[row0 * N + x] = (double)z[spr(x)].x;
+      real_io[(row0 + 1) * N + x] = (double)z[spr(x)].y;
     }
   } else {
     // Z_q = A_q + i B_q over the full x-spectrum, element k = lane + i T
@@ -530,7 +530,7 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
 #pragma unroll
       for (int q = 0; q < NS; ++q)
 #pragma unroll
-        for (int i = 0; i < E; ++i) z[q * (SEQ + 1) + sp(lane + i * T)] = v[q][i];
+        for (int i = 0; i < E; ++i) z[q * (SEQ + 1) + spr(lane + i * T)] = v[q][i];
       fft_sync<N, E>();
       const R h = (R)0.5 * pc.invP;
       if constexpr (G3) {
@@ -539,7 +539,7 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
         for (int i = 0; i < KH + 1; ++i) {
           if (i == KH && lane != 0) break;
           const int k = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
-          const int km = sp((N - k) & (N - 1));
+          const int km = spr((N - k) & (N - 1));
           C sx[NS], dy[NS];
 #pragma unroll
           for (int q = 0; q < NS; ++q) {
@@ -567,7 +567,7 @@ __device__ __forceinline__ void k3d_row_body(const Params& P, C_t<R>* __restrict
           for (int i = 0; i < KH + 1; ++i) {
             if (i == KH && lane != 0) break;
             const int k = lane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
-            const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + sp((N - k) & (N - 1))]);
+            const C zk = v[q][i], zm = cconj(z[q * (SEQ + 1) + spr((N - k) & (N - 1))]);
             const C sx = cadd(zk, zm), dy = csub(zk, zm);
             Oa[ra * NH + k] = cscale(sx, h);
             Ob[rb * NH + k] = mk<C>(dy.y * h, -dy.x * h);

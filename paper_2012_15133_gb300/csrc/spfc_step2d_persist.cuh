@@ -315,7 +315,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
 #pragma unroll
       for (int q = 0; q < NSR; ++q)
 #pragma unroll
-        for (int i = 0; i < E; ++i) zrow[q * (SEQ + 1) + sp(rlane + i * T)] = v[q][i];
+        for (int i = 0; i < E; ++i) zrow[q * (SEQ + 1) + spr(rlane + i * T)] = v[q][i];
       fft_sync<N, E>();
       const R half = (R)0.5 * pc.invP;
 #pragma unroll
@@ -326,7 +326,7 @@ k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __
         for (int i = 0; i < KH + 1; ++i) {
           if (i == KH && rlane != 0) break;
           const int kk = rlane + i * T;  // i == KH: the Nyquist entry N/2 (lane 0)
-          const C zk = v[q][i], zm = cconj(zrow[q * (SEQ + 1) + sp((N - kk) & (N - 1))]);
+          const C zk = v[q][i], zm = cconj(zrow[q * (SEQ + 1) + spr((N - kk) & (N - 1))]);
           const C sx = cadd(zk, zm), dy = csub(zk, zm);
           W0[roff + kk] = cscale(sx, half);                  // W_x = (Z_k + conj Z_{N-k}) / 2
           W1[roff + kk] = mk<C>(dy.y * half, -dy.x * half);  // W_y = (Z_k - conj Z_{N-k}) / (2i)
