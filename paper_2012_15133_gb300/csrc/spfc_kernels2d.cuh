@@ -101,10 +101,15 @@ __device__ __forceinline__ R sym_L(R K2, const PC<R>& c) {
 // 1 / (c0 + dt |k|^2 L(k) + A dt |k|^2): inverse symbol of A_N (c0 = 3/2,
 // eq. solver-1) or of the first-order operator (c0 = 1); the last term is the
 // stabiliser of Sec. 5.2 (exactly zero when A = 0).
+// The correctly rounded reciprocal (the value of an IEEE 1 / x, by the
+// shorter reciprocal intrinsic rather than the general division).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <typename R>
 __device__ __forceinline__ R sym_invA(R K2, R c0, const PC<R>& c) {
   const R A = rn_fma(c.sdt, K2, rn_fma(c.dt, rn_mul(K2, sym_L<R>(K2, c)), c0));
-  return (R)1 / A;
+  return rcp_rn(A);
 }
 
 // Zero mode of the BDF2 update: A_0 = 3/2 and Delta_N N has no mean, so
