@@ -78,24 +78,25 @@ struct spfc_batch_s {
     return code;
   }
 
-  // one step of every class, the classes as parallel branches of the graph
+  // nsteps steps of every class: each class a chain of its own steps, the
+  // classes as parallel branches of the graph joined once at its end (their
+  // runs share nothing, so a class never waits for another between steps)
   int capture(int nsteps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(SPFC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
     int rc = 0;
     const size_t nc = classes.size();
-    for (int s = 0; s < nsteps && !rc; ++s) {
-      cudaEvent_t fork = evs[2 * nc * s];
-      cudaEventRecord(fork, cap);
+    cudaEventRecord(evs[0], cap);
+    for (size_t c = 0; c < nc; ++c) cudaStreamWaitEvent(side[c], evs[0], 0);
+    for (int s = 0; s < nsteps && !rc; ++s)
       for (size_t c = 0; c < nc && !rc; ++c) {
-        cudaStreamWaitEvent(side[c], fork, 0);
         rc = classes[c]->launch_step(side[c]);
         if (rc) err = classes[c]->err;
-        cudaEvent_t join = evs[2 * nc * s + 1 + c];
-        cudaEventRecord(join, side[c]);
-        cudaStreamWaitEvent(cap, join, 0);
       }
+    for (size_t c = 0; c < nc; ++c) {  // joined also after a failed launch, so that the capture ends
+      cudaEventRecord(evs[1 + c], side[c]);
+      cudaStreamWaitEvent(cap, evs[1 + c], 0);
     }
     e = cudaStreamEndCapture(cap, &g);
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -190,7 +191,7 @@ int spfc_batch_create_scheduled(int nruns, const int* n, const double* L, const 
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) b->side.push_back(s);
   }
-  const size_t nev = 8 * (1 + b->classes.size()) * 2;
+  const size_t nev = 1 + b->classes.size();  // the graph's fork and one join per class
   for (size_t i = 0; i < nev && e == cudaSuccess; ++i) {
     cudaEvent_t ev;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
