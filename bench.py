@@ -506,9 +506,9 @@ def measure_surrogate(modes=16, train_runs=64, snapshots=8, iters=300, eval_runs
 
 
 # DRAM bytes per launch (read + write) of the 512^2 FP32 persistent step from
-# the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,325,376
+# the committed ncu capture (profiles/step2d_512_fp32_persist_ncu.md: 4,326,144
 # read, 0 written); None whenever the kernel changes after the capture
-TRAFFIC_STEP_512_FP32 = 4325376
+TRAFFIC_STEP_512_FP32 = 4326144
 
 
 def measure_precision_split(steps=1000, n=N_GRID):
@@ -816,7 +816,7 @@ def run_driver(args):
         return 0
     from seeded_inputs import crystal_2d_case
     c = crystal_2d_case(args.n)
-    s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision)
+    s = Solver(2, c["n"], c["L"], c["eps"], c["beta"], c["dt"], args.precision, schedule=args.schedule)
     if args.workload == "gamma3":
         s.set_gamma3(1.0)
     s.init(c["phi0"], "bdf1")
@@ -845,6 +845,8 @@ def main():
     ap.add_argument("--ncu-driver", action="store_true",
                     help="only run init + STEPS steps with per-kernel launches (for ncu captures)")
     ap.add_argument("--n", type=int, default=N_GRID, help="grid size for --ncu-driver")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="launch schedule of the 2D run of --ncu-driver (default: the library's)")
     ap.add_argument("--workload", default="crystal", choices=["crystal", "gamma3", "cube", "cube_gamma3", "ensemble", "surrogate"],
                     help="workload of --ncu-driver")
     args = ap.parse_args()
