@@ -547,6 +547,7 @@ def _summary(line):
     out = {"value": r4(line["value"]), "ms_per_step": r4(line["ms_per_step"]),
            "frac": r4(line["roofline"]["frac"]), "e2e": r4(line["e2e"]["value"]),
            "l2_resident": r4(line.get("l2_resident_value")),
+           "l2_frac": r4((line.get("l2_resident_roofline") or {}).get("frac")),
            "unflushed_us": r4((line.get("unflushed_step_us") or {}).get("median"))}
     for k, v in line.items():
         if k == "config" or not isinstance(v, dict) or "workload" not in v:
@@ -669,6 +670,28 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     resident = P * nres / (e0.elapsed_time(e1) * 1e-3) / 1e6
+    resident_s = e0.elapsed_time(e1) * 1e-3 / nres
+
+    # --- L2 roofline of the resident run: the step's algorithmic bytes per step
+    # at the resident rate, against a copy measured on this GPU between two
+    # 24 MB buffers that stay in L2 (read + write bytes per second)
+    l2n = 24 * 1024 * 1024 // 4
+    l2a = torch.ones(l2n, dtype=torch.float32, device="cuda")
+    l2b = torch.empty_like(l2a)
+    for _ in range(10):
+        l2b.copy_(l2a)
+    e0.record(stream)
+    for _ in range(200):
+        l2b.copy_(l2a)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l2_peak = 2 * l2n * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del l2a, l2b
+    csz = 8 if args.precision == "fp32" else 16
+    l2_ach = 15 * N_GRID * (N_GRID // 2 + 1) * csz / resident_s / 1e9
+    l2_roof = {"bound": "l2", "achieved": l2_ach, "peak": l2_peak, "unit": "GB/s", "frac": l2_ach / l2_peak,
+               "peak_source": "measured here: device copy between two 24 MB buffers resident in L2",
+               "note": "15 half-spectrum passes per step at the L2-resident rate (one launch of 2048 steps)"}
 
     # --- the same single-step calls as the timed region, back to back with no
     # flush between them (what the flush costs a step)
@@ -757,6 +780,7 @@ def run_ours(args):
                                 "over the run plus the 64-byte record"},
                 "gpu_launches": sum(v[0] for v in kt.values()),
                 "l2_resident_value": resident,
+                "l2_resident_roofline": l2_roof,
                 "unflushed_step_us": {"median": unflushed_us, "note": "spfc_step(1) calls back to back, no flush "
                                       "between them (the timed region flushes the L2 before each)"},
                 "clocks": clk.summary(),
