@@ -242,7 +242,7 @@ def measure_cube(steps, warmup, precision, peak, flush, gamma3=0.0):
     it; then the same steps with the kernels launched one by one and CUDA
     events around each, for the HBM fraction of every kernel at the passes it
     moves (row 3 + 3, y-forward 3 + 2, z-forward 4 + 1, z-inverse 3 + 3,
-    y-inverse 2 + 3; the one-block scalar solve moves none). gamma3 > 0 adds
+    y-inverse 2 + 3; the scalar solve moves none). gamma3 > 0 adds
     the phi^4 term with the same passes."""
     import torch
     from paper_2012_15133_gb300 import Solver
