@@ -79,18 +79,18 @@ int spfc_create(int d, const int* n, const double* L, double eps, double beta, d
 
 /* Kernel launch schedules compiled for a grid: the tile shapes of the
  * two-kernel step (row pass, then the column pass with its grid barrier;
- * six for N >= 128, one below) and, as the last schedule (6 for N >= 128, 1
- * below), the persistent step: every step of a spfc_step call in one
- * cooperative launch (row pass, column forward pass, scalar solve, update
- * and the next column inverse pass behind bounded grid barriers). spfc_create
- * uses the grid's default, measured on GB300 (2D float32: 512 -> 6, 256 -> 2,
- * 128 -> 5, 16..64 -> 1; 2D float64: 512 -> 6, 128 and 256 -> 5, otherwise
- * 0: the autotuner's choices, except the persistent step at 512^2 float32,
- * which ties on a flushed step and runs a spfc_step call in one launch), as
- * does spfc_create_scheduled with schedule = -1; a schedule
- * in [0, spfc_num_schedules(d, n)) picks one explicitly, which is how the
- * autotuner times the choices. All schedules compute the same step; results
- * agree to rounding. spfc_schedule returns the handle's schedule. */
+ * six for N >= 128, one below) and the persistent step: every step of a
+ * spfc_step call in one cooperative launch (row pass, column forward pass,
+ * scalar solve, update and the next column inverse pass behind bounded grid
+ * barriers), as schedule 6 for N >= 128 (8 values per FFT lane), 7 for
+ * N >= 128 (4 values per lane, twice the threads) and 1 below. spfc_create
+ * uses the grid's default, the autotuner's choice measured on GB300 (2D
+ * float32: 512 -> 6, 256 and 128 -> 7, 16..64 -> 1; 2D float64: 512 -> 6,
+ * 128 and 256 -> 5, otherwise 0), as does spfc_create_scheduled with
+ * schedule = -1; a schedule in [0, spfc_num_schedules(d, n)) picks one
+ * explicitly, which is how the autotuner times the choices. All schedules
+ * compute the same step; results agree to rounding. spfc_schedule returns
+ * the handle's schedule. */
 int spfc_num_schedules(int d, int n);
 int spfc_create_scheduled(int d, const int* n, const double* L, double eps, double beta, double dt,
                           int precision, void* cuda_stream, int schedule, spfc_t* out);

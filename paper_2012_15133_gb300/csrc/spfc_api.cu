@@ -36,19 +36,15 @@ static int fail(spfc_t h, int code, const std::string& msg) {
 }
 
 // Default launch schedule per grid: the autotuner's choice on GB300 (the
-// smallest sum of flushed and L2-resident step time; autotune_cache.json),
-// except at 512^2 float32 bulk, where the persistent step (6) is the default:
-// its flushed step matches schedule 0's (25.3 against 25.5 us in the tuner,
-// 25.5 against 26.7 us in the bench runs) and it runs a whole spfc_step call
-// in one launch, which the end-to-end flow measures at 9.3k against 7.0k
-// Mpoint-steps/s. float32 bulk: 2 at 256, 5 at 128, the persistent step (1)
-// below; float64: the persistent step (6) at 512, 5 at 128 and 256, 0 below.
+// smallest sum of flushed and L2-resident step time; autotune_cache.json).
+// float32 bulk: the persistent step (6) at 512, its 4-values-per-lane form
+// (7) at 256 and 128, the persistent step (1) below; float64: the persistent
+// step (6) at 512, 5 at 128 and 256, 0 below.
 static int default_schedule(int d, int n, int precision) {
   if (d != 2) return 0;
   if (precision == SPFC_FP64) return n == 512 ? 6 : ((n == 128 || n == 256) ? 5 : 0);
   if (n == 512) return 6;
-  if (n == 256) return 2;
-  return n == 128 ? 5 : 1;
+  return (n == 128 || n == 256) ? 7 : 1;
 }
 
 static int wrap(spfc_t h, int rc) {

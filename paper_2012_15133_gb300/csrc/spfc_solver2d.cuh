@@ -97,15 +97,19 @@ template <typename R> inline void host_twiddles(std::vector<C_t<R>>& tw) {
 // (k2d_step_persist): the last index of every grid; its start-up and
 // diagnostics passes use schedule 0's tiles.
 constexpr int persist_schedule(int N) { return (N >= 128) ? 6 : 1; }
+// From N = 128, schedule 7: the persistent step with 4 values per FFT lane
+// (twice the threads per sequence).
+constexpr int persist_e4_schedule(int N) { return (N >= 128) ? 7 : -1; }
 // Steps per launch of the persistent kernel (a long run is a few launches).
 constexpr long long kPersistMaxSteps = 4096;
 
 template <typename R, int N, int SCHED = 0>
 class Solver2D final : public SolverBase {
   using C = C_t<R>;
-  static constexpr bool PERSIST = (SCHED == persist_schedule(N));
+  static constexpr bool PERSIST = (SCHED == persist_schedule(N) || SCHED == persist_e4_schedule(N));
+  static constexpr int PEV = (SCHED == persist_e4_schedule(N)) ? 4 : 8;
   using SH = Shape2D<N, PERSIST ? 0 : SCHED>;
-  using PS = PShape<R, N>;
+  using PS = PShape<R, N, PEV>;
   static constexpr int NH = N / 2 + 1;
   static constexpr int CT = SH::CT, RPC = SH::RPC, T = SH::T, E = SH::E;
   static constexpr int GCOL = (NH + CT - 1) / CT;
@@ -191,8 +195,8 @@ class Solver2D final : public SolverBase {
         return 3;
       }
       if (PERSIST) {
-        SPFC_CK(set_smem(k2d_step_persist<R, N>, PS::smem_bytes()));
-        SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_step_persist<R, N>, PS::NT,
+        SPFC_CK(set_smem(k2d_step_persist<R, N, PEV>, PS::smem_bytes()));
+        SPFC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2d_step_persist<R, N, PEV>, PS::NT,
                                                                PS::smem_bytes()));
         if (per * nsm < PS::G) {
           err = "the persistent step does not fit co-resident on this GPU";
@@ -731,7 +735,7 @@ class Solver2D final : public SolverBase {
   // nsteps BDF2 steps in one cooperative launch (W prepared, nothing pending)
   int launch_persist(int nsteps) {
     const unsigned long long base = bar_rounds_ * (unsigned long long)PS::G;
-    SPFC_CK(launch_k(k2d_step_persist<R, N>, PS::G, PS::NT, PS::smem_bytes(), st_, false, true, P, S_, W_[0],
+    SPFC_CK(launch_k(k2d_step_persist<R, N, PEV>, PS::G, PS::NT, PS::smem_bytes(), st_, false, true, P, S_, W_[0],
                      W_[1], partP_, partP_ + 2 * PS::G, sc_, sync64p_, base, tw_, nsteps));
     bar_rounds_ += 3ull * (unsigned long long)nsteps - 1ull;  // the launch's barrier rounds
     return 0;
@@ -847,7 +851,7 @@ class Solver2D final : public SolverBase {
 
 // Number of launch schedules compiled for a 2D grid size: the tile shapes of
 // the two-kernel step (six from N = 128, one below) and the persistent step.
-inline int num_schedules_2d(int N) { return persist_schedule(N) + 1; }
+inline int num_schedules_2d(int N) { return (N >= 128 ? persist_e4_schedule(N) : persist_schedule(N)) + 1; }
 
 template <typename R, int N, int SCHED>
 SolverBase* new_solver_2d(const Params& P, cudaStream_t st, int* status, std::string* err) {
@@ -874,6 +878,7 @@ SolverBase* make_solver_2d_n(const Params& P, cudaStream_t st, int schedule, int
     case 4: return new_solver_2d<R, N, 4>(P, st, status, err);
     case 5: return new_solver_2d<R, N, 5>(P, st, status, err);
     case 6: return new_solver_2d<R, N, 6>(P, st, status, err);
+    case 7: return new_solver_2d<R, N, 7>(P, st, status, err);
     default: return new_solver_2d<R, N, 0>(P, st, status, err);
   }
 }

@@ -40,8 +40,8 @@ namespace spfc {
 // threads), G = ceil((N/2+1)/CT) blocks; in the row pass each group of T
 // lanes takes NSR rows at once (2 in float32; 1 in float64, for registers),
 // the block RPB rows in NRR rounds.
-template <typename R, int N> struct PShape {
-  static constexpr int E = 8;
+template <typename R, int N, int EV = 8> struct PShape {
+  static constexpr int E = EV;
   static constexpr int T = N / E;
   static constexpr int CT = (32 / T > 2) ? 32 / T : 2;
   static constexpr int NT = CT * T;
@@ -194,15 +194,15 @@ __device__ __forceinline__ void block_sum_values(double* d, double (*sd)[32]) {
   }
 }
 
-template <typename R, int N>
-__global__ void __launch_bounds__(PShape<R, N>::NT)
+template <typename R, int N, int EV>
+__global__ void __launch_bounds__(PShape<R, N, EV>::NT)
 k2d_step_persist(const Params P, Slots<R> S, C_t<R>* __restrict__ W0, C_t<R>* __restrict__ W1,
                  double* __restrict__ partE, double* __restrict__ partG, SavScal* __restrict__ sc,
                  unsigned long long* __restrict__ sync64, unsigned long long bar_base,
                  const C_t<R>* __restrict__ tw_g, int nsteps) {
   using C = C_t<R>;
   using RD = Red<R>;
-  using SH = PShape<R, N>;
+  using SH = PShape<R, N, EV>;
   constexpr int E = SH::E, T = SH::T, CT = SH::CT, NH = SH::NH, SEQ = SH::SEQ, CTP = SH::CTP;
   constexpr int NSR = SH::NSR, RPR = SH::RPR, RPB = SH::RPB, NRR = SH::NRR;
   constexpr int KH = (N / 2) / T;  // half-spectrum entries per lane in the row split, Nyquist aside

@@ -197,12 +197,12 @@ def test_device_pointer_io_matches_host_io():
     assert np.array_equal(out.cpu().numpy(), s1.get_field(0))
 
 
-@pytest.mark.parametrize("schedule,classes", [(0, {"row", "col_fused"}), (6, {"step"})])
+@pytest.mark.parametrize("schedule,classes", [(0, {"row", "col_fused"}), (6, {"step"}), (7, {"step"})])
 def test_timing_mode_matches_production_mode(schedule, classes):
     """Per-kernel timed launches (one step per launch, events around each)
     give the same steps as production launches: the graph-replayed two-kernel
     step (schedule 0) and the persistent step, whose production launch runs
-    all seven steps in one kernel (schedule 6)."""
+    all seven steps in one kernel (schedules 6 and 7)."""
     c = crystal_2d_case(128)
     a = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
     b = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
@@ -279,7 +279,7 @@ def test_device_noise_start_equals_the_host_noise_field():
         assert np.array_equal(a.get_field(0), b.get_field(0))
 
 
-@pytest.mark.parametrize("schedule", [0, 6])
+@pytest.mark.parametrize("schedule", [0, 6, 7])
 def test_scalar_ring_records_every_step(schedule):
     """The device writes every committed step's scalars into a pinned host
     ring (no per-step synchronisation): after one sync the records equal the
