@@ -250,8 +250,7 @@ class Solver3D final : public SolverBase {
   }
 
   int sync() override {
-    SPFC_CK(cudaStreamSynchronize(st_));
-    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));
+    SPFC_CK(cudaMemcpyAsync(hsc_, sc_, sizeof(SavScal), cudaMemcpyDeviceToHost, st_));  // after all queued work
     SPFC_CK(cudaStreamSynchronize(st_));
     SavScal h = *hsc_;
     if (h.status != DEV_OK) {
@@ -456,10 +455,12 @@ class Solver3D final : public SolverBase {
   int load_field(const double* f, bool on_device, int slot_rel, bool reset) {
     const size_t bytes = (size_t)N * N * N * sizeof(double);
     if (reset) {
-      SavScal z{};
-      apply_ring(&z);
-      SPFC_CK(cudaMemcpyAsync(sc_, &z, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
-      SPFC_CK(cudaStreamSynchronize(st_));  // z is a stack object
+      // the cleared record goes up from the pinned buffer, so the copy does not
+      // synchronise the stream; the buffer is not written again before the
+      // synchronisation at the end of this call
+      *hsc_ = SavScal{};
+      apply_ring(hsc_);
+      SPFC_CK(cudaMemcpyAsync(sc_, hsc_, sizeof(SavScal), cudaMemcpyHostToDevice, st_));
       drop_graphs();
     }
     SPFC_CK(cudaMemcpyAsync(real_, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st_));
