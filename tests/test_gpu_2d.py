@@ -309,3 +309,28 @@ def test_scalar_ring_records_every_step(schedule):
         assert e[4] == sc["gamma"] and e[5] == sc["E1"] and e[7] == 0.0
     assert np.array_equal(a.get_field(0), b.get_field(0))
     a.set_scalar_ring(None)
+
+
+@pytest.mark.parametrize("schedule", [6, 7])
+def test_persistent_step_failure_latches_status_and_context_survives(schedule):
+    """A finite state whose step overflows (|grad phi|^4 beyond float32) makes
+    the persistent step's scalar solve fail: every block takes the same
+    decision and returns, the status word reports a non-finite value, a later
+    launch on the failed handle returns at entry with the same error, and the
+    context stays usable."""
+    from paper_2012_15133_gb300 import SPFCError
+    c = crystal_2d_case(128)
+    s = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
+    big = c["phi0"] * 1e20
+    s.set_state(big, big, 1.0, 1.0)
+    with pytest.raises(SPFCError) as ei:
+        s.step(3)
+        s.sync()
+    assert ei.value.code == 4
+    with pytest.raises(SPFCError) as ei:
+        s.step(1)
+        s.sync()
+    assert ei.value.code == 4
+    good = _solver(c, "fp32", schedule=schedule).init(c["phi0"], "bdf1")
+    good.step(4)
+    assert np.all(np.isfinite(good.get_field(0)))
