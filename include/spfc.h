@@ -227,11 +227,13 @@ int spfc_kernel_times(spfc_t h, int max, const char** names, int64_t* launches, 
 int64_t spfc_device_bytes(spfc_t h);
 
 /* Self-test of failure detection (the paper has no counterpart): runs the
- * bounded device-side wait of the fused column pass's grid barrier on a
- * counter that starts at 0 and that nothing advances, for at most `polls`
- * polls (~100 ns each, polls <= 2^24). Returns SPFC_ETIMEOUT when the wait
- * ran out (target > 0), SPFC_OK when it was already satisfied (target == 0),
- * SPFC_EINVAL for a bad poll count. The context stays usable either way. */
+ * bounded device-side waits of the grid barriers (the fused column pass's,
+ * then the persistent step's acquire polls) on a counter that starts at 0
+ * and that nothing advances, each for at most `polls` polls (~100 ns each,
+ * polls <= 2^24). Returns SPFC_ETIMEOUT when the waits ran out (target > 0),
+ * SPFC_OK when they were already satisfied (target == 0), SPFC_EINVAL for a
+ * bad poll count, SPFC_ECUDA if the two disagree. The context stays usable
+ * either way. */
 int spfc_wait_selftest(unsigned long long target, long long polls, void* cuda_stream);
 
 /* Measured float64 FMA throughput of the current device in GFLOP/s (one FMA

@@ -1,18 +1,24 @@
-// Self-test of the device-side bounded wait used by the grid barrier of the
-// fused column pass (declared in include/spfc.h).
+// Self-test of the device-side bounded waits used by the grid barriers of
+// the fused column pass and of the persistent step (declared in
+// include/spfc.h).
 #include <cuda_runtime.h>
 
 #include "../../include/spfc.h"
-#include "spfc_kernels2d.cuh"
+#include "spfc_step2d_persist.cuh"
 
 namespace {
 
-// One thread waits (bounded) until *ctr >= target; nothing advances the
-// counter, so the wait ends by its limit unless target <= *ctr already.
+// One thread runs both bounded waits (the fused column pass's, then the
+// persistent step's acquire polls) until *ctr >= target; nothing advances the
+// counter, so each ends by its limit unless target <= *ctr already. Both give
+// the same answer, or the status reports the disagreement (-1).
 __global__ void k_wait_selftest(const unsigned long long* ctr, unsigned long long target, long long polls,
                                 int* status) {
-  if (threadIdx.x == 0 && blockIdx.x == 0)
-    *status = spfc::wait_counter(ctr, target, polls) ? (int)spfc::DEV_OK : (int)spfc::DEV_TIMEOUT;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const bool a = spfc::wait_counter(ctr, target, polls);
+    const bool b = spfc::wait_counter_acquire(ctr, target, polls);
+    *status = (a != b) ? -1 : (a ? (int)spfc::DEV_OK : (int)spfc::DEV_TIMEOUT);
+  }
 }
 
 }  // namespace
