@@ -319,7 +319,11 @@ const char* spfc_batch_last_error(spfc_batch_t b);
  * complex channel mixing, inverse truncated DFT, 1x1 conv, GELU), projection
  * width -> proj -> 1, output phi^n + 0.1 (d - mean d) (mass kept exactly).
  * Weights: float32 master and bfloat16 copy; products in BF16 with float32
- * accumulation. Fields are float32 device arrays [batch][n][n].
+ * accumulation, on the fifth-generation tensor cores (tcgen05.mma with the
+ * accumulator in tensor memory). Fields are float32 device arrays
+ * [batch][n][n]. The products' device-side waits are bounded: one that runs
+ * out latches a status that spfc_fno_predict, spfc_fno_loss_grad (and every
+ * later call of the handle) report as SPFC_ETIMEOUT.
  * ------------------------------------------------------------------------- */
 typedef struct spfc_fno_s* spfc_fno_t;
 
@@ -339,6 +343,17 @@ int spfc_fno_loss_grad(spfc_fno_t f, int batch, const float* phi_n, const float*
 int spfc_fno_adam_step(spfc_fno_t f, float lr, float beta1, float beta2, float epsilon, float weight_decay);
 void spfc_fno_destroy(spfc_fno_t f);
 const char* spfc_fno_last_error(spfc_fno_t f);
+/* Self-test of the network's tensor-core product (no paper counterpart):
+ * C[b] = A[b] B[b] for b < batch, A M x K, B K x N, C M x N, all float32 host
+ * arrays, row-major, batches contiguous. The product rounds A and B to
+ * bfloat16 (nearest even) and accumulates in float32; splits > 1 sums K in
+ * `splits` chunks in a fixed order. flags: 1 = A stored as bfloat16 on the
+ * device, 2 = A stored column-major, 4 = B stored column-major (the storage
+ * only; the arguments stay row-major). Synchronises the stream. SPFC_EINVAL
+ * for bad sizes (each array <= 2^26 elements, splits <= 1024) or flags,
+ * SPFC_ETIMEOUT if a bounded wait ran out. */
+int spfc_gemm_selftest(int M, int N, int K, int batch, int splits, int flags, const float* A, const float* B,
+                       float* C, void* cuda_stream);
 /* Weight file: magic "SPFCFNO1", int32 {n, width, modes1, modes2, layers,
  * proj}, int64 parameter count, then the float32 parameters in the order of
  * spfc_fno_set_params. spfc_fno_load requires a network of the same shape

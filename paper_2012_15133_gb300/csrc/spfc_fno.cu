@@ -270,6 +270,7 @@ struct spfc_fno_s {
   std::vector<float*> v, u, Vh;
   float *eps_d = nullptr, *beta_d = nullptr, *ws = nullptr, *out = nullptr;
   double *mean = nullptr, *dmean = nullptr, *lossb = nullptr, *bpart = nullptr;
+  int* gstat = nullptr;  // set to 1 by a GEMM whose bounded wait ran out
   // gradients of activations
   float *gd = nullptr, *gz = nullptr, *gv0 = nullptr, *gv1 = nullptr, *gu = nullptr, *gXf = nullptr, *gVh = nullptr,
         *gOh = nullptr, *gZ = nullptr;
@@ -294,10 +295,20 @@ struct spfc_fno_s {
 
   int gemm(int M, int N, int K, int batch, const Mat& A, const Mat& B, const Out& O, int splits = 1) {
     while (splits > 1 && (long long)batch * splits * M * N > ws_elems) splits /= 2;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch * splits);
-    k_gemm<<<grid, GT, 0, st>>>(M, N, K, batch, splits, A, B, O, ws);
-    if (splits > 1) k_gemm_reduce<<<1024, 256, 0, st>>>(M, N, batch, splits, ws, O);
-    return ck(cudaGetLastError(), "gemm");
+    return ck(launch_gemm(M, N, K, batch, A, B, O, splits, ws, gstat, st), "gemm");
+  }
+
+  // The GEMMs' latched status (a bounded tensor-core wait that ran out),
+  // read with the stream's work so far.
+  int check_status() {
+    int h = 0;
+    int rc = ck(cudaMemcpyAsync(&h, gstat, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    if (!rc) rc = ck(cudaStreamSynchronize(st), "sync");
+    if (!rc && h != 0) {
+      err = "tensor-core GEMM: a bounded wait ran out";
+      rc = SPFC_ETIMEOUT;
+    }
+    return rc;
   }
 
   Mat mf(const float* p, Ix r, Ix c, long long sb = 0) {
@@ -410,7 +421,9 @@ struct spfc_fno_s {
         (rc = alloc(&gOh, mix)) || (rc = alloc(&gZ, spec)))
       return rc;
     ws_elems = 4LL << 20;  // split-K partial tiles of the weight-gradient GEMMs (M, N <= 64)
-    if ((rc = alloc(&ws, ws_elems)) || (rc = alloc(&bpart, 64LL * kBiasChunks))) return rc;
+    if ((rc = alloc(&ws, ws_elems)) || (rc = alloc(&bpart, 64LL * kBiasChunks)) || (rc = alloc(&gstat, 1)))
+      return rc;
+    if ((rc = ck(cudaMemset(gstat, 0, sizeof(int)), "memset"))) return rc;
     const size_t smix = (size_t)(2 * W * W + 4 * Bmax * W) * sizeof(float);
     if (smix > 48 * 1024) {
       if ((rc = ck(cudaFuncSetAttribute(k_mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smix), "attr")) ||
@@ -566,7 +579,7 @@ struct spfc_fno_s {
     for (int i = 0; i < B; ++i) { e[i] = (float)eps[i]; bt[i] = (float)beta[i]; }
     int rc = ck(cudaMemcpyAsync(eps_d, e.data(), B * 4, cudaMemcpyHostToDevice, st), "eps");
     if (!rc) rc = ck(cudaMemcpyAsync(beta_d, bt.data(), B * 4, cudaMemcpyHostToDevice, st), "beta");
-    if (!rc) rc = ck(cudaStreamSynchronize(st), "sync");
+    if (!rc) rc = check_status();  // also reports a wait that ran out in an earlier call
     return rc;
   }
 };
@@ -686,7 +699,7 @@ int spfc_fno_loss_grad(spfc_fno_t f, int batch, const float* phi_n, const float*
   if ((rc = f->ck(cudaMemcpyAsync(lb.data(), f->lossb, batch * 8, cudaMemcpyDeviceToHost, f->st), "loss"))) return rc;
   if (grad_host && (rc = f->ck(cudaMemcpyAsync(grad_host, f->g, f->np * 4, cudaMemcpyDeviceToHost, f->st), "grad")))
     return rc;
-  if ((rc = f->ck(cudaStreamSynchronize(f->st), "sync"))) return rc;
+  if ((rc = f->check_status())) return rc;
   double s = 0.0;
   for (double x : lb) s += x;
   if (loss) *loss = s / ((double)batch * f->P);
@@ -703,6 +716,81 @@ int spfc_fno_adam_step(spfc_fno_t f, float lr, float beta1, float beta2, float e
 }
 
 void spfc_fno_destroy(spfc_fno_t f) { delete f; }
+
+int spfc_gemm_selftest(int M, int N, int K, int batch, int splits, int flags, const float* A, const float* B,
+                       float* C, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || splits < 1 || splits > 1024 || (flags & ~7))
+    return SPFC_EINVAL;
+  const long long na = (long long)batch * M * K, nb = (long long)batch * K * N, nc = (long long)batch * M * N;
+  if (na > (1ll << 26) || nb > (1ll << 26) || nc * splits > (1ll << 26)) return SPFC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool a_bf16 = flags & 1, a_t = flags & 2, b_t = flags & 4;
+  // host copies in the requested storage: A column-major per batch (a_t), B column-major (b_t)
+  std::vector<float> ha((size_t)na), hb((size_t)nb);
+  for (long long b = 0; b < batch; ++b)
+    for (int m = 0; m < M; ++m)
+      for (int k = 0; k < K; ++k)
+        ha[(size_t)(b * M * K + (a_t ? (long long)k * M + m : (long long)m * K + k))] = A[b * M * K + (long long)m * K + k];
+  for (long long b = 0; b < batch; ++b)
+    for (int k = 0; k < K; ++k)
+      for (int n = 0; n < N; ++n)
+        hb[(size_t)(b * K * N + (b_t ? (long long)n * K + k : (long long)k * N + n))] = B[b * K * N + (long long)k * N + n];
+  std::vector<uint16_t> ha16;
+  if (a_bf16) {  // round to nearest even, as the kernel's own conversion does
+    ha16.resize(ha.size());
+    for (size_t i = 0; i < ha.size(); ++i) {
+      uint32_t u;
+      std::memcpy(&u, &ha[i], 4);
+      ha16[i] = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+    }
+  }
+  void* da = nullptr;
+  float *db = nullptr, *dc = nullptr, *ws = nullptr;
+  int* status = nullptr;
+  int rc = SPFC_OK;
+  auto fail = [&](cudaError_t e) { return e != cudaSuccess; };
+  if (fail(cudaMalloc(&da, (size_t)na * (a_bf16 ? 2 : 4))) || fail(cudaMalloc((void**)&db, (size_t)nb * 4)) ||
+      fail(cudaMalloc((void**)&dc, (size_t)nc * 4)) ||
+      fail(cudaMalloc((void**)&ws, (size_t)(splits > 1 ? nc * splits : 1) * 4)) ||
+      fail(cudaMalloc((void**)&status, sizeof(int))))
+    rc = SPFC_ENOMEM;
+  int hs = 0;
+  if (!rc) {
+    cudaError_t e = a_bf16 ? cudaMemcpyAsync(da, ha16.data(), (size_t)na * 2, cudaMemcpyHostToDevice, st)
+                           : cudaMemcpyAsync(da, ha.data(), (size_t)na * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db, hb.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+      Mat ma, mbm;
+      ma.p = da;
+      ma.bf16 = a_bf16 ? 1 : 0;
+      ma.r = a_t ? make_ix(1) : make_ix(K);
+      ma.c = a_t ? make_ix(M) : make_ix(1);
+      ma.sb = (long long)M * K;
+      mbm.p = db;
+      mbm.r = b_t ? make_ix(1) : make_ix(N);
+      mbm.c = b_t ? make_ix(K) : make_ix(1);
+      mbm.sb = (long long)K * N;
+      Out o;
+      o.p = dc;
+      o.r = make_ix(N);
+      o.c = make_ix(1);
+      o.sb = (long long)M * N;
+      e = launch_gemm(M, N, K, batch, ma, mbm, o, splits, ws, status, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(C, dc, (size_t)nc * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = SPFC_ECUDA;
+  }
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dc);
+  cudaFree(ws);
+  cudaFree(status);
+  if (!rc && hs != 0) rc = SPFC_ETIMEOUT;
+  return rc;
+}
 
 const char* spfc_fno_last_error(spfc_fno_t f) { return f ? f->err.c_str() : g_fno_err.c_str(); }
 

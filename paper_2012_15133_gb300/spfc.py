@@ -83,6 +83,7 @@ _SIGS = {
     "spfc_fno_adam_step": (_I, [_P, _F, _F, _F, _F, _F]),
     "spfc_fno_destroy": (None, [_P]),
     "spfc_fno_last_error": (ct.c_char_p, [_P]),
+    "spfc_gemm_selftest": (_I, [_I, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "spfc_fno_save": (_I, [_P, ct.c_char_p]),
     "spfc_fno_load": (_I, [_P, ct.c_char_p]),
     "spfc_surrogate_advance": (_I, [_P, ct.POINTER(_P), ct.POINTER(_P), _I, _I, _I, _I, _D,
@@ -163,6 +164,29 @@ def fp64_fma_rate(stream=None):
     if rc != 0:
         raise SPFCError(rc, "FP64 FMA rate measurement failed")
     return out.value
+
+
+def gemm_selftest(A, B, splits=1, flags=0, stream=None):
+    """C = A @ B through the surrogate network's tensor-core product (operands
+    rounded to bfloat16, float32 accumulation). A: (batch, M, K), B: (batch,
+    K, N) float32 host arrays; flags select the device storage of A and B
+    (see include/spfc.h). Returns C as a (batch, M, N) float32 array."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    if A.ndim != 3 or B.ndim != 3 or A.shape[0] != B.shape[0] or A.shape[2] != B.shape[1]:
+        raise ValueError("A must be (batch, M, K) and B (batch, K, N)")
+    bt, M, K = A.shape
+    N = B.shape[2]
+    C = np.empty((bt, M, N), dtype=np.float32)
+    lib = load_library()
+    sp = _current_stream_ptr() if stream is None else ct.c_void_p(
+        stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = lib.spfc_gemm_selftest(M, N, K, bt, int(splits), int(flags), A.ctypes.data_as(_P),
+                                B.ctypes.data_as(_P), C.ctypes.data_as(_P), sp)
+    if rc != 0:
+        raise SPFCError(rc, "tensor-core GEMM self-test failed")
+    return C
 
 
 def num_schedules(d, n):

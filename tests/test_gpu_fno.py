@@ -150,3 +150,56 @@ def test_invalid_sizes_are_rejected():
     x = torch.zeros((3, 32, 32), device="cuda")
     with pytest.raises(SPFCError):
         net.predict(x, x, [0.1] * 3, [1.0] * 3)
+
+
+def _round_bf16(x):
+    """float32 -> bfloat16 -> float32, round to nearest even (bit arithmetic)."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+# (batch, M, N, K, splits, flags): ragged tiles in every dimension; the tile's
+# rows on M or on N (N > M); 16-, 32- and 64-column tiles; K below one stage,
+# not a multiple of 8, and many stages; split-K with empty splits; each device
+# storage (A as bfloat16, A or B column-major: strided and contiguous gathers,
+# aligned and unaligned).
+GEMM_CASES = [
+    (1, 200, 64, 70, 1, 0),
+    (2, 33, 300, 45, 1, 0),
+    (3, 128, 16, 256, 1, 1),
+    (1, 64, 5, 513, 1, 2),
+    (1, 1, 1000, 40, 1, 4),
+    (1, 40, 24, 1000, 4, 0),
+    (1, 17, 29, 100, 8, 3),
+    (2, 130, 100, 32, 1, 6),
+    (1, 8, 1, 7, 1, 7),
+    (4, 300, 48, 96, 1, 5),
+]
+
+
+@pytest.mark.parametrize("bt,M,N,K,splits,flags", GEMM_CASES)
+def test_tensor_core_gemm_matches_the_bf16_product(bt, M, N, K, splits, flags):
+    """The tcgen05 product equals the float64 product of the bf16-rounded
+    operands to float32 accumulation: |C - ref| <= 4 K 2^-24 (|A| |B|)."""
+    from paper_2012_15133_gb300 import spfc
+    rng = np.random.default_rng(1000 + M + 7 * N + 13 * K + flags)
+    A = rng.standard_normal((bt, M, K)).astype(np.float32)
+    B = rng.standard_normal((bt, K, N)).astype(np.float32)
+    C = spfc.gemm_selftest(A, B, splits=splits, flags=flags)
+    Ab = _round_bf16(A).astype(np.float64)
+    Bb = _round_bf16(B).astype(np.float64)
+    ref = Ab @ Bb
+    bound = 4 * K * 2.0 ** -24 * (np.abs(Ab) @ np.abs(Bb)) + 1e-30
+    err = np.abs(C.astype(np.float64) - ref)
+    assert np.all(err <= bound), (float(np.max(err / bound)), np.unravel_index(np.argmax(err / bound), err.shape))
+
+
+def test_tensor_core_gemm_is_deterministic():
+    from paper_2012_15133_gb300 import spfc
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((2, 150, 300)).astype(np.float32)
+    B = rng.standard_normal((2, 300, 40)).astype(np.float32)
+    C1 = spfc.gemm_selftest(A, B, splits=3)
+    C2 = spfc.gemm_selftest(A, B, splits=3)
+    assert np.array_equal(C1, C2)
