@@ -134,7 +134,8 @@ constexpr int kXBytes = TM * TK * 2;     // one stage of X (BF16)
 constexpr int kYBytes = TNMAX * TK * 2;  // one stage of Y
 constexpr int kStage = kXBytes + kYBytes;
 constexpr int kEpiPitch = TNMAX + 1;
-constexpr int kTcSmem = (2 * kStage > TM * kEpiPitch * 4) ? 2 * kStage : TM * kEpiPitch * 4;
+constexpr int kEpiBytes = (2 * kStage > TM * kEpiPitch * 4) ? 2 * kStage : TM * kEpiPitch * 4;
+constexpr int kTcSmem = kEpiBytes + (TM + TNMAX) * 8 + (TM + TNMAX) * 4;  // + per-row/column offsets and biases
 constexpr long long kTcWaitNs = 1000000000ll;  // bound of one mbarrier wait
 
 // One MMA operand: element (r, k) at sb * batch + rm(r) + km(k).
@@ -425,11 +426,56 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) cs[row * kEpiPitch + cb + j] = __uint_as_float(r[j]);
   }
+  // Per tile row and per tile column: the output offset and the bias term
+  // (the index maps and the bias's division once per row or column, not per
+  // element). With split-K the offsets address the partial-sum workspace.
+  long long* poff = reinterpret_cast<long long*>(tc_smem + kEpiBytes);
+  long long* qoff = poff + TM;
+  float* pbias = reinterpret_cast<float*>(qoff + TNMAX);
+  float* qbias = pbias + TM;
+  {
+    const Out& o = g.O;
+    const bool spl = g.splits > 1;
+    const int p = p0 + tid;  // TT == TM: one tile row per thread
+    long long po = 0;
+    float pb = 0.f;
+    if (p < g.X.rows) {
+      if (!g.swap) {  // tile row = output row
+        po = spl ? ((long long)z * g.M + p) * g.N : o.r(p);
+        if (!spl && o.bias && !o.bias_col) pb = o.bias[(p / o.bdiv) % o.bmod];
+      } else {        // tile row = output column
+        po = spl ? (long long)p : o.c(p);
+        if (!spl && o.bias && o.bias_col) pb = o.bias[p];
+      }
+    }
+    poff[tid] = po;
+    pbias[tid] = pb;
+    if (tid < g.tn) {
+      const int q = q0 + tid;
+      long long qo = 0;
+      float qb = 0.f;
+      if (q < g.Y.rows) {
+        if (!g.swap) {
+          qo = spl ? (long long)q : o.c(q);
+          if (!spl && o.bias && o.bias_col) qb = o.bias[q];
+        } else {
+          qo = spl ? ((long long)z * g.M + q) * g.N : o.r(q);
+          if (!spl && o.bias && !o.bias_col) qb = o.bias[(q / o.bdiv) % o.bmod];
+        }
+      }
+      qoff[tid] = qo;
+      qbias[tid] = qb;
+    }
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TNMAX) : "memory");
 
-  const long long obase = (long long)bt * g.O.sb;
+  const Out& o = g.O;
+  float* const dst = g.splits > 1 ? g.ws : o.p + (long long)bt * o.sb;
+  const float* const cin = o.beta != 0.f ? (o.cin ? o.cin : o.p) + (long long)bt * o.sb : nullptr;
+  float* const pre = o.pre ? o.pre + (long long)bt * o.sb : nullptr;
+  const bool raw = g.splits > 1;
   const int total = TM * g.tn;
   for (int lin = tid; lin < total; lin += TT) {
     int i, j;
@@ -440,12 +486,21 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
       j = lin & (g.tn - 1);
       i = lin >> g.tn_log2;
     }
-    const int p = p0 + i, q = q0 + j;
-    if (p >= g.X.rows || q >= g.Y.rows) continue;
+    if (p0 + i >= g.X.rows || q0 + j >= g.Y.rows) continue;
     const float acc = cs[i * kEpiPitch + j];
-    const int orow = g.swap ? q : p, ocol = g.swap ? p : q;
-    if (g.splits > 1) g.ws[((long long)z * g.M + orow) * g.N + ocol] = acc;
-    else store_out(g.O, obase, orow, ocol, acc);
+    const long long off = poff[i] + qoff[j];
+    if (raw) {
+      dst[off] = acc;
+      continue;
+    }
+    float v = o.alpha * acc;  // the order of store_out: alpha A B, + beta C, + bias, then GELU
+    if (cin) v += o.beta * cin[off];
+    if (o.bias) v += pbias[i] + qbias[j];  // one of the two is zero
+    if (o.act == 1) {
+      if (pre) pre[off] = v;
+      v = gelu_f(v);
+    }
+    dst[off] = v;
   }
 }
 
