@@ -6,6 +6,7 @@
 // GELU between layers), projection W -> Q -> 1, output phi^n + s (d - mean d).
 // Weights are held in float32 (master, for Adam) and bfloat16 (used by every
 // product); accumulation is float32.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -28,12 +29,28 @@ constexpr float kScale = 0.1f;
 // small kernels
 // --------------------------------------------------------------------------
 
-// per-sample mean of x[b][0..P) (float64 accumulation, fixed order); one block per sample
-__global__ void k_sample_mean(const float* __restrict__ x, int P, double* __restrict__ mean) {
+// Per-sample sums of x[b][0..P) in float64 and a fixed order, in two stages
+// so that every SM takes part: kSampleChunks contiguous chunks per sample
+// (grid (kSampleChunks, B)), then one block per sample sums its chunk
+// partials.
+constexpr int kSampleChunks = 64;
+
+__global__ void k_sample_part(const float* __restrict__ x, int P, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int j = blockIdx.x, b = blockIdx.y;
+  const int len = (P + kSampleChunks - 1) / kSampleChunks;
+  const int i1 = min(P, (j + 1) * len);
+  double s = 0.0;
+  for (int p = j * len + threadIdx.x; p < i1; p += blockDim.x) s += (double)x[(long long)b * P + p];
+  s = spfc::block_sum(s, red);
+  if (threadIdx.x == 0) part[b * kSampleChunks + j] = s;
+}
+
+// mean[b] = (sum of the chunk partials of sample b) / P; kSampleChunks threads per block
+__global__ void k_sample_final(const double* __restrict__ part, int P, double* __restrict__ mean) {
   __shared__ double red[32];
   const int b = blockIdx.x;
-  double s = 0.0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s += (double)x[(long long)b * P + p];
+  double s = part[b * kSampleChunks + threadIdx.x];
   s = spfc::block_sum(s, red);
   if (threadIdx.x == 0) mean[b] = s / P;
 }
@@ -152,45 +169,71 @@ __global__ void k_output(int B, int P, const float* __restrict__ phi_n, const fl
     out[i] = phi_n[i] + kScale * (d[i] - (float)dmean[i / P]);
 }
 
-// Loss and dL/dd for one sample per block (two passes over the sample).
-__global__ void k_loss(int P, float inv_cnt, const float* __restrict__ d, const double* __restrict__ dmean,
-                       const float* __restrict__ phi_n, const float* __restrict__ target, double* __restrict__ loss_b,
-                       float* __restrict__ gd) {
+// Loss and dL/dd of the mean-free residual res = d - mean d - (target - phi^n) / s:
+// partial sums over chunks, per-sample totals, then the gradient pass.
+__device__ __forceinline__ float loss_res(const float* __restrict__ d, float dm, const float* __restrict__ phi_n,
+                                          const float* __restrict__ target, long long i) {
+  return d[i] - dm - (target[i] - phi_n[i]) / kScale;
+}
+
+// partial sums of the residual and its square per (chunk, sample); grid (kSampleChunks, B)
+__global__ void k_loss_part(int P, const float* __restrict__ d, const double* __restrict__ dmean,
+                            const float* __restrict__ phi_n, const float* __restrict__ target,
+                            double* __restrict__ part) {
   __shared__ double red[32];
-  __shared__ double mres_s;
-  const int b = blockIdx.x;
-  const long long o = (long long)b * P;
+  const int j = blockIdx.x, b = blockIdx.y;
   const float dm = (float)dmean[b];
+  const int len = (P + kSampleChunks - 1) / kSampleChunks;
+  const int i1 = min(P, (j + 1) * len);
   double s1 = 0.0, s2 = 0.0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const float res = d[o + p] - dm - (target[o + p] - phi_n[o + p]) / kScale;
+  for (int p = j * len + threadIdx.x; p < i1; p += blockDim.x) {
+    const float res = loss_res(d, dm, phi_n, target, (long long)b * P + p);
     s1 += res;
     s2 += (double)res * res;
   }
   s1 = spfc::block_sum(s1, red);
   s2 = spfc::block_sum(s2, red);
   if (threadIdx.x == 0) {
-    mres_s = s1 / P;
+    part[(b * kSampleChunks + j) * 2] = s1;
+    part[(b * kSampleChunks + j) * 2 + 1] = s2;
+  }
+}
+
+// per sample: mean residual and sum of squares from the chunk partials; kSampleChunks threads per block
+__global__ void k_loss_final(int P, const double* __restrict__ part, double* __restrict__ mres,
+                             double* __restrict__ loss_b) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  double s1 = part[(b * kSampleChunks + threadIdx.x) * 2], s2 = part[(b * kSampleChunks + threadIdx.x) * 2 + 1];
+  s1 = spfc::block_sum(s1, red);
+  s2 = spfc::block_sum(s2, red);
+  if (threadIdx.x == 0) {
+    mres[b] = s1 / P;
     loss_b[b] = s2;
   }
-  __syncthreads();
-  const float mres = (float)mres_s;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const float res = d[o + p] - dm - (target[o + p] - phi_n[o + p]) / kScale;
-    gd[o + p] = 2.f * inv_cnt * (res - mres);
+}
+
+// gradient of the mean-square loss of the mean-free residual
+__global__ void k_loss_grad(int B, int P, float inv_cnt, const float* __restrict__ d, const double* __restrict__ dmean,
+                            const double* __restrict__ mres, const float* __restrict__ phi_n,
+                            const float* __restrict__ target, float* __restrict__ gd) {
+  const long long total = (long long)B * P;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / P);
+    const float res = loss_res(d, (float)dmean[b], phi_n, target, i);
+    gd[i] = 2.f * inv_cnt * (res - (float)mres[b]);
   }
 }
 
 // gz[b][q][p] = q2w[q] gd[b][p] gelu'(z[b][q][p])
-__global__ void k_proj_back(int B, int Q, int P, const float* __restrict__ gd, const __nv_bfloat16* __restrict__ q2w,
+// grid (x: chunks of the P points, y: b * Q + q)
+__global__ void k_proj_back(int Q, int P, const float* __restrict__ gd, const __nv_bfloat16* __restrict__ q2w,
                             const float* __restrict__ z, float* __restrict__ gz) {
-  const long long total = (long long)B * Q * P;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(i % P);
-    const long long bq = i / P;
-    const int q = (int)(bq % Q), b = (int)(bq / Q);
-    gz[i] = __bfloat162float(q2w[q]) * gd[(long long)b * P + p] * gelu_grad_f(z[i]);
-  }
+  const int bq = blockIdx.y, b = bq / Q, q = bq - b * Q;
+  const float w = __bfloat162float(q2w[q]);
+  const long long o = (long long)bq * P, ob = (long long)b * P;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    gz[o + p] = w * gd[ob + p] * gelu_grad_f(z[o + p]);
 }
 
 // g *= gelu'(u)
@@ -211,9 +254,14 @@ __global__ void k_bias_grad_part(int B, int C, int P, const float* __restrict__ 
   const long long len = (total + kBiasChunks - 1) / kBiasChunks;
   const long long i0 = j * len, i1 = min(total, i0 + len);
   double s = 0.0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const long long b = i / P, p = i - b * P;
+  long long i = i0 + threadIdx.x, b = i / P, p = i - b * P;  // (b, p) of i, advanced without a division
+  for (; i < i1; i += blockDim.x) {
     s += X[(b * C + c) * P + p];
+    p += blockDim.x;
+    while (p >= P) {
+      p -= P;
+      ++b;
+    }
   }
   s = spfc::block_sum(s, red);
   if (threadIdx.x == 0) part[c * kBiasChunks + j] = s;
@@ -269,7 +317,7 @@ struct spfc_fno_s {
   float *a = nullptr, *z = nullptr, *q = nullptr, *d = nullptr, *Xf = nullptr, *Oh = nullptr, *Zb = nullptr;
   std::vector<float*> v, u, Vh;
   float *eps_d = nullptr, *beta_d = nullptr, *ws = nullptr, *out = nullptr;
-  double *mean = nullptr, *dmean = nullptr, *lossb = nullptr, *bpart = nullptr;
+  double *mean = nullptr, *dmean = nullptr, *lossb = nullptr, *bpart = nullptr, *spart = nullptr, *mres = nullptr;
   int* gstat = nullptr;  // set to 1 by a GEMM whose bounded wait ran out
   // gradients of activations
   float *gd = nullptr, *gz = nullptr, *gv0 = nullptr, *gv1 = nullptr, *gu = nullptr, *gXf = nullptr, *gVh = nullptr,
@@ -414,7 +462,8 @@ struct spfc_fno_s {
     if ((rc = alloc(&a, (long long)Bmax * 4 * P)) || (rc = alloc(&z, BQP)) || (rc = alloc(&q, BQP)) ||
         (rc = alloc(&d, (long long)Bmax * P)) || (rc = alloc(&out, (long long)Bmax * P)) || (rc = alloc(&Xf, spec)) ||
         (rc = alloc(&Oh, mix)) || (rc = alloc(&Zb, spec)) || (rc = alloc(&eps_d, Bmax)) || (rc = alloc(&beta_d, Bmax)) ||
-        (rc = alloc(&mean, Bmax)) || (rc = alloc(&dmean, Bmax)) || (rc = alloc(&lossb, Bmax)))
+        (rc = alloc(&mean, Bmax)) || (rc = alloc(&dmean, Bmax)) || (rc = alloc(&lossb, Bmax)) ||
+        (rc = alloc(&spart, 2LL * Bmax * kSampleChunks)) || (rc = alloc(&mres, Bmax)))
       return rc;
     if ((rc = alloc(&gd, (long long)Bmax * P)) || (rc = alloc(&gz, BQP)) || (rc = alloc(&gv0, BWP)) ||
         (rc = alloc(&gv1, BWP)) || (rc = alloc(&gu, BWP)) || (rc = alloc(&gXf, spec)) || (rc = alloc(&gVh, mix)) ||
@@ -433,12 +482,17 @@ struct spfc_fno_s {
     return 0;
   }
 
+  void sample_mean(int B, const float* x, double* out) {
+    k_sample_part<<<dim3(kSampleChunks, B), 256, 0, st>>>(x, P, spart);
+    k_sample_final<<<B, kSampleChunks, 0, st>>>(spart, P, out);
+  }
+
   int gs(long long n_el) const { return (int)std::min<long long>((n_el + 255) / 256, 4096); }
 
   // forward pass for B samples already in phi_n / phi_nm1 device buffers (float)
   int forward(int B, const float* phi_n, const float* phi_nm1) {
     int rc;
-    k_sample_mean<<<B, 256, 0, st>>>(phi_n, P, mean);
+    sample_mean(B, phi_n, mean);
     k_features_lift<<<gs((long long)B * P), 256, 0, st>>>(B, P, W, phi_n, phi_nm1, eps_d, beta_d, mean, wbf + o_lw,
                                                            wbf + o_lb, a, v[0]);
     if ((rc = ck(cudaGetLastError(), "lift"))) return rc;
@@ -496,7 +550,7 @@ struct spfc_fno_s {
       O2.bmod = 1;
       if ((rc = gemm(1, P, Q, B, mb(o_q2w, ix(Q), ix(1)), mf(q, ix(P), ix(1), (long long)Q * P), O2))) return rc;
     }
-    k_sample_mean<<<B, 256, 0, st>>>(d, P, dmean);
+    sample_mean(B, d, dmean);
     return ck(cudaGetLastError(), "forward");
   }
 
@@ -516,7 +570,7 @@ struct spfc_fno_s {
       Out O = of(g + o_q2w, ix(1), ix(1));
       if ((rc = gemm(1, Q, BP, 1, mf(gd, ix(0), ix(1)), mf(q, ix(1, P, QP), ix(P)), O, splits))) return rc;
       bias_grad(B, 1, gd, g + o_q2b);
-      k_proj_back<<<gs((long long)B * QP), 256, 0, st>>>(B, Q, P, gd, wbf + o_q2w, z, gz);
+      k_proj_back<<<dim3(std::min((P + 255) / 256, 64), B * Q), 256, 0, st>>>(Q, P, gd, wbf + o_q2w, z, gz);
       if ((rc = ck(cudaGetLastError(), "proj_back"))) return rc;
       Out O1 = of(g + o_q1w, ix(W), ix(1));
       if ((rc = gemm(Q, W, BP, 1, mf(gz, ix(P), ix(1, P, QP)), mf(v[L], ix(1, P, WP), ix(P)), O1, splits))) return rc;
@@ -692,7 +746,10 @@ int spfc_fno_loss_grad(spfc_fno_t f, int batch, const float* phi_n, const float*
   if (!rc) rc = f->forward(batch, phi_n, phi_nm1);
   if (rc) return rc;
   const float inv_cnt = 1.f / ((float)batch * f->P);
-  k_loss<<<batch, 256, 0, f->st>>>(f->P, inv_cnt, f->d, f->dmean, phi_n, target, f->lossb, f->gd);
+  k_loss_part<<<dim3(kSampleChunks, batch), 256, 0, f->st>>>(f->P, f->d, f->dmean, phi_n, target, f->spart);
+  k_loss_final<<<batch, kSampleChunks, 0, f->st>>>(f->P, f->spart, f->mres, f->lossb);
+  k_loss_grad<<<f->gs((long long)batch * f->P), 256, 0, f->st>>>(batch, f->P, inv_cnt, f->d, f->dmean, f->mres, phi_n,
+                                                                  target, f->gd);
   if ((rc = f->ck(cudaGetLastError(), "loss"))) return rc;
   if ((rc = f->backward(batch))) return rc;
   std::vector<double> lb(batch);
