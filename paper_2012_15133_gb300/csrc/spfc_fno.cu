@@ -255,10 +255,11 @@ __global__ void k_bias_grad_part(int B, int C, int P, const float* __restrict__ 
   const long long i0 = j * len, i1 = min(total, i0 + len);
   double s = 0.0;
   long long i = i0 + threadIdx.x, b = i / P, p = i - b * P;  // (b, p) of i, advanced without a division
-  for (; i < i1; i += blockDim.x) {
+#pragma unroll 8
+  for (; i < i1; i += blockDim.x) {  // loads of several iterations in flight; the sum in the same order
     s += X[(b * C + c) * P + p];
     p += blockDim.x;
-    while (p >= P) {
+    if (p >= P) {  // blockDim.x <= P: at most one carry
       p -= P;
       ++b;
     }

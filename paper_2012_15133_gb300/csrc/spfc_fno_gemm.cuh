@@ -251,43 +251,79 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// k .. k+7 (k a multiple of 8) of row r as one core-matrix row of BF16;
-// zero beyond the operand's rows or beyond ke.
-__device__ __forceinline__ uint4 gather8(const Opnd& x, long long base, int r, int k, int ke) {
-  float v[8];
+// k .. k+7 (k a multiple of 8) of row r, loaded into v without any use of
+// the loaded values, so that the loads of every chunk of a K step are in
+// flight together (a use would stall the in-order issue until its load
+// lands). Returns how v holds them: 0 float32 values (zero beyond the
+// operand's rows or beyond ke), 1 eight BF16 values already packed in
+// v[0..3], 2 one BF16 bit pattern in the low half of each v[j].
+__device__ __forceinline__ int load8(const Opnd& x, long long base, int r, int k, int ke, float (&v)[8]) {
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = 0.f;
-  if (r < x.rows) {
-    const long long roff = base + x.rm(r);
-    if (x.kcontig && k + 8 <= ke) {
-      const long long off = roff + x.km(k);
-      if (x.bf16) {
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(x.p) + off;
-        if ((reinterpret_cast<uintptr_t>(h) & 15) == 0) return *reinterpret_cast<const uint4*>(h);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __bfloat162float(h[j]);
-      } else {
-        const float* f = reinterpret_cast<const float*>(x.p) + off;
-        if ((reinterpret_cast<uintptr_t>(f) & 15) == 0) {
-          const float4 a = reinterpret_cast<const float4*>(f)[0], b = reinterpret_cast<const float4*>(f)[1];
-          v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-          v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = f[j];
-        }
+  if (r >= x.rows) return 0;
+  const long long roff = base + x.rm(r);
+  if (x.kcontig && k + 8 <= ke) {
+    const long long off = roff + x.km(k);
+    if (x.bf16) {
+      const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(x.p) + off;
+      if ((reinterpret_cast<uintptr_t>(h) & 15) == 0) {
+        const uint4 u = *reinterpret_cast<const uint4*>(h);
+        v[0] = __uint_as_float(u.x);
+        v[1] = __uint_as_float(u.y);
+        v[2] = __uint_as_float(u.z);
+        v[3] = __uint_as_float(u.w);
+        return 1;
       }
+      const unsigned short* hb = reinterpret_cast<const unsigned short*>(h);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __uint_as_float((uint32_t)hb[j]);
+      return 2;
+    }
+    const float* f = reinterpret_cast<const float*>(x.p) + off;
+    if ((reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+      const float4 a = reinterpret_cast<const float4*>(f)[0], b = reinterpret_cast<const float4*>(f)[1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (k + j < ke) v[j] = ldx(x, roff + x.km(k + j));
+      for (int j = 0; j < 8; ++j) v[j] = f[j];
     }
+    return 0;
   }
+  if (x.bf16) {
+    const unsigned short* hb = reinterpret_cast<const unsigned short*>(x.p);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < ke) v[j] = __uint_as_float((uint32_t)hb[roff + x.km(k + j)]);  // zero bits: +0
+    return 2;
+  }
+  const float* f = reinterpret_cast<const float*>(x.p);
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (k + j < ke) v[j] = f[roff + x.km(k + j)];
+  return 0;
+}
+
+// The chunk loaded by load8 as one core-matrix row of BF16 (float32 values
+// rounded to nearest even; BF16 values as they are).
+__device__ __forceinline__ uint4 pack8(int mode, const float (&v)[8]) {
   uint4 u;
-  u.x = pack_bf16(v[0], v[1]);
-  u.y = pack_bf16(v[2], v[3]);
-  u.z = pack_bf16(v[4], v[5]);
-  u.w = pack_bf16(v[6], v[7]);
+  if (mode == 1) {
+    u.x = __float_as_uint(v[0]);
+    u.y = __float_as_uint(v[1]);
+    u.z = __float_as_uint(v[2]);
+    u.w = __float_as_uint(v[3]);
+  } else if (mode == 2) {
+    u.x = __float_as_uint(v[0]) | (__float_as_uint(v[1]) << 16);
+    u.y = __float_as_uint(v[2]) | (__float_as_uint(v[3]) << 16);
+    u.z = __float_as_uint(v[4]) | (__float_as_uint(v[5]) << 16);
+    u.w = __float_as_uint(v[6]) | (__float_as_uint(v[7]) << 16);
+  } else {
+    u.x = pack_bf16(v[0], v[1]);
+    u.y = pack_bf16(v[2], v[3]);
+    u.z = pack_bf16(v[4], v[5]);
+    u.w = pack_bf16(v[6], v[7]);
+  }
   return u;
 }
 
@@ -348,24 +384,25 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
   bool ok = true;
   for (int kt = 0; kt < nk; ++kt) {
     const int k0 = kb + kt * TK;
-    uint4 xr[4], yr[2];
-    int xo[4], yo[2];
+    float xv[4][8], yv[2][8];  // every load of the step is issued before any is used
+    int xo[4], yo[2], xm[4], ym[2];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       int r, kg;
       chunk_rk(g.X.rowfast, tid + e * TT, TM - 1, 7, r, kg);
       xo[e] = core_off(r, kg);
-      xr[e] = gather8(g.X, xb, p0 + r, k0 + kg * 8, ke);
+      xm[e] = load8(g.X, xb, p0 + r, k0 + kg * 8, ke, xv[e]);
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int c = tid + e * TT;
       yo[e] = -1;
+      ym[e] = 0;
       if (c >= g.tn * 4) continue;
       int r, kg;
       chunk_rk(g.Y.rowfast, c, g.tn - 1, g.tn_log2, r, kg);
       yo[e] = core_off(r, kg);
-      yr[e] = gather8(g.Y, yb, q0 + r, k0 + kg * 8, ke);
+      ym[e] = load8(g.Y, yb, q0 + r, k0 + kg * 8, ke, yv[e]);
     }
     const int s = kt & 1;
     if (kt >= 2) {  // stage s was read by the instructions of step kt - 2
@@ -379,10 +416,10 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
     uint8_t* xs = tc_smem + s * kStage;
     uint8_t* ys = xs + kXBytes;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) *reinterpret_cast<uint4*>(xs + xo[e]) = xr[e];
+    for (int e = 0; e < 4; ++e) *reinterpret_cast<uint4*>(xs + xo[e]) = pack8(xm[e], xv[e]);
 #pragma unroll
     for (int e = 0; e < 2; ++e)
-      if (yo[e] >= 0) *reinterpret_cast<uint4*>(ys + yo[e]) = yr[e];
+      if (yo[e] >= 0) *reinterpret_cast<uint4*>(ys + yo[e]) = pack8(ym[e], yv[e]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stores, before the tensor core reads
     __syncthreads();
     if (tid == 0) {
