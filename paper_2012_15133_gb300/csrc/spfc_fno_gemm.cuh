@@ -512,32 +512,50 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
   float* const dst = g.splits > 1 ? g.ws : o.p + (long long)bt * o.sb;
   const float* const cin = o.beta != 0.f ? (o.cin ? o.cin : o.p) + (long long)bt * o.sb : nullptr;
   float* const pre = o.pre ? o.pre + (long long)bt * o.sb : nullptr;
-  const bool raw = g.splits > 1;
-  const int total = TM * g.tn;
-  for (int lin = tid; lin < total; lin += TT) {
-    int i, j;
-    if (g.ifast) {
-      i = lin & (TM - 1);
-      j = lin >> 7;
-    } else {
-      j = lin & (g.tn - 1);
-      i = lin >> g.tn_log2;
+  // raw: split-K partial sums, or an epilogue that is the identity
+  const bool raw = g.splits > 1 || (o.alpha == 1.f && !cin && !o.bias && o.act != 1);
+  // EG elements per thread at a time: their C loads are all in flight before the first use
+  constexpr int EG = 8;
+  for (int l0 = tid; l0 < TM * g.tn; l0 += TT * EG) {  // TM * tn is a multiple of TT * EG
+    long long off[EG];
+    float c[EG];
+    int ci[EG];
+#pragma unroll
+    for (int u = 0; u < EG; ++u) {
+      const int lin = l0 + u * TT;
+      int i, j;
+      if (g.ifast) {
+        i = lin & (TM - 1);
+        j = lin >> 7;
+      } else {
+        j = lin & (g.tn - 1);
+        i = lin >> g.tn_log2;
+      }
+      const bool in = p0 + i < g.X.rows && q0 + j < g.Y.rows;
+      ci[u] = in ? i * kEpiPitch + j : -1;
+      off[u] = in ? poff[i] + qoff[j] : 0;
+      c[u] = (in && cin) ? cin[off[u]] : 0.f;
     }
-    if (p0 + i >= g.X.rows || q0 + j >= g.Y.rows) continue;
-    const float acc = cs[i * kEpiPitch + j];
-    const long long off = poff[i] + qoff[j];
-    if (raw) {
-      dst[off] = acc;
-      continue;
+#pragma unroll
+    for (int u = 0; u < EG; ++u) {
+      if (ci[u] < 0) continue;
+      const float acc = cs[ci[u]];
+      if (raw) {
+        dst[off[u]] = acc;
+        continue;
+      }
+      const int lin = l0 + u * TT;
+      const int i = g.ifast ? (lin & (TM - 1)) : (lin >> g.tn_log2);
+      const int j = g.ifast ? (lin >> 7) : (lin & (g.tn - 1));
+      float v = o.alpha * acc;  // the order of store_out: alpha A B, + beta C, + bias, then GELU
+      if (cin) v += o.beta * c[u];
+      if (o.bias) v += pbias[i] + qbias[j];  // one of the two is zero
+      if (o.act == 1) {
+        if (pre) pre[off[u]] = v;
+        v = gelu_f(v);
+      }
+      dst[off[u]] = v;
     }
-    float v = o.alpha * acc;  // the order of store_out: alpha A B, + beta C, + bias, then GELU
-    if (cin) v += o.beta * cin[off];
-    if (o.bias) v += pbias[i] + qbias[j];  // one of the two is zero
-    if (o.act == 1) {
-      if (pre) pre[off] = v;
-      v = gelu_f(v);
-    }
-    dst[off] = v;
   }
 }
 
