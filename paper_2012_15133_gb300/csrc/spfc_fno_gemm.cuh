@@ -181,14 +181,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
 
+// One test of the phase; the thread may sleep until the phase completes, for
+// at most the hint (1 ms), instead of spinning.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
+      : "r"(smem_u32(b)), "r"(parity), "r"(1000000u)
       : "memory");
   return ok != 0;
 }
@@ -298,6 +300,19 @@ __device__ __forceinline__ int load8(const Opnd& x, long long base, int r, int k
     return 2;
   }
   const float* f = reinterpret_cast<const float*>(x.p);
+  if (x.km.m == 0) {  // one-level map: consecutive k a fixed stride apart
+    const float* fk = f + roff + (long long)k * x.km.a;
+    const long long a = x.km.a;
+    if (k + 8 <= ke) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = fk[j * a];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k + j < ke) v[j] = fk[j * a];
+    }
+    return 0;
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j)
     if (k + j < ke) v[j] = f[roff + x.km(k + j)];
