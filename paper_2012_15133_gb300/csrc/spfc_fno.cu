@@ -242,36 +242,39 @@ __global__ void k_gelu_back(long long n, const float* __restrict__ u, float* __r
     g[i] *= gelu_grad_f(u[i]);
 }
 
-// out[c] = sum_{b,p} X[b][c][p] in two fixed-order stages: block (c, j)
-// sums chunk j of the B*P values of channel c into part[c][j]; then one
-// block per channel sums its parts.
-constexpr int kBiasChunks = 64;
+// out[c] = sum_{b,p} X[b][c][p] in two fixed-order stages: one block per
+// (quarter of the points, sample, channel) into part[c][b][quarter], then
+// one block per channel sums its parts.
+constexpr int kBiasSplit = 4;  // blocks per (channel, sample): P / 4 contiguous points each
 
+// grid (kBiasSplit, B, C): the sum of X[b][c][s P/4 .. (s+1) P/4) (P a
+// multiple of 16, X 16-byte aligned), fixed order: each thread sums its
+// float4s in four float32 partials (a few dozen values each; float64 per
+// element would make the FP64 pipe the bound), then float64 across threads.
 __global__ void k_bias_grad_part(int B, int C, int P, const float* __restrict__ X, double* __restrict__ part) {
   __shared__ double red[32];
-  const int c = blockIdx.x, j = blockIdx.y;
-  const long long total = (long long)B * P;
-  const long long len = (total + kBiasChunks - 1) / kBiasChunks;
-  const long long i0 = j * len, i1 = min(total, i0 + len);
-  double s = 0.0;
-  long long i = i0 + threadIdx.x, b = i / P, p = i - b * P;  // (b, p) of i, advanced without a division
-#pragma unroll 8
-  for (; i < i1; i += blockDim.x) {  // loads of several iterations in flight; the sum in the same order
-    s += X[(b * C + c) * P + p];
-    p += blockDim.x;
-    if (p >= P) {  // blockDim.x <= P: at most one carry
-      p -= P;
-      ++b;
-    }
+  const int sp = blockIdx.x, b = blockIdx.y, c = blockIdx.z;
+  const int len4 = P / (4 * kBiasSplit);
+  const float4* x4 = reinterpret_cast<const float4*>(X + ((long long)b * C + c) * P) + (long long)sp * len4;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < len4; i += blockDim.x) {
+    const float4 v = x4[i];
+    a.x += v.x;
+    a.y += v.y;
+    a.z += v.z;
+    a.w += v.w;
   }
+  double s = ((double)a.x + (double)a.y) + ((double)a.z + (double)a.w);
   s = spfc::block_sum(s, red);
-  if (threadIdx.x == 0) part[c * kBiasChunks + j] = s;
+  if (threadIdx.x == 0) part[((long long)c * B + b) * kBiasSplit + sp] = s;
 }
 
-__global__ void k_bias_grad_final(const double* __restrict__ part, float* __restrict__ out) {
+// out[c] = the sum of channel c's B * kBiasSplit partials (<= blockDim.x), fixed order
+__global__ void k_bias_grad_final(int n, const double* __restrict__ part, float* __restrict__ out) {
   __shared__ double red[32];
   const int c = blockIdx.x;
-  double s = threadIdx.x < kBiasChunks ? part[c * kBiasChunks + threadIdx.x] : 0.0;
+  double s = threadIdx.x < n ? part[(long long)c * n + threadIdx.x] : 0.0;
   s = spfc::block_sum(s, red);
   if (threadIdx.x == 0) out[c] = (float)s;
 }
@@ -471,7 +474,7 @@ struct spfc_fno_s {
         (rc = alloc(&gOh, mix)) || (rc = alloc(&gZ, spec)))
       return rc;
     ws_elems = 4LL << 20;  // split-K partial tiles of the weight-gradient GEMMs (M, N <= 64)
-    if ((rc = alloc(&ws, ws_elems)) || (rc = alloc(&bpart, 64LL * kBiasChunks)) || (rc = alloc(&gstat, 1)))
+    if ((rc = alloc(&ws, ws_elems)) || (rc = alloc(&bpart, 64LL * 64 * kBiasSplit)) || (rc = alloc(&gstat, 1)))
       return rc;
     if ((rc = ck(cudaMemset(gstat, 0, sizeof(int)), "memset"))) return rc;
     const size_t smix = (size_t)(2 * W * W + 4 * Bmax * W) * sizeof(float);
@@ -556,8 +559,8 @@ struct spfc_fno_s {
   }
 
   void bias_grad(int B, int C, const float* X, float* out) {
-    k_bias_grad_part<<<dim3(C, kBiasChunks), 256, 0, st>>>(B, C, P, X, bpart);
-    k_bias_grad_final<<<C, 64, 0, st>>>(bpart, out);
+    k_bias_grad_part<<<dim3(kBiasSplit, B, C), 256, 0, st>>>(B, C, P, X, bpart);
+    k_bias_grad_final<<<C, 256, 0, st>>>(B * kBiasSplit, bpart, out);
   }
 
   // dL/d(parameters) for the B samples of the last forward pass, given gd = dL/dd

@@ -88,17 +88,23 @@ __device__ __forceinline__ void store_out(const Out& o, long long base, int row,
   o.p[off] = v;
 }
 
-// Fixed-order reduction of the split-K partial sums, then the epilogue.
+// Fixed-order reduction of the split-K partial sums, then the epilogue: one
+// warp per output element, lane l summing splits l, l + 32, .. in order, then
+// a fixed butterfly; lane 0 stores.
 __global__ void k_gemm_reduce(int M, int N, int batch, int splits, const float* __restrict__ ws, Out O) {
   const long long total = (long long)batch * M * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = w0; i < total; i += nw) {
     const int bt = (int)(i / ((long long)M * N));
     const int rem = (int)(i % ((long long)M * N));
     const int row = rem / N, col = rem % N;
     float s = 0.f;
-    for (int sp = 0; sp < splits; ++sp) s += ws[(((long long)bt * splits + sp) * M + row) * N + col];
-    store_out(O, (long long)bt * O.sb, row, col, s);
+    for (int sp = lane; sp < splits; sp += 32) s += ws[(((long long)bt * splits + sp) * M + row) * N + col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) store_out(O, (long long)bt * O.sb, row, col, s);
   }
 }
 
