@@ -349,9 +349,13 @@ const char* spfc_fno_last_error(spfc_fno_t f);
  * bfloat16 (nearest even) and accumulates in float32; splits > 1 sums K in
  * `splits` chunks in a fixed order. flags: 1 = A stored as bfloat16 on the
  * device, 2 = A stored column-major, 4 = B stored column-major (the storage
- * only; the arguments stay row-major). Synchronises the stream. SPFC_EINVAL
- * for bad sizes (each array <= 2^26 elements, splits <= 1024) or flags,
- * SPFC_ETIMEOUT if a bounded wait ran out. */
+ * only; the arguments stay row-major), 8 = a test of the wait bound: after
+ * its product, each tile waits for an mbarrier phase that nothing completes,
+ * so the wait runs out after about a second, latches the status and the
+ * tile is left unwritten (C undefined); the call returns SPFC_ETIMEOUT and
+ * the context stays usable. Synchronises the stream. SPFC_EINVAL for bad
+ * sizes (each array <= 2^26 elements, splits <= 1024) or flags, SPFC_ETIMEOUT
+ * if a bounded wait ran out. */
 int spfc_gemm_selftest(int M, int N, int K, int batch, int splits, int flags, const float* A, const float* B,
                        float* C, void* cuda_stream);
 /* Weight file: magic "SPFCFNO1", int32 {n, width, modes1, modes2, layers,

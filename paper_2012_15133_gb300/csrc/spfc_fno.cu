@@ -780,7 +780,7 @@ void spfc_fno_destroy(spfc_fno_t f) { delete f; }
 
 int spfc_gemm_selftest(int M, int N, int K, int batch, int splits, int flags, const float* A, const float* B,
                        float* C, void* stream) {
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || splits < 1 || splits > 1024 || (flags & ~7))
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || splits < 1 || splits > 1024 || (flags & ~15))
     return SPFC_EINVAL;
   const long long na = (long long)batch * M * K, nb = (long long)batch * K * N, nc = (long long)batch * M * N;
   if (na > (1ll << 26) || nb > (1ll << 26) || nc * splits > (1ll << 26)) return SPFC_EINVAL;
@@ -837,7 +837,7 @@ int spfc_gemm_selftest(int M, int N, int K, int batch, int splits, int flags, co
       o.r = make_ix(N);
       o.c = make_ix(1);
       o.sb = (long long)M * N;
-      e = launch_gemm(M, N, K, batch, ma, mbm, o, splits, ws, status, st);
+      e = launch_gemm(M, N, K, batch, ma, mbm, o, splits, ws, status, st, (flags & 8) ? 1 : 0);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dc, (size_t)nc * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -164,6 +164,7 @@ struct TcArgs {
   Out O;
   float* ws = nullptr;
   int* status = nullptr;
+  int stall_test = 0;  // self-test of the wait bound (never set by the network)
 };
 
 __host__ __device__ constexpr uint32_t tc_idesc(int n) {
@@ -454,14 +455,18 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
     issued = kt + 1;
   }
   if (ok && issued > 0) {
-    if (tid == 0) ok_s = mbar_wait_bounded(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+    if (tid == 0) {
+      ok_s = mbar_wait_bounded(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+      if (ok_s && g.stall_test)  // test of the bound: the next phase, which no instruction completes
+        ok_s = mbar_wait_bounded(&mbar[(issued - 1) & 1], (((issued - 1) >> 1) + 1) & 1);
+    }
     __syncthreads();
     ok = ok_s != 0;
   }
   if (!ok) {
     if (tid == 0) {
       atomicExch(g.status, 1);
-      mbar_wait_bounded(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
+      if (issued > 0) mbar_wait_bounded(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -599,8 +604,9 @@ inline Opnd make_opnd(const Mat& m, const Ix& rm, const Ix& km, int rows) {
 // ws (batch * splits * M * N floats) in a fixed order. status: a device int
 // that a wait which ran out sets to 1.
 inline cudaError_t launch_gemm(int M, int N, int K, int batch, const Mat& A, const Mat& B, const Out& O, int splits,
-                               float* ws, int* status, cudaStream_t st) {
+                               float* ws, int* status, cudaStream_t st, int stall_test = 0) {
   TcArgs t;
+  t.stall_test = stall_test;
   t.swap = N > M ? 1 : 0;
   if (!t.swap) {
     t.X = make_opnd(A, A.r, A.c, M);

@@ -203,3 +203,23 @@ def test_tensor_core_gemm_is_deterministic():
     C1 = spfc.gemm_selftest(A, B, splits=3)
     C2 = spfc.gemm_selftest(A, B, splits=3)
     assert np.array_equal(C1, C2)
+
+
+def test_tensor_core_gemm_wait_bound_latches_timeout_and_context_survives():
+    """A wait that nothing completes (the self-test's flag 8) ends by its
+    bound (about a second), the call reports SPFC_ETIMEOUT, and the next
+    product on the same context is exact again."""
+    import time
+    from paper_2012_15133_gb300 import spfc, SPFCError
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((1, 100, 64)).astype(np.float32)
+    B = rng.standard_normal((1, 64, 16)).astype(np.float32)
+    t0 = time.perf_counter()
+    with pytest.raises(SPFCError) as ei:
+        spfc.gemm_selftest(A, B, flags=8)
+    assert ei.value.code == 5  # SPFC_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    C = spfc.gemm_selftest(A, B)
+    ref = _round_bf16(A).astype(np.float64) @ _round_bf16(B).astype(np.float64)
+    bound = 4 * 64 * 2.0 ** -24 * (np.abs(_round_bf16(A)).astype(np.float64) @ np.abs(_round_bf16(B)).astype(np.float64))
+    assert np.all(np.abs(C - ref) <= bound)
