@@ -322,8 +322,11 @@ const char* spfc_batch_last_error(spfc_batch_t b);
  * accumulation, on the fifth-generation tensor cores (tcgen05.mma with the
  * accumulator in tensor memory). Fields are float32 device arrays
  * [batch][n][n]. The products' device-side waits are bounded: one that runs
- * out latches a status that spfc_fno_predict, spfc_fno_loss_grad (and every
- * later call of the handle) report as SPFC_ETIMEOUT.
+ * out latches a status word of the handle, and the tile it was computing is
+ * left unwritten. spfc_fno_loss_grad, which synchronises, reports it as
+ * SPFC_ETIMEOUT; spfc_fno_predict does not synchronise, so the next
+ * spfc_fno_predict or spfc_fno_loss_grad call reports it. Every call after
+ * that returns SPFC_ETIMEOUT too.
  * ------------------------------------------------------------------------- */
 typedef struct spfc_fno_s* spfc_fno_t;
 
