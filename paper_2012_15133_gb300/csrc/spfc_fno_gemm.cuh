@@ -536,51 +536,75 @@ __global__ void __launch_bounds__(TT) k_gemm_tc(const TcArgs g) {
 
   const Out& o = g.O;
   float* const dst = g.splits > 1 ? g.ws : o.p + (long long)bt * o.sb;
-  const float* const cin = o.beta != 0.f ? (o.cin ? o.cin : o.p) + (long long)bt * o.sb : nullptr;
+  // with split-K the offsets address the workspace and k_gemm_reduce applies beta C: no C here
+  const float* const cin =
+      (g.splits == 1 && o.beta != 0.f) ? (o.cin ? o.cin : o.p) + (long long)bt * o.sb : nullptr;
   float* const pre = o.pre ? o.pre + (long long)bt * o.sb : nullptr;
   // raw: split-K partial sums, or an epilogue that is the identity
   const bool raw = g.splits > 1 || (o.alpha == 1.f && !cin && !o.bias && o.act != 1);
-  // EG elements per thread at a time: their C loads are all in flight before the first use
-  constexpr int EG = 8;
-  for (int l0 = tid; l0 < TM * g.tn; l0 += TT * EG) {  // TM * tn is a multiple of TT * EG
-    long long off[EG];
-    float c[EG];
-    int ci[EG];
-#pragma unroll
-    for (int u = 0; u < EG; ++u) {
-      const int lin = l0 + u * TT;
-      int i, j;
-      if (g.ifast) {
-        i = lin & (TM - 1);
-        j = lin >> 7;
-      } else {
-        j = lin & (g.tn - 1);
-        i = lin >> g.tn_log2;
-      }
-      const bool in = p0 + i < g.X.rows && q0 + j < g.Y.rows;
-      ci[u] = in ? i * kEpiPitch + j : -1;
-      off[u] = in ? poff[i] + qoff[j] : 0;
-      c[u] = (in && cin) ? cin[off[u]] : 0.f;
+  // One output element: the epilogue in the order of store_out (alpha A B, + beta C, + bias, then GELU).
+  auto emit = [&](long long off, float acc, float c, float bias) {
+    if (raw) {
+      dst[off] = acc;
+      return;
     }
+    float v = o.alpha * acc;
+    if (cin) v += o.beta * c;
+    if (o.bias) v += bias;  // one of the row and column terms is zero
+    if (o.act == 1) {
+      if (pre) pre[off] = v;
+      v = gelu_f(v);
+    }
+    dst[off] = v;
+  };
+  // EG elements per thread at a time: their C loads are all in flight before the first use.
+  // Consecutive threads run along the output's unit-stride dimension, so each thread keeps one
+  // tile row (ifast) or one tile column for the whole tile.
+  constexpr int EG = 8;
+  if (g.ifast) {
+    const int i = tid;  // TT == TM
+    const int jn = min(g.tn, g.Y.rows - q0);
+    if (p0 + i < g.X.rows) {
+      const long long pi = poff[i];
+      const float pb = pbias[i];
+      for (int j0 = 0; j0 < jn; j0 += EG) {
+        long long off[EG];
+        float c[EG];
 #pragma unroll
-    for (int u = 0; u < EG; ++u) {
-      if (ci[u] < 0) continue;
-      const float acc = cs[ci[u]];
-      if (raw) {
-        dst[off[u]] = acc;
-        continue;
+        for (int u = 0; u < EG; ++u) {
+          const int j = j0 + u;
+          off[u] = j < jn ? pi + qoff[j] : 0;
+          c[u] = (j < jn && cin) ? cin[off[u]] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < EG; ++u) {
+          const int j = j0 + u;
+          if (j < jn) emit(off[u], cs[i * kEpiPitch + j], c[u], pb + qbias[j]);
+        }
       }
-      const int lin = l0 + u * TT;
-      const int i = g.ifast ? (lin & (TM - 1)) : (lin >> g.tn_log2);
-      const int j = g.ifast ? (lin >> 7) : (lin & (g.tn - 1));
-      float v = o.alpha * acc;  // the order of store_out: alpha A B, + beta C, + bias, then GELU
-      if (cin) v += o.beta * c[u];
-      if (o.bias) v += pbias[i] + qbias[j];  // one of the two is zero
-      if (o.act == 1) {
-        if (pre) pre[off[u]] = v;
-        v = gelu_f(v);
+    }
+  } else {
+    const int j = tid & (g.tn - 1);
+    const int istep = TT >> g.tn_log2;  // rows covered by the block per pass: 8, 4 or 2
+    const int in = min(TM, g.X.rows - p0);
+    if (q0 + j < g.Y.rows) {
+      const long long qj = qoff[j];
+      const float qb = qbias[j];
+      for (int i0 = tid >> g.tn_log2; i0 < in; i0 += istep * EG) {
+        long long off[EG];
+        float c[EG];
+#pragma unroll
+        for (int u = 0; u < EG; ++u) {
+          const int i = i0 + u * istep;
+          off[u] = i < in ? poff[i] + qj : 0;
+          c[u] = (i < in && cin) ? cin[off[u]] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < EG; ++u) {
+          const int i = i0 + u * istep;
+          if (i < in) emit(off[u], cs[i * kEpiPitch + j], c[u], pbias[i] + qb);
+        }
       }
-      dst[off[u]] = v;
     }
   }
 }
