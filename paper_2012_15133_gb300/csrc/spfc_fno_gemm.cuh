@@ -129,8 +129,10 @@ __global__ void k_gemm_reduce(int M, int N, int batch, int splits, const float* 
 // Epilogue: tcgen05.ld moves each warp's 32 accumulator rows to registers,
 // then to shared memory (pitch tn_max + 1, conflict-free), and the tile is
 // written out with consecutive threads along the output's unit-stride
-// dimension, through the same epilogue as before (alpha, beta * C, bias,
-// GELU, pre-activation store) or, with split-K, as raw partial sums.
+// dimension (each thread keeping one tile row or one tile column), through
+// the epilogue of store_out (alpha, beta * C, bias, GELU, pre-activation
+// store) or, with split-K, as raw partial sums. The output offsets and the
+// bias of every tile row and column are computed once, into shared memory.
 // ---------------------------------------------------------------------------
 constexpr int TM = 128;                  // MMA rows = tensor-memory lanes
 constexpr int TNMAX = 64;                // MMA columns at most = tensor-memory columns allocated
