@@ -81,6 +81,13 @@ def test_other_entry_points_refuse_bad_arguments_before_touching_the_gpu(lib):
     assert L.spfc_batch_create(1, n1, L1, (ct.c_double * 1)(1.2), (ct.c_double * 1)(1.0), 0.02, 1, None,
                                ct.byref(b)) == 1                                  # a = 1 - eps <= 0
     assert b"1 - eps" in L.spfc_batch_last_error(None)
+    # the tensor-core GEMM self-test: sizes, split count and flags are checked first
+    buf = (ct.c_float * 64)()
+    assert L.spfc_gemm_selftest(0, 4, 4, 1, 1, 0, buf, buf, buf, None) == 1       # M = 0
+    assert L.spfc_gemm_selftest(4, 4, 4, 1, 2000, 0, buf, buf, buf, None) == 1    # splits > 1024
+    assert L.spfc_gemm_selftest(4, 4, 4, 1, 1, 16, buf, buf, buf, None) == 1      # unknown flag
+    assert L.spfc_gemm_selftest(4, 4, 4, 1, 1, 0, None, buf, buf, None) == 1      # NULL operand
+    assert L.spfc_gemm_selftest(1 << 14, 1 << 13, 1, 1, 1, 0, buf, buf, buf, None) == 1  # C beyond 2^26
 
 
 def test_product_path_has_no_oracle_dependency():
